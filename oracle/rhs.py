@@ -14,6 +14,8 @@ Sources:
 
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from .green import NCOMP, lin_axis
@@ -31,12 +33,18 @@ def _f0(k):
 
 
 def _f1(k):
-    """int_{-1/2}^{1/2} s exp(-i k s) ds = i d/dk _f0(k)."""
+    """int_{-1/2}^{1/2} s exp(-i k s) ds = i d/dk _f0(k).
+
+    The closed form i (cos(k/2)/k - 2 sin(k/2)/k^2) cancels for small k; below
+    |k| = 1/4 the Taylor series sum_{n odd} (-i k)^n 2^-(n+1) / (n! (n+2)) is used
+    (terms to k^9; the first omitted term is below 1e-17 relative there)."""
     k = np.asarray(k, dtype=float)
-    small = np.abs(k) < 1e-3
+    small = np.abs(k) < 0.25
     ks = np.where(small, 1.0, k)
     exact = 1j * (np.cos(ks / 2.0) / ks - 2.0 * np.sin(ks / 2.0) / ks**2)
-    series = -1j * (k / 12.0 - k**3 / 480.0 + k**5 / 53760.0)
+    series = np.zeros_like(k, dtype=complex)
+    for n in (1, 3, 5, 7, 9):
+        series = series + (-1j * k) ** n * 0.5 ** (n + 1) / (math.factorial(n) * (n + 2))
     return np.where(small, series, exact)
 
 

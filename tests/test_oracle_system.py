@@ -187,3 +187,13 @@ def test_sphere_absorbed_power_vs_mie():
         _, Pabs = P.absorbed_power(prob, x)
         errs.append(abs(Pabs - mie.absorbed_power(50.0, 0.5, 0.1, 298e6)) / mie.absorbed_power(50.0, 0.5, 0.1, 298e6))
     assert errs[0] < 0.15 and errs[1] < errs[0]
+
+
+def test_planewave_voxel_integrals_vs_mpmath():
+    """The 1-D voxel integrals of Eq. 30 for a plane wave, int s^k exp(-i kappa s) ds, vs mpmath quadrature
+    across the switch between the Taylor series and the closed form."""
+    mp = pytest.importorskip("mpmath")
+    for kap in (1e-6, 1e-3, 0.07, 0.2499, 0.25, 0.3, 1.3, 4.0):
+        for k, f in ((0, R._f0), (1, R._f1)):
+            ref = complex(mp.quad(lambda s: s ** k * mp.exp(-1j * kap * s), [-0.5, 0.5]))
+            assert abs(complex(f(np.array(kap))) - ref) <= 1e-13 * abs(ref)
