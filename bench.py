@@ -1,0 +1,483 @@
+#!/usr/bin/env python3
+"""Benchmark of the PWL-VIE hot path on GB300.
+
+Workload (one step = the whole hot path over one batch): the 64^3 head-size
+ellipsoid phantom (4 nested shells + smoothed seeded noise, 3 mm voxels,
+298 MHz), 16 right-hand sides from z-directed Hertzian dipoles on a 15 cm ring;
+one step is a batched mixed-precision solve (FP32 FFT matvec and FP32 GMRES
+inside FP64 iterative refinement) to a preconditioned relative residual of
+1e-6 for all 16 right-hand sides, followed by the post-processing of the
+solution (tested fields / PWL field coefficients and absorbed-power density).
+`value` is right-hand sides solved per second over all ranks.
+
+Also reported: the plain FP64 GPU solve of the same batch (solves/s and the
+ratio), step latency p50/p99, the batched FP32 matvec's algorithmic HBM
+throughput, the roofline of the dominant kernel (device time from CUDA events
+recorded around every library launch on the launch stream), the end-to-end
+figure through the C ABI with host buffers, and the FP64 CPU oracle on a
+bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; each rank solves its own batch
+(independent replicas, weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PWL-VIE matvec HBM GB/s & solves/s vs plain FP64 at 1e-6 residual; p99 latency"
+WORKLOAD = ("head64: 64x64x64 head ellipsoid phantom (4 shells + smoothed noise, seed 1234), 3 mm voxels, "
+            "298 MHz, 16 z-dipole RHS on a 15 cm ring; batched FP32 GMRES + FP64 refinement to 1e-6 "
+            "preconditioned residual, then fields + SAR post-processing")
+NRHS = 16
+TOL = 1e-6
+RESTART = 50
+MAXIT = 30
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (subprocess: fresh interpreter, no CUDA)
+# ---------------------------------------------------------------------------
+ORACLE_SAMPLE = r"""
+import os, sys, time, json, math
+sys.path.insert(0, {root!r})
+import numpy as np
+from synth import workload
+from oracle import operator as O, rhs as R, solver as S
+w = workload("head", n={n})
+g = w["grid"]
+prob = O.Problem(g, w["freq"], w["eps_real"], w["sigma"])
+t0 = time.perf_counter(); Nop = O.NOperator(g, prob.k0); t_setup = time.perf_counter() - t0
+e = R.dipoles_tested(g, prob.k0, prob.ce, w["dip_pos"][:1], w["dip_mom"][:1])[0]
+b = R.rhs(prob, e)
+times = []; iters = []
+for s in range({reps}):
+    t0 = time.perf_counter()
+    x, info = S.gmres(lambda v: O.apply_PA(prob, Nop, v), O.apply_Pinv(prob, b), tol={tol}, restart={restart}, maxit={maxit})
+    times.append(time.perf_counter() - t0); iters.append(info["iters"])
+print(json.dumps(dict(times=times, iters=iters, setup_s=t_setup, nv=g.nv)))
+"""
+
+
+def oracle_sample(n=16, reps=1):
+    """Oracle GMRES (FP64, NumPy, single thread) for one dipole RHS of the head phantom family at n^3
+    (192 mm box, voxel 192/n mm), Green setup excluded; returns dict(times, iters, setup_s, nv)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ORACLE_SAMPLE.format(root=ROOT, n=n, reps=reps, tol=TOL, restart=RESTART, maxit=MAXIT)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if p.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def scale_to_workload(t_sample, n_sample, n_target=64):
+    """Per-solve time scaled from the sample grid to the target grid by the FFT-matvec work ratio
+    (padded size M = (2n)^3 times log2 M), assuming the preconditioned iteration count does not grow
+    with refinement (Section V-C observes nearly h-independent counts with the preconditioner)."""
+    def work(n):
+        M = (2 * n) ** 3
+        return M * math.log2(M)
+
+    return t_sample * work(n_target) / work(n_sample)
+
+
+def cpu_baseline_block(n=16):
+    s = oracle_sample(n=n, reps=1)
+    t = statistics.median(s["times"])
+    t64 = scale_to_workload(t, n)
+    return dict(
+        value=1.0 / t64,
+        unit="solves/s",
+        cores=1,
+        kind="oracle",
+        sample=(f"oracle FP64 GMRES (NumPy, 1 thread) of 1 dipole RHS on the {n}^3 head-phantom grid "
+                f"(same 192 mm box, {192.0 / n:.0f} mm voxels) to 1e-6: {t:.2f} s, {s['iters'][0]} iterations, "
+                f"Green setup {s['setup_s']:.1f} s excluded; scaled to 64^3 by the matvec work ratio "
+                f"M log2 M (x{t64 / t:.0f})"),
+        sample_seconds=t,
+    )
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle, as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    n = 16
+    s = oracle_sample(n=n, reps=args.warmup + args.steps)
+    times = s["times"][args.warmup:]
+    t = sum(times)
+    per = [scale_to_workload(ti, n) for ti in times]
+    value = len(per) / sum(per)
+    line = dict(
+        impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus, steps=args.steps,
+        warmup=args.warmup, ms_per_step=1000.0 * sum(per) / len(per), higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=WORKLOAD, nrhs=1, sample=f"{n}^3"),
+        cpu_baseline=dict(value=value, unit="solves/s", cores=1, kind="oracle",
+                          sample=f"oracle FP64 GMRES, 1 dipole RHS at {n}^3 per step ({t / len(times):.2f} s), "
+                                 f"scaled to 64^3 by M log2 M"),
+        e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+    )
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=smax, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes / flops per launch of the matvec kernels (FP32: c = 8 bytes, FP64: c = 16)
+# ---------------------------------------------------------------------------
+def kernel_model(name, grid, L, R):
+    nx, ny, nz = grid
+    Lx, Ly, Lz = L
+    Ox, Oy, Oz = Lx // 2 + 1, Ly // 2 + 1, Lz // 2 + 1
+    c = 16 if name.endswith("f64") else 8
+    C = 12 * R
+    nv = nx * ny * nz
+    lg = math.log2
+    if name.startswith("fft_x"):
+        return C * nv * c + C * nz * ny * Lx * c, 5.0 * Lx * lg(Lx) * C * nz * ny
+    if name.startswith("fft_y"):
+        return C * nz * ny * Lx * c + C * nz * Ly * Lx * c, 5.0 * Ly * lg(Ly) * C * nz * Lx
+    if name.startswith("zpass_block"):
+        b = 2 * C * nz * Ly * Lx * c + 60 * Ox * Oy * Oz * c
+        f = 2 * 5.0 * Lz * lg(Lz) * C * Lx * Ly + 144 * 8.0 * R * Lx * Ly * Lz
+        return b, f
+    if name.startswith("ifft_y"):
+        return C * nz * Ly * Lx * c + C * nz * ny * Lx * c, 5.0 * Ly * lg(Ly) * C * nz * Lx
+    if name.startswith("ifft_x_epilogue"):
+        return C * nz * ny * Lx * c + 2 * C * nv * c + 2 * nv * c, 5.0 * Lx * lg(Lx) * C * nz * ny
+    return None, None
+
+
+def matvec_alg_bytes(grid, L, R, c):
+    """Three-sweep lower bound of one batched matvec: x read once, half-padded spectrum written after
+    the xy transforms, read and written by the z pass, read by the inverse xy pass, x re-read and y
+    written by the epilogue; Green octant read once."""
+    nx, ny, nz = grid
+    Lx, Ly, Lz = L
+    C = 12 * R
+    spec = C * nz * Ly * Lx * c
+    return C * nx * ny * nz * c * 3 + 3 * spec + 60 * (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1) * c
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1902_02196_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import workload
+
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vie.build()
+    w = workload("head64")
+    g = w["grid"]
+    grid = (g.nx, g.ny, g.nz)
+    t0 = time.perf_counter()
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), w["freq"], w["eps_real"], w["sigma"])
+    setup_s = time.perf_counter() - t0
+    L, _ = vie.vie_info(h)
+    stream = torch.cuda.current_stream(dev)
+    shape = (NRHS, 12) + g.shape
+    e_inc = torch.empty(shape, dtype=torch.complex128, device=dev)
+    b = torch.empty_like(e_inc)
+    vie.vie_rhs_dipoles(h, w["dip_pos"], w["dip_mom"], e_inc, b, stream=stream)
+    x = torch.empty_like(b)
+    e_coeff = torch.empty_like(b)
+    p_abs = torch.empty((NRHS,) + g.shape, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def step(mode=vie.VIE_SOLVE_FP32_REFINE):
+        rc, info = vie.vie_solve(h, b, x, tol=TOL, restart=RESTART, maxit=MAXIT, mode=mode, stream=stream)
+        P = vie.vie_fields(h, x, e_inc, e_coeff, p_abs, stream=stream)
+        return rc, info, P
+
+    for _ in range(max(3, args.warmup)):
+        rc, info, P = step()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    vie.vie_stats_reset(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        rc, info, P = step()
+        evs[i][1].record(stream)
+        infos.append((rc, info, P))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier()
+    clk = clocks.stop()
+    total_launches, kstats = vie.vie_stats_read()
+    vie.vie_stats_reset(False)
+    step_ms = [a.elapsed_time(bb) for a, bb in evs]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = NRHS * args.steps * ws / (total_ms / 1000.0)
+    rcs = [r for r, _, _ in infos]
+    last_info = infos[-1][1]
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+        return
+
+    # dominant kernel over the timed region
+    dom = max(kstats.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms) = dom
+    bytes_pl, flops_pl = kernel_model(dname, grid, L, NRHS)
+    hbm_peak, peak_kind = peaks()
+    avg_s = dms / dl / 1000.0
+    if bytes_pl is not None and dname.endswith("f32"):
+        achieved = bytes_pl / avg_s / 1e9
+        roofline = dict(bound="hbm", kernel=dname, achieved=achieved, peak=hbm_peak, unit="GB/s",
+                        frac=achieved / hbm_peak, traffic=measured_traffic(dname), peak_kind=peak_kind,
+                        launches=dl, avg_ms=1000 * avg_s, alg_bytes_per_launch=bytes_pl)
+    elif flops_pl is not None:
+        fp64_peak = 1250.0  # GFLOP/s, nominal GB300 FP64 rate
+        achieved = flops_pl / avg_s / 1e9
+        roofline = dict(bound="alu", kernel=dname, achieved=achieved, peak=fp64_peak, unit="GFLOP/s",
+                        frac=achieved / fp64_peak, traffic=measured_traffic(dname), peak_kind="nominal FP64",
+                        launches=dl, avg_ms=1000 * avg_s, alg_flops_per_launch=flops_pl)
+    else:
+        roofline = dict(bound="hbm", kernel=dname, achieved=None, peak=hbm_peak, unit="GB/s", frac=None,
+                        traffic=None, launches=dl, avg_ms=1000 * avg_s)
+    share = {k: round(v[1] / max(1e-9, sum(x[1] for x in kstats.values())), 4) for k, v in
+             sorted(kstats.items(), key=lambda kv: -kv[1][1])[:8]}
+
+    # batched FP32 matvec throughput (events on the launch stream)
+    x32 = torch.randn(shape, dtype=torch.complex64, device=dev)
+    y32 = torch.empty_like(x32)
+    for _ in range(3):
+        vie.vie_matvec(h, x32, y32, vie.VIE_FP32, vie.VIE_OP_PA, stream=stream)
+    nmv = 20
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(nmv):
+        vie.vie_matvec(h, x32, y32, vie.VIE_FP32, vie.VIE_OP_PA, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = a0.elapsed_time(a1) / nmv
+    mv_bytes = matvec_alg_bytes(grid, L, NRHS, 8)
+    x64 = x32.to(torch.complex128)
+    y64 = torch.empty_like(x64)
+    vie.vie_matvec(h, x64, y64, vie.VIE_FP64, vie.VIE_OP_PA, stream=stream)
+    a0.record(stream)
+    vie.vie_matvec(h, x64, y64, vie.VIE_FP64, vie.VIE_OP_PA, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    mv64_ms = a0.elapsed_time(a1)
+    del x32, y32, x64, y64
+
+    out = dict(
+        metric=METRIC, value=value, unit="solves/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32/f64", data="synthetic",
+        config=dict(workload=WORKLOAD, nrhs=NRHS, grid=list(grid), fft=list(L), tol=TOL, restart=RESTART,
+                    l2="inputs larger than L2 (16-RHS batch: 805 MB per vector)", parallelism=f"replicas x{ws}"),
+        latency_ms=dict(p50=statistics.median(step_ms), p99=float(np.percentile(step_ms, 99)),
+                        max=max(step_ms)),
+        solve=dict(rc=rcs[-1], iterations=[i["iterations"] for i in last_info][:4],
+                   refinements=last_info[0]["refinements"], fp64_matvecs=last_info[0]["fp64_matvecs"],
+                   max_resid=max(i["resid"] for i in last_info), converged=all(i["converged"] for i in last_info)),
+        matvec=dict(fp32_ms=mv_ms, fp32_alg_gbs=mv_bytes / (mv_ms / 1000) / 1e9,
+                    fp32_frac_of_hbm=mv_bytes / (mv_ms / 1000) / 1e9 / hbm_peak, fp64_ms=mv64_ms,
+                    alg_bytes=mv_bytes),
+        roofline=roofline, kernel_share=share, gpu_launches=total_launches, setup_s=setup_s, clocks=clk,
+        wall_s=wall,
+    )
+
+    if not args.no_fp64:
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        rc64, info64, _ = step(vie.VIE_SOLVE_FP64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1000.0
+        out["fp64"] = dict(value=NRHS / t64, unit="solves/s", seconds=t64, rc=rc64,
+                           iterations=info64[0]["iterations"], max_resid=max(i["resid"] for i in info64))
+        out["speedup_vs_fp64"] = value / (NRHS * ws / t64)
+
+    if not args.no_e2e:
+        bh = b.cpu().pin_memory()
+        eh = e_inc.cpu().pin_memory()
+        xh = torch.empty(shape, dtype=torch.complex128).pin_memory()
+        ph = torch.empty((NRHS,) + g.shape, dtype=torch.float64).pin_memory()
+
+        def step_host():
+            vie.vie_solve(h, bh, xh, tol=TOL, restart=RESTART, maxit=MAXIT, mode=vie.VIE_SOLVE_FP32_REFINE,
+                          stream=stream)
+            return vie.vie_fields(h, xh, eh, None, ph, stream=stream)
+
+        step_host()
+        ke = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            step_host()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        vb = NRHS * 12 * g.nv * 16
+        out["e2e"] = dict(value=NRHS * ws / te, unit="solves/s", h2d_bytes_per_step=3 * vb,
+                          d2h_bytes_per_step=vb + NRHS * g.nv * 8,
+                          note="C ABI with pinned host buffers: b in, x out; x and e_inc in, p_abs and P_abs out")
+    if not args.no_cpu and ws == 1:
+        try:
+            out["cpu_baseline"] = cpu_baseline_block()
+        except Exception as ex:  # the CPU leg is informative only
+            out["cpu_baseline"] = dict(value=None, unit="solves/s", cores=1, kind="oracle", sample=str(ex)[:200])
+    print(json.dumps(out), flush=True)
+    h.close()
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * vie.h -- C ABI of the GB300 library for the FFT-accelerated PWL current-based
+ * volume integral equation of Georgakis, Giannakopoulos, Litsarev and
+ * Polimeridis, "A Fast Volume Integral Equation Solver with Linear Basis
+ * Functions for the Accurate Computation of EM Fields in MRI" (arXiv 1902.02196).
+ *
+ * Problem (Section II, Eq. 16):  (M_eps - M_chi N) j = c_e M_chi e_inc, dielectric body,
+ * time factor exp(i omega t), c_e = i omega eps0, chi = eps - 1, eps = eps' - i sigma/(omega eps0).
+ * Discretisation (Section III): Galerkin MoM with 4 scalar PWL functions
+ * {1, (x-xn)/dx, (y-yn)/dy, (z-zn)/dz} x 3 vector components = 12 unknowns per
+ * voxel (Eq. 19-22), system A x = b with A = M_eps G - M_chi N, b = c_e M_chi e_inc (Eq. 24).
+ *
+ * Data conventions used by every entry point:
+ *  - grid of nx*ny*nz voxels, box centred at the origin; voxel (ix,iy,iz) has its
+ *    centre at ((ix+1/2-nx/2) dx, (iy+1/2-ny/2) dy, (iz+1/2-nz/2) dz); N_V = nx*ny*nz;
+ *  - per-voxel real maps: double[nz][ny][nx] (x fastest);
+ *  - coefficient vectors: complex numbers stored as interleaved (re, im) pairs,
+ *    layout [nrhs][12][nz][ny][nx]; component alpha = 4 p + (l - 1) with p = 0,1,2
+ *    for the x,y,z vector component and l = 1..4 the scalar PWL function;
+ *  - "C128" buffers hold double pairs, "C64" buffers hold float pairs;
+ *  - every buffer is owned by the caller.  Pointers may be host or device memory
+ *    (detected with cudaPointerGetAttributes); host buffers are staged through
+ *    device memory owned by the handle and copied back before the call returns;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the handle's own stream).
+ *    Calls with device buffers are asynchronous with respect to the host unless
+ *    stated otherwise; calls with host buffers synchronise the stream.
+ *
+ * Errors: every int-returning function returns VIE_OK (0), a negative error
+ * code, or the positive VIE_NOT_CONVERGED.  No exception or abort crosses the
+ * ABI.  vie_strerror() gives a static description; vie_last_error() the detail
+ * of the most recent failure on the calling thread.
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VIE_OK 0
+#define VIE_EINVAL (-1)        /* invalid argument (sizes, NULL pointer, NaN input, unknown flag) */
+#define VIE_ENOMEM (-2)        /* device or host allocation failed */
+#define VIE_EDEVICE (-3)       /* a CUDA call or kernel launch failed */
+#define VIE_ETIMEOUT (-4)      /* a bounded wait ran out */
+#define VIE_NOT_CONVERGED 1    /* solver hit its iteration limit; best iterate returned */
+
+/* Compute precision of a matvec; also the element type of its vectors. */
+#define VIE_FP64 0 /* complex128 vectors, FP64 FFT and block product */
+#define VIE_FP32 1 /* complex64 vectors, FP32 FFT and block product */
+
+/* Operator applied by vie_matvec. */
+#define VIE_OP_A 0      /* y = A x = M_eps G x - M_chi N x                     (Eq. 24) */
+#define VIE_OP_PA 1     /* y = P^-1 A x, P = M_eps G: x/eps - tau G^-1 (N - G) x (Section IV-B, Eq. 17) */
+#define VIE_OP_NSCAT 2  /* y = (N - G) x, the Galerkin "N - I" operator (tested scattered field * c_e) */
+
+/* Solver modes of vie_solve. */
+#define VIE_SOLVE_FP64 0         /* plain FP64 GMRES */
+#define VIE_SOLVE_FP32_REFINE 1  /* FP32 inner GMRES inside FP64 iterative refinement */
+
+typedef struct vie_handle vie_handle;
+
+typedef struct {
+    int nx, ny, nz;    /* voxels per axis, >= 1 */
+    double dx, dy, dz; /* voxel side lengths in metres, > 0 */
+} vie_grid;
+
+typedef struct {
+    int converged;       /* 1 if resid <= tol */
+    int iterations;      /* GMRES (Arnoldi) steps taken, all precisions */
+    int fp64_matvecs;    /* FP64 operator applications (refinement residuals, plain FP64 steps) */
+    int fp32_matvecs;    /* FP32 operator applications */
+    int refinements;     /* outer refinement sweeps (mode VIE_SOLVE_FP32_REFINE) */
+    double resid;        /* final ||P^-1 (b - A x)|| / ||P^-1 b||, recomputed in FP64 */
+    double true_resid;   /* final ||b - A x|| / ||b||, recomputed in FP64 */
+} vie_solve_info;
+
+/*
+ * vie_setup -- build a handle for one grid, frequency and dielectric map.
+ * Computes on the GPU, in FP64: the Galerkin entries of N for every offset
+ * (Section III-C, Eq. 25, Eq. 34, Eq. 42-43), their circulant embedding and 3-D
+ * FFT (Section IV-A), stored once in FP64 and once in FP32; and the per-voxel
+ * material coefficients eps, chi = eps - 1, tau = chi/eps (Eq. 7, Eq. 17, Eq. 29).
+ *   grid          : voxel counts and sizes (see above)
+ *   freq_hz       : frequency f > 0; omega = 2 pi f, k0 = omega / c0
+ *   eps_real      : double[nz][ny][nx], eps' >= 1 (1 in air), host or device
+ *   sigma         : double[nz][ny][nx], conductivity in S/m >= 0, host or device
+ *   flags         : 0 (reserved)
+ *   out           : receives the handle; release with vie_destroy
+ * Synchronous.  Returns VIE_EINVAL on bad sizes/NaN, VIE_ENOMEM, VIE_EDEVICE.
+ */
+int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma, int flags,
+              vie_handle** out);
+
+/* Release every device buffer of the handle.  NULL is ignored. */
+void vie_destroy(vie_handle* h);
+
+/*
+ * vie_matvec -- apply the operator `op` (VIE_OP_*) to nrhs vectors at once by the
+ * FFT-accelerated circulant product (Section IV-A): zero-pad to the embedding
+ * grid, 3-D FFT, 12x12 block product with the Green tensor at every frequency
+ * point, inverse FFT, crop, then the per-voxel material and Gram terms.
+ *   nrhs      : number of vectors >= 1
+ *   x, y      : [nrhs][12][nz][ny][nx] complex, element type by `precision`
+ *               (VIE_FP64: double pairs, VIE_FP32: float pairs); x and y must not overlap
+ *   precision : VIE_FP64 or VIE_FP32
+ *   op        : VIE_OP_A, VIE_OP_PA or VIE_OP_NSCAT
+ */
+int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream);
+
+/*
+ * vie_rhs_planewave -- tested incident field of e_inc = pol exp(-i k0 dir.r)
+ * (Eq. 27, Eq. 30; Section V-A uses pol = x, dir = z) in closed form, and the
+ * right-hand side b = c_e chi e_inc (Eq. 31).
+ *   pol, dir : 3-vectors (dir normalised by the library; pol used as given, V/m)
+ *   e_inc    : [12][nz][ny][nx] C128 output or NULL
+ *   b        : [12][nz][ny][nx] C128 output or NULL
+ */
+int vie_rhs_planewave(vie_handle* h, const double pol[3], const double dir[3], void* e_inc, void* b, void* stream);
+
+/*
+ * vie_rhs_dipoles -- tested incident fields of nrhs Hertzian dipoles, one per
+ * right-hand side: e_inc = (1/c_e)(k0^2 g p + grad(p . grad g)) (Eq. 13 with a
+ * point current p = I l, g of Eq. 10), tested with a 6x6x6 Gauss-Legendre rule
+ * per voxel, and b = c_e chi e_inc (Eq. 31).
+ *   pos : double[nrhs][3] positions (m);  mom : double[nrhs][3] moments (A m); host memory
+ *   e_inc, b : [nrhs][12][nz][ny][nx] C128 outputs, either may be NULL
+ */
+int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mom, void* e_inc, void* b,
+                    void* stream);
+
+/*
+ * vie_solve -- solve A x = b for nrhs right-hand sides with left-preconditioned
+ * restarted GMRES, P = M_eps G (Section IV-B, Section V: GMRES(restart), at most
+ * maxit restart cycles), stopping when ||P^-1 (b - A x)|| / ||P^-1 b|| <= tol.
+ *   b       : [nrhs][12][nz][ny][nx] C128
+ *   x       : [nrhs][12][nz][ny][nx] C128; on entry the initial guess when
+ *             (flags & 1), else ignored (zero guess); on exit the solution
+ *   restart : Krylov dimension m >= 1;  maxit: cycles (plain) or refinement sweeps x cycles
+ *   mode    : VIE_SOLVE_FP64 (plain FP64) or VIE_SOLVE_FP32_REFINE (FP32 GMRES with
+ *             FP64 iterative refinement; inner products, Hessenberg and Givens
+ *             rotations in FP64, Krylov basis stored in FP32)
+ *   info    : vie_solve_info[nrhs] host array or NULL
+ * Synchronous.  Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
+ */
+int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int mode,
+              int flags, vie_solve_info* info, void* stream);
+
+/*
+ * vie_fields -- post-processing (Section IV-C): tested total field
+ * e~ = e_inc + (1/c_e)(N - G) x, PWL field coefficients e = G^-1 e~, and the
+ * absorbed power (Eq. 44) P_abs = 1/2 Re{x^* (c_e M_chi)^-1 G x}, as a per-voxel
+ * density p_abs (W/m^3, zero in air) and its total, all in FP64.
+ *   x, e_inc : [nrhs][12][nz][ny][nx] C128
+ *   e_coeff  : [nrhs][12][nz][ny][nx] C128 output or NULL
+ *   p_abs    : double[nrhs][nz][ny][nx] output or NULL
+ *   P_abs    : double[nrhs] host output or NULL
+ * Synchronous when P_abs is requested.
+ */
+int vie_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, void* e_coeff, double* p_abs,
+               double* P_abs, void* stream);
+
+/*
+ * vie_green_toeplitz -- copy the 60 unique Toeplitz tensors of N - G computed by
+ * vie_setup (the Gram term at offset 0 excluded) for offsets d in [0,nx)x[0,ny)x[0,nz):
+ * out[t][dz][dy][dx] C128 with t = 10 * pq + ll, pq indexing the unordered
+ * vector pair (xx,xy,xz,yy,yz,zz) and ll the ordered scalar pair l <= l'
+ * ((1,1),(1,2),(1,3),(1,4),(2,2),(2,3),(2,4),(3,3),(3,4),(4,4)) (Section III-C: 6 x 10 = 60).
+ * Entries for negative offsets follow from the reflection parities.  Synchronous.
+ */
+int vie_green_toeplitz(vie_handle* h, void* out);
+
+/* Sizes used by the handle: FFT lengths per axis and bytes of device memory held. */
+int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes);
+
+/*
+ * Launch accounting.  The library counts every kernel it launches, per kernel
+ * name; with timing enabled it also records a CUDA event pair on the launch
+ * stream around each launch and accumulates the device time per name.
+ * vie_stats_reset clears the counters and switches timing on (1) or off (0).
+ * vie_stats_read synchronises on the recorded events and returns up to
+ * max_entries rows: names (max_entries x 48 chars, NUL-terminated), launch
+ * counts, milliseconds (0 without timing); *n_entries rows written and
+ * *total_launches over all names.  Any output pointer may be NULL.  Host memory.
+ */
+int vie_stats_reset(int enable_timing);
+int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, int* n_entries,
+                   long long* total_launches);
+
+/* Static description of an error code. */
+const char* vie_strerror(int code);
+
+/* Detail of the most recent error on the calling thread ("" if none). */
+const char* vie_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIE_H */

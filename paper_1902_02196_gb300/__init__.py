@@ -1,0 +1,234 @@
+"""Python binding of libvie (include/vie.h): the FFT-accelerated PWL current-based VIE on GB300.
+
+Argument marshalling only: every function here forwards to the C ABI entry point
+of the same name; all arithmetic runs in the library's CUDA kernels.  Arrays may
+be torch tensors (CUDA or CPU) or NumPy arrays (host); complex arrays use
+complex128 (FP64 entry points) or complex64 (FP32 matvec) with the layout
+[nrhs][12][nz][ny][nx].  The library is built in place by `build()`; importing
+works without it, but every call raises if libvie.so is missing - there is no
+fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvie.so")
+
+VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_EDEVICE, VIE_ETIMEOUT, VIE_NOT_CONVERGED = 0, -1, -2, -3, -4, 1
+VIE_FP64, VIE_FP32 = 0, 1
+VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT = 0, 1, 2
+VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
+
+EXPORTS = (
+    "vie_setup", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
+    "vie_fields", "vie_green_toeplitz", "vie_info", "vie_strerror", "vie_last_error",
+    "vie_stats_reset", "vie_stats_read",
+)
+
+
+class vie_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+class vie_solve_info(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
+                ("fp32_matvecs", ctypes.c_int), ("refinements", ctypes.c_int), ("resid", ctypes.c_double),
+                ("true_resid", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VieError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        lib = _lib()
+        detail = lib.vie_last_error().decode()
+        super().__init__(f"{where}: {lib.vie_strerror(code).decode()} ({code}) {detail}")
+
+
+_LIB = None
+
+
+def build(verbose=False):
+    """Compile libvie.so for sm_103a in place (nvcc) and return its path."""
+    from . import _builder as _b
+
+    return _b.build(verbose=verbose)
+
+
+def _lib():
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; call paper_1902_02196_gb300.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.vie_setup.argtypes = [ctypes.POINTER(vie_grid), D, P, P, I, ctypes.POINTER(P)]
+    lib.vie_destroy.argtypes = [P]
+    lib.vie_destroy.restype = None
+    lib.vie_matvec.argtypes = [P, I, P, P, I, I, P]
+    lib.vie_rhs_planewave.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D), P, P, P]
+    lib.vie_rhs_dipoles.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D), P, P, P]
+    lib.vie_solve.argtypes = [P, I, P, P, D, I, I, I, I, ctypes.POINTER(vie_solve_info), P]
+    lib.vie_fields.argtypes = [P, I, P, P, P, P, ctypes.POINTER(D), P]
+    lib.vie_green_toeplitz.argtypes = [P, P]
+    lib.vie_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(S)]
+    lib.vie_strerror.argtypes = [I]
+    lib.vie_strerror.restype = ctypes.c_char_p
+    lib.vie_stats_reset.argtypes = [I]
+    lib.vie_stats_read.argtypes = [I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]
+    lib.vie_last_error.argtypes = []
+    lib.vie_last_error.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw data pointer of a torch tensor or NumPy array (must be contiguous); None -> NULL."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def _nrhs(a, nv):
+    n = 1
+    for d in a.shape:
+        n *= int(d)
+    if n % (12 * nv):
+        raise ValueError("array size is not a multiple of 12 * N_V")
+    return n // (12 * nv)
+
+
+def _check(rc, where):
+    if rc < 0:
+        raise VieError(rc, where)
+    return rc
+
+
+class Handle:
+    """Owns a vie_handle (one grid, frequency and material map)."""
+
+    def __init__(self, ptr, grid, freq):
+        self.ptr = ptr
+        self.grid = grid
+        self.freq = freq
+        self.nv = grid[0] * grid[1] * grid[2]
+
+    def close(self):
+        if self.ptr:
+            vie_destroy(self)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vie_setup(grid, freq_hz, eps_real, sigma, flags=0):
+    """grid = (nx, ny, nz, dx, dy, dz); eps_real, sigma: float64 (nz, ny, nx) maps (host or device)."""
+    lib = _lib()
+    g = vie_grid(*[int(v) for v in grid[:3]], *[float(v) for v in grid[3:]])
+    out = ctypes.c_void_p()
+    _check(lib.vie_setup(ctypes.byref(g), float(freq_hz), _ptr(eps_real), _ptr(sigma), int(flags), ctypes.byref(out)),
+           "vie_setup")
+    return Handle(out.value, (g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), freq_hz)
+
+
+def vie_destroy(h):
+    _lib().vie_destroy(h.ptr)
+
+
+def vie_matvec(h, x, y, precision=VIE_FP64, op=VIE_OP_A, stream=None):
+    return _check(_lib().vie_matvec(h.ptr, _nrhs(x, h.nv), _ptr(x), _ptr(y), int(precision), int(op), _stream(stream)),
+                  "vie_matvec")
+
+
+def vie_rhs_planewave(h, pol, direction, e_inc=None, b=None, stream=None):
+    D3 = ctypes.c_double * 3
+    return _check(_lib().vie_rhs_planewave(h.ptr, D3(*pol), D3(*direction), _ptr(e_inc), _ptr(b), _stream(stream)),
+                  "vie_rhs_planewave")
+
+
+def vie_rhs_dipoles(h, pos, mom, e_inc=None, b=None, stream=None):
+    import numpy as np
+
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    mom = np.ascontiguousarray(mom, dtype=np.float64).reshape(-1, 3)
+    Dp = ctypes.POINTER(ctypes.c_double)
+    return _check(_lib().vie_rhs_dipoles(h.ptr, pos.shape[0], pos.ctypes.data_as(Dp), mom.ctypes.data_as(Dp),
+                                         _ptr(e_inc), _ptr(b), _stream(stream)), "vie_rhs_dipoles")
+
+
+def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFINE, guess=False, stream=None):
+    """Returns (rc, [info dict per right-hand side]); rc is VIE_OK or VIE_NOT_CONVERGED."""
+    n = _nrhs(b, h.nv)
+    info = (vie_solve_info * n)()
+    rc = _check(_lib().vie_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
+                                 1 if guess else 0, info, _stream(stream)), "vie_solve")
+    return rc, [i.as_dict() for i in info]
+
+
+def vie_fields(h, x, e_inc, e_coeff=None, p_abs=None, stream=None):
+    """Returns the absorbed power P_abs (W) per right-hand side as a list."""
+    n = _nrhs(x, h.nv)
+    P = (ctypes.c_double * n)()
+    _check(_lib().vie_fields(h.ptr, n, _ptr(x), _ptr(e_inc), _ptr(e_coeff), _ptr(p_abs), P, _stream(stream)),
+           "vie_fields")
+    return list(P)
+
+
+def vie_green_toeplitz(h, out):
+    return _check(_lib().vie_green_toeplitz(h.ptr, _ptr(out)), "vie_green_toeplitz")
+
+
+def vie_info(h):
+    L = (ctypes.c_int * 3)()
+    nb = ctypes.c_size_t()
+    _check(_lib().vie_info(h.ptr, L, ctypes.byref(nb)), "vie_info")
+    return tuple(L), nb.value
+
+
+def vie_strerror(code):
+    return _lib().vie_strerror(int(code)).decode()
+
+
+def vie_stats_reset(timing=False):
+    return _check(_lib().vie_stats_reset(1 if timing else 0), "vie_stats_reset")
+
+
+def vie_stats_read(max_entries=256):
+    """Returns (total_launches, {kernel name: (launches, device ms)})."""
+    names = ctypes.create_string_buffer(48 * max_entries)
+    launches = (ctypes.c_longlong * max_entries)()
+    ms = (ctypes.c_double * max_entries)()
+    n = ctypes.c_int()
+    tot = ctypes.c_longlong()
+    _check(_lib().vie_stats_read(max_entries, ctypes.addressof(names), ctypes.addressof(launches),
+                                 ctypes.addressof(ms), ctypes.byref(n), ctypes.byref(tot)), "vie_stats_read")
+    out = {}
+    for i in range(n.value):
+        nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (launches[i], ms[i])
+    return tot.value, out

@@ -1,0 +1,358 @@
+// C ABI entry points (include/vie.h): argument checks, host-buffer staging, handle lifetime.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int next_pow2(int v) {
+    int L = 2;
+    while (L < v) L *= 2;
+    return L;
+}
+
+cudaStream_t pick(vie_handle* h, void* s) { return s ? reinterpret_cast<cudaStream_t>(s) : h->stream; }
+
+size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Two-phase staging: declare every buffer, reserve once, then bind.
+struct Stager {
+    vie_handle* h;
+    cudaStream_t st;
+    struct Item {
+        const void* user;
+        size_t bytes;
+        bool is_out;
+        bool host;
+        size_t off;
+    };
+    std::vector<Item> items;
+    bool any_host = false;
+    int add(const void* p, size_t bytes, bool is_out) {
+        Item it{p, bytes, is_out, p != nullptr && !is_device_ptr(p), 0};
+        if (it.host) any_host = true;
+        items.push_back(it);
+        return (int)items.size() - 1;
+    }
+    int bind(std::vector<void*>& dev) {
+        size_t off = 0;
+        for (auto& it : items)
+            if (it.host) {
+                it.off = off;
+                off += a256(it.bytes);
+            }
+        if (off) VIE_TRY(ws_reserve(h, h->stage_ws, off));
+        dev.resize(items.size());
+        for (size_t i = 0; i < items.size(); ++i) {
+            auto& it = items[i];
+            if (!it.user) {
+                dev[i] = nullptr;
+            } else if (it.host) {
+                dev[i] = static_cast<char*>(h->stage_ws.ptr) + it.off;
+                if (!it.is_out) VIE_CUDA(cudaMemcpyAsync(dev[i], it.user, it.bytes, cudaMemcpyHostToDevice, st));
+            } else {
+                dev[i] = const_cast<void*>(it.user);
+            }
+        }
+        return VIE_OK;
+    }
+    int finish(const std::vector<void*>& dev) {
+        for (size_t i = 0; i < items.size(); ++i) {
+            auto& it = items[i];
+            if (it.user && it.host && it.is_out)
+                VIE_CUDA(cudaMemcpyAsync(const_cast<void*>(it.user), dev[i], it.bytes, cudaMemcpyDeviceToHost, st));
+        }
+        if (any_host) VIE_CUDA(cudaStreamSynchronize(st));
+        return VIE_OK;
+    }
+};
+
+void release(vie_handle* h) {
+    if (!h) return;
+    cudaFree(h->eps64);
+    cudaFree(h->chi64);
+    cudaFree(h->tau64);
+    cudaFree(h->ieps64);
+    cudaFree(h->chi32);
+    cudaFree(h->tau32);
+    cudaFree(h->ieps32);
+    cudaFree(h->green64);
+    cudaFree(h->green32);
+    cudaFree(h->tw64);
+    cudaFree(h->tw32);
+    cudaFree(h->toeplitz);
+    cudaFree(h->fft_ws.ptr);
+    cudaFree(h->stage_ws.ptr);
+    cudaFree(h->solve_ws.ptr);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+#define REQUIRE(cond, msg)           \
+    do {                             \
+        if (!(cond)) {               \
+            set_error(msg);          \
+            return VIE_EINVAL;       \
+        }                            \
+    } while (0)
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int ws_reserve(vie_handle* h, Workspace& w, size_t bytes) {
+    if (w.bytes >= bytes) return VIE_OK;
+    if (w.ptr) {
+        VIE_CUDA(cudaFree(w.ptr));
+        h->bytes_held -= w.bytes;
+        w.ptr = nullptr;
+        w.bytes = 0;
+    }
+    if (cudaMalloc(&w.ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        w.ptr = nullptr;
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+        return VIE_ENOMEM;
+    }
+    w.bytes = bytes;
+    h->bytes_held += bytes;
+    return VIE_OK;
+}
+
+extern "C" {
+
+const char* vie_strerror(int code) {
+    switch (code) {
+        case VIE_OK: return "success";
+        case VIE_EINVAL: return "invalid argument";
+        case VIE_ENOMEM: return "out of memory";
+        case VIE_EDEVICE: return "CUDA device error";
+        case VIE_ETIMEOUT: return "timed out";
+        case VIE_NOT_CONVERGED: return "solver did not reach the tolerance";
+    }
+    return "unknown error";
+}
+
+const char* vie_last_error(void) { return g_last_error.c_str(); }
+
+int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma, int flags,
+              vie_handle** out) {
+    g_last_error.clear();
+    REQUIRE(out, "out is NULL");
+    *out = nullptr;
+    REQUIRE(grid && eps_real && sigma, "NULL argument");
+    REQUIRE(grid->nx >= 1 && grid->ny >= 1 && grid->nz >= 1, "grid sizes must be >= 1");
+    REQUIRE(grid->nx <= 512 && grid->ny <= 512 && grid->nz <= 512, "grid sizes above 512 are not supported");
+    REQUIRE(std::isfinite(grid->dx) && std::isfinite(grid->dy) && std::isfinite(grid->dz) && grid->dx > 0 &&
+                grid->dy > 0 && grid->dz > 0,
+            "voxel sizes must be finite and positive");
+    REQUIRE(std::isfinite(freq_hz) && freq_hz > 0, "frequency must be finite and positive");
+    REQUIRE(flags == 0, "flags must be 0");
+    vie_handle* h = new (std::nothrow) vie_handle();
+    if (!h) {
+        set_error("host allocation failed");
+        return VIE_ENOMEM;
+    }
+    std::memset(static_cast<void*>(h), 0, sizeof(vie_handle));
+    h->nx = grid->nx, h->ny = grid->ny, h->nz = grid->nz;
+    h->dx = grid->dx, h->dy = grid->dy, h->dz = grid->dz;
+    h->freq = freq_hz;
+    h->omega = 2.0 * VIE_PI * freq_hz;
+    h->k0 = h->omega / VIE_C0;
+    const int n[3] = {h->nx, h->ny, h->nz};
+    for (int i = 0; i < 3; ++i) {
+        h->L[i] = next_pow2(2 * n[i] - 1);
+        h->O[i] = h->L[i] / 2 + 1;
+    }
+    h->nv = (size_t)h->nx * h->ny * h->nz;
+    int rc = VIE_OK;
+    auto fail = [&](int code) {
+        release(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess || cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("no usable CUDA device");
+        return fail(VIE_EDEVICE);
+    }
+    // validate the material maps on the host
+    std::vector<double> er(h->nv), sg(h->nv);
+    const bool dev_in = is_device_ptr(eps_real);
+    if (dev_in) {
+        if (cudaMemcpy(er.data(), eps_real, sizeof(double) * h->nv, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(sg.data(), sigma, sizeof(double) * h->nv, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("cannot read material maps");
+            return fail(VIE_EINVAL);
+        }
+    } else {
+        std::memcpy(er.data(), eps_real, sizeof(double) * h->nv);
+        std::memcpy(sg.data(), sigma, sizeof(double) * h->nv);
+    }
+    for (size_t m = 0; m < h->nv; ++m)
+        if (!std::isfinite(er[m]) || !std::isfinite(sg[m]) || er[m] <= 0.0 || sg[m] < 0.0) {
+            set_error("material map entry " + std::to_string(m) + " is not finite or out of range");
+            return fail(VIE_EINVAL);
+        }
+    const size_t nv = h->nv;
+    if (cudaMalloc(&h->eps64, sizeof(double2) * nv) != cudaSuccess ||
+        cudaMalloc(&h->chi64, sizeof(double2) * nv) != cudaSuccess ||
+        cudaMalloc(&h->tau64, sizeof(double2) * nv) != cudaSuccess ||
+        cudaMalloc(&h->ieps64, sizeof(double2) * nv) != cudaSuccess ||
+        cudaMalloc(&h->chi32, sizeof(float2) * nv) != cudaSuccess ||
+        cudaMalloc(&h->tau32, sizeof(float2) * nv) != cudaSuccess ||
+        cudaMalloc(&h->ieps32, sizeof(float2) * nv) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("material allocation failed");
+        return fail(VIE_ENOMEM);
+    }
+    h->bytes_held += nv * (4 * sizeof(double2) + 3 * sizeof(float2));
+    double* dmat = nullptr;
+    if (cudaMalloc(&dmat, sizeof(double) * 2 * nv) != cudaSuccess) {
+        set_error("material staging failed");
+        return fail(VIE_ENOMEM);
+    }
+    cudaMemcpy(dmat, er.data(), sizeof(double) * nv, cudaMemcpyHostToDevice);
+    cudaMemcpy(dmat + nv, sg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice);
+    rc = materials_device(h, dmat, dmat + nv, h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(dmat);
+    if (rc < 0) return fail(rc);
+    if ((rc = twiddle_setup(h)) < 0) return fail(rc);
+    if ((rc = green_setup(h)) < 0) return fail(rc);
+    *out = h;
+    return VIE_OK;
+}
+
+void vie_destroy(vie_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+}
+
+int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes) {
+    REQUIRE(h, "NULL handle");
+    if (fft_len_xyz)
+        for (int i = 0; i < 3; ++i) fft_len_xyz[i] = h->L[i];
+    if (device_bytes) *device_bytes = h->bytes_held;
+    return VIE_OK;
+}
+
+int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && x && y, "NULL argument");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    REQUIRE(precision == VIE_FP64 || precision == VIE_FP32, "unknown precision");
+    REQUIRE(op == VIE_OP_A || op == VIE_OP_PA || op == VIE_OP_NSCAT, "unknown operator");
+    REQUIRE(x != y, "x and y must not overlap");
+    const size_t bytes = (size_t)nrhs * 12 * h->nv * (precision == VIE_FP64 ? sizeof(double2) : sizeof(float2));
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(x, bytes, false);
+    sg.add(y, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(matvec_device(h, nrhs, d[0], d[1], precision, op, st));
+    return sg.finish(d);
+}
+
+int vie_rhs_planewave(vie_handle* h, const double pol[3], const double dir[3], void* e_inc, void* b, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && pol && dir, "NULL argument");
+    for (int i = 0; i < 3; ++i) REQUIRE(std::isfinite(pol[i]) && std::isfinite(dir[i]), "non-finite source");
+    const size_t bytes = 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(e_inc, bytes, true);
+    sg.add(b, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(rhs_planewave_device(h, pol, dir, (double2*)d[0], (double2*)d[1], st));
+    return sg.finish(d);
+}
+
+int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mom, void* e_inc, void* b,
+                    void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && pos && mom, "NULL argument");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    for (int i = 0; i < 3 * nrhs; ++i) REQUIRE(std::isfinite(pos[i]) && std::isfinite(mom[i]), "non-finite source");
+    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(e_inc, bytes, true);
+    sg.add(b, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(rhs_dipoles_device(h, nrhs, pos, mom, (double2*)d[0], (double2*)d[1], st));
+    return sg.finish(d);
+}
+
+int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int mode,
+              int flags, vie_solve_info* info, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && b && x, "NULL argument");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    REQUIRE(std::isfinite(tol) && tol > 0 && tol < 1, "tol must be in (0, 1)");
+    REQUIRE(restart >= 1 && restart <= 1000, "restart must be in [1, 1000]");
+    REQUIRE(maxit >= 1, "maxit must be >= 1");
+    REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE, "unknown mode");
+    REQUIRE((flags & ~1) == 0, "unknown flags");
+    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(b, bytes, false);
+    sg.add(x, bytes, (flags & 1) ? false : true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    sg.items[1].is_out = true;  // x is returned even when it carried the initial guess
+    int rc = solve_device(h, nrhs, (const double2*)d[0], (double2*)d[1], tol, restart, maxit, mode, flags & 1, info, st);
+    if (rc < 0) return rc;
+    VIE_TRY(sg.finish(d));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int vie_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, void* e_coeff, double* p_abs,
+               double* P_abs, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && x && e_inc, "NULL argument");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(x, bytes, false);
+    sg.add(e_inc, bytes, false);
+    sg.add(e_coeff, bytes, true);
+    sg.add(p_abs, (size_t)nrhs * h->nv * sizeof(double), true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(fields_device(h, nrhs, (const double2*)d[0], (const double2*)d[1], (double2*)d[2], (double*)d[3], P_abs,
+                          st));
+    return sg.finish(d);
+}
+
+int vie_green_toeplitz(vie_handle* h, void* out) {
+    g_last_error.clear();
+    REQUIRE(h && out, "NULL argument");
+    const size_t bytes = 60 * h->nv * sizeof(double2);
+    VIE_CUDA(cudaStreamSynchronize(h->stream));
+    VIE_CUDA(cudaMemcpy(out, h->toeplitz, bytes, cudaMemcpyDefault));
+    return VIE_OK;
+}
+
+}  // extern "C"

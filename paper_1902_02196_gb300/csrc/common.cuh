@@ -1,0 +1,186 @@
+// Internal declarations shared by the translation units of libvie.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/vie.h"
+
+// ---------------------------------------------------------------------------
+// Complex helpers on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CT;
+template <>
+struct CT<float> {
+    using C = float2;
+};
+template <>
+struct CT<double> {
+    using C = double2;
+};
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename C>
+__host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C cmul(C a, C b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C>
+__host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C>
+__host__ __device__ __forceinline__ C cneg(C a) { return mk(-a.x, -a.y); }
+// multiply by -i (dir = -1) or +i (dir = +1)
+template <typename C>
+__host__ __device__ __forceinline__ C cmul_i(C a, int dir) { return dir < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x); }
+// acc += a * b
+template <typename C>
+__host__ __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float2 cfma_f(float2 acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// The 60 unique tensors of N (Section III-C): t = 10 * pq + ll.
+//   pq : unordered vector pair (xx, xy, xz, yy, yz, zz)
+//   ll : ordered scalar pair l <= l' ((1,1),(1,2),(1,3),(1,4),(2,2),(2,3),(2,4),(3,3),(3,4),(4,4))
+// Entry (alpha = 4p + l - 1, beta = 4q + l' - 1) of the 12 x 12 block equals
+// sgn * U_t with, for l > l', the swap relation N^{pl,ql'} = (-1)^{[l>1]+[l'>1]} N^{pl',ql}
+// (reciprocity combined with the point-inversion parity of the PWL functions).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pq_index(int p, int q) {
+    return p > q ? pq_index(q, p) : (p == 0 ? q : (p == 1 ? 2 + q : 5));
+}
+__host__ __device__ constexpr int ll_index(int l, int lp) {  // 1-based, l <= lp
+    return l > lp ? ll_index(lp, l) : (l == 1 ? lp - 1 : (l == 2 ? 2 + lp : (l == 3 ? 4 + lp : 9)));
+}
+__host__ __device__ constexpr int tensor_of(int a, int b) {
+    return 10 * pq_index(a / 4, b / 4) + ll_index(a % 4 + 1, b % 4 + 1);
+}
+__host__ __device__ constexpr int sign_of(int a, int b) {
+    return ((a % 4) > (b % 4)) ? ((((a % 4) > 0) + ((b % 4) > 0)) % 2 ? -1 : 1) : 1;
+}
+// reflection parity of component alpha under x_i -> -x_i: -1 if p == i, times -1 if N^l is linear along i
+__host__ __device__ constexpr int parity_of(int a, int i) {
+    return ((a / 4 == i) ? -1 : 1) * ((a % 4 == i + 1) ? -1 : 1);
+}
+// bit mask over the 12 components of parity -1 under reflection of axis i
+__host__ __device__ constexpr unsigned flip_mask(int i) {
+    unsigned m = 0;
+    for (int a = 0; a < 12; ++a)
+        if (parity_of(a, i) < 0) m |= 1u << a;
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct vie_handle {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double freq, omega, k0;
+    int L[3];   // FFT lengths (x, y, z), powers of two >= 2N - 1
+    int O[3];   // octant sizes L/2 + 1
+    size_t nv;  // nx*ny*nz
+    cudaStream_t stream;
+    int device;
+    // per-voxel coefficients (complex): eps, chi, tau, 1/eps; double and float copies
+    double2 *eps64, *chi64, *tau64, *ieps64;
+    float2 *chi32, *tau32, *ieps32;
+    // FFT'd circulant Green tensors (of N - G), octant k_i in [0, L_i/2], pre-scaled by 1/(Lx Ly Lz):
+    // layout [60][Oz][Oy][Ox]
+    double2* green64;
+    float2* green32;
+    // twiddle tables exp(-2 pi i m / L) for L = 2^k, k = 1..11, concatenated at offset L
+    double2* tw64;
+    float2* tw32;
+    // scratch
+    Workspace fft_ws;    // matvec spectrum buffers
+    Workspace stage_ws;  // host-buffer staging
+    Workspace solve_ws;  // solver vectors
+    double2* toeplitz;   // [60][nz][ny][nx] Toeplitz tensors of N - G for offsets d >= 0
+    size_t bytes_held;
+};
+
+// ---------------------------------------------------------------------------
+// Error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+#define VIE_CUDA(call)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_) + " at " + __FILE__ + ":" +  \
+                      std::to_string(__LINE__));                                                       \
+            return e_ == cudaErrorMemoryAllocation ? VIE_ENOMEM : VIE_EDEVICE;                         \
+        }                                                                                              \
+    } while (0)
+#define VIE_CHECK_LAUNCH() VIE_CUDA(cudaGetLastError())
+#define VIE_TRY(expr)             \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ < 0) return rc_;  \
+    } while (0)
+
+int ws_reserve(vie_handle* h, Workspace& w, size_t bytes);
+
+// ---------------------------------------------------------------------------
+// Launch accounting (stats.cu): every kernel launch of the library is counted per
+// kernel name; when timing is enabled, CUDA events recorded on the launch stream
+// around each launch give its device duration.
+// ---------------------------------------------------------------------------
+struct LaunchScope {
+    LaunchScope(const char* name, cudaStream_t s);
+    ~LaunchScope();
+    const char* name;
+    cudaStream_t stream;
+    bool timed;
+    cudaEvent_t ev0, ev1;
+};
+#define VIE_KLAUNCH(name, stream, ...) \
+    do {                                \
+        LaunchScope ls_(name, stream);  \
+        __VA_ARGS__;                    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Entry points between translation units
+// ---------------------------------------------------------------------------
+int green_setup(vie_handle* h);                 // green.cu
+int twiddle_setup(vie_handle* h);               // matvec.cu
+int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
+size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);
+// full 3-D FFT of `batch` complex double volumes [batch][Lz][Ly][Lx] in place (forward, unscaled)
+int fft3d_inplace64(vie_handle* h, double2* data, int batch, cudaStream_t s);
+int solve_device(vie_handle* h, int nrhs, const double2* b, double2* x, double tol, int restart, int maxit,
+                 int mode, int use_guess, vie_solve_info* info, cudaStream_t s);
+int rhs_planewave_device(vie_handle* h, const double pol[3], const double dir[3], double2* e, double2* b,
+                         cudaStream_t s);
+int rhs_dipoles_device(vie_handle* h, int nrhs, const double* pos, const double* mom, double2* e, double2* b,
+                       cudaStream_t s);
+int materials_device(vie_handle* h, const double* eps_real, const double* sigma, cudaStream_t s);
+int fields_device(vie_handle* h, int nrhs, const double2* x, const double2* e_inc, double2* e_out, double* p_abs,
+                  double* P_abs_host, cudaStream_t s);
+
+// physical constants (SI)
+constexpr double VIE_C0 = 299792458.0;
+constexpr double VIE_EPS0 = 8.8541878128e-12;
+constexpr double VIE_PI = 3.14159265358979323846;

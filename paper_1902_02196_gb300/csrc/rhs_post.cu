@@ -1,0 +1,325 @@
+// Material coefficients, tested incident fields / right-hand sides (Eq. 27-31) and
+// post-processing: fields and absorbed power (Section IV-C, Eq. 44).
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+__constant__ double c_g6x[6];
+__constant__ double c_g6w[6];
+bool g_rule6_ready = false;
+
+// Gauss-Legendre 6-point rule on [0,1] (Newton on the Legendre recurrence).
+void rule6(double* x, double* w) {
+    const int n = 6;
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(VIE_PI * (i + 0.75) / (n + 0.5)), p0 = 1, p1 = z, dp = 1;
+        for (int it = 0; it < 100; ++it) {
+            p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1, p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1, p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// eps = eps' - i sigma / (omega eps0), chi = eps - 1, tau = chi / eps, 1/eps  (Eq. 2, 7, 17)
+__global__ void materials_kernel(const double* __restrict__ er, const double* __restrict__ sg, long long nv, double omega,
+                                 double2* eps, double2* chi, double2* tau, double2* ieps, float2* chi32, float2* tau32,
+                                 float2* ieps32) {
+    long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nv) return;
+    const double2 e = make_double2(er[m], -sg[m] / (omega * VIE_EPS0));
+    const double2 c = make_double2(e.x - 1.0, e.y);
+    const double2 ie = cdivd(make_double2(1.0, 0.0), e);
+    const double2 t = cmuld(c, ie);
+    eps[m] = e, chi[m] = c, tau[m] = t, ieps[m] = ie;
+    chi32[m] = make_float2((float)c.x, (float)c.y);
+    tau32[m] = make_float2((float)t.x, (float)t.y);
+    ieps32[m] = make_float2((float)ie.x, (float)ie.y);
+}
+
+// int_{-1/2}^{1/2} exp(-i k s) ds
+__device__ double2 vint0(double k) {
+    if (fabs(k) < 1e-8) return make_double2(1.0 - k * k / 24.0, 0.0);
+    return make_double2(2.0 * sin(0.5 * k) / k, 0.0);
+}
+// int_{-1/2}^{1/2} s exp(-i k s) ds: odd Taylor series below |k| = 1/4, closed form above
+__device__ double2 vint1(double k) {
+    if (fabs(k) < 0.25) {
+        // -i (k/12 - k^3/480 + k^5/53760 - k^7/11612160 + k^9/4087480320)
+        const double k2 = k * k;
+        double s = k * (1.0 / 12.0 - k2 * (1.0 / 480.0 - k2 * (1.0 / 53760.0 - k2 * (1.0 / 11612160.0 - k2 / 4087480320.0))));
+        return make_double2(0.0, -s);
+    }
+    double sn, cs;
+    sincos(0.5 * k, &sn, &cs);
+    return make_double2(0.0, cs / k - 2.0 * sn / (k * k));
+}
+
+struct GridD {
+    int nx, ny, nz;
+    double dx, dy, dz;
+};
+
+__device__ __forceinline__ void centre(const GridD& g, long long m, double* r) {
+    const int ix = (int)(m % g.nx), iy = (int)((m / g.nx) % g.ny), iz = (int)(m / ((long long)g.nx * g.ny));
+    r[0] = (ix + 0.5 - 0.5 * g.nx) * g.dx;
+    r[1] = (iy + 0.5 - 0.5 * g.ny) * g.dy;
+    r[2] = (iz + 0.5 - 0.5 * g.nz) * g.dz;
+}
+
+__global__ void planewave_kernel(GridD g, double k0, double px, double py, double pz, double ux, double uy, double uz,
+                                 double2 ce, const double2* __restrict__ chi, double2* e, double2* b) {
+    const long long nv = (long long)g.nx * g.ny * g.nz;
+    long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nv) return;
+    double r[3];
+    centre(g, m, r);
+    const double kv[3] = {k0 * ux, k0 * uy, k0 * uz};
+    const double d[3] = {g.dx, g.dy, g.dz};
+    double sn, cs;
+    sincos(-(kv[0] * r[0] + kv[1] * r[1] + kv[2] * r[2]), &sn, &cs);
+    const double2 phase = make_double2(cs, sn);
+    double2 f0[3], f1[3];
+    for (int i = 0; i < 3; ++i) {
+        f0[i] = vint0(kv[i] * d[i]);
+        f1[i] = vint1(kv[i] * d[i]);
+    }
+    const double dV = g.dx * g.dy * g.dz;
+    const double pol[3] = {px, py, pz};
+    const double2 cc = cmuld(ce, chi[m]);
+    for (int l = 0; l < 4; ++l) {
+        double2 fac = make_double2(dV, 0.0);
+        for (int i = 0; i < 3; ++i) fac = cmuld(fac, (l == i + 1) ? f1[i] : f0[i]);
+        fac = cmuld(fac, phase);
+        for (int p = 0; p < 3; ++p) {
+            const double2 v = make_double2(pol[p] * fac.x, pol[p] * fac.y);
+            const long long o = (long long)(4 * p + l) * nv + m;
+            if (e) e[o] = v;
+            if (b) b[o] = cmuld(cc, v);
+        }
+    }
+}
+
+// Tested fields of one z-, y- or x-moment dipole per right-hand side; thread per (voxel, rhs).
+__global__ void dipole_kernel(GridD g, double k0, double2 ice, int R, const double* __restrict__ pos,
+                              const double* __restrict__ mom, double2 ce, const double2* __restrict__ chi, double2* e,
+                              double2* b) {
+    const long long nv = (long long)g.nx * g.ny * g.nz;
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nv * R) return;
+    const long long m = gid % nv;
+    const int rr = (int)(gid / nv);
+    double rc[3];
+    centre(g, m, rc);
+    const double d[3] = {g.dx, g.dy, g.dz};
+    const double p[3] = {mom[3 * rr], mom[3 * rr + 1], mom[3 * rr + 2]};
+    double2 acc[12];
+    for (int i = 0; i < 12; ++i) acc[i] = make_double2(0, 0);
+    const double dV = g.dx * g.dy * g.dz;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j)
+            for (int k = 0; k < 6; ++k) {
+                const double s[3] = {c_g6x[i] - 0.5, c_g6x[j] - 0.5, c_g6x[k] - 0.5};
+                const double w = c_g6w[i] * c_g6w[j] * c_g6w[k] * dV;
+                double R3[3], Rn2 = 0;
+                for (int q = 0; q < 3; ++q) {
+                    R3[q] = rc[q] + d[q] * s[q] - pos[3 * rr + q];
+                    Rn2 += R3[q] * R3[q];
+                }
+                const double Rn = sqrt(Rn2);
+                double sn, cs;
+                sincos(k0 * Rn, &sn, &cs);
+                const double2 gg = make_double2(cs / (4.0 * VIE_PI * Rn), -sn / (4.0 * VIE_PI * Rn));
+                // grad grad g = g [(-1/R^2 - i k/R) I + (3/R^2 + 3 i k/R - k^2) Rh Rh]
+                const double2 a = cmuld(gg, make_double2(-1.0 / Rn2 + k0 * k0, -k0 / Rn));
+                const double2 c = cmuld(gg, make_double2(3.0 / Rn2 - k0 * k0, 3.0 * k0 / Rn));
+                const double pr = (p[0] * R3[0] + p[1] * R3[1] + p[2] * R3[2]) / Rn;
+                for (int q = 0; q < 3; ++q) {
+                    // E_q = (1/c_e) [ (k0^2 g + a_) p_q + c pr Rh_q ]  with a = a_ + k0^2 g folded above
+                    double2 Eq = make_double2(a.x * p[q] + c.x * pr * R3[q] / Rn, a.y * p[q] + c.y * pr * R3[q] / Rn);
+                    Eq = cmuld(Eq, ice);
+                    acc[4 * q].x += w * Eq.x;
+                    acc[4 * q].y += w * Eq.y;
+                    for (int l = 1; l < 4; ++l) {
+                        acc[4 * q + l].x += w * s[l - 1] * Eq.x;
+                        acc[4 * q + l].y += w * s[l - 1] * Eq.y;
+                    }
+                }
+            }
+    const double2 cc = cmuld(ce, chi[m]);
+    for (int a = 0; a < 12; ++a) {
+        const long long o = ((long long)rr * 12 + a) * nv + m;
+        if (e) e[o] = acc[a];
+        if (b) b[o] = cmuld(cc, acc[a]);
+    }
+}
+
+// e = (e_inc + Nx / c_e) / G ; p_abs(m) = 1/2 Re{sum_a |x_a|^2 G_a / (c_e chi)} / dV ; partial sums of p_abs dV
+__global__ void fields_kernel(long long nv, int R, const double2* __restrict__ x, const double2* __restrict__ einc,
+                              const double2* __restrict__ nx_, const double2* __restrict__ chi, double2 ice, double g1,
+                              double g234, double dV, double2* e, double* pabs, double* partial) {
+    __shared__ double sh[256];
+    const int rr = blockIdx.y;
+    long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double pv = 0.0;
+    if (m < nv) {
+        double q = 0.0;
+        for (int a = 0; a < 12; ++a) {
+            const long long o = ((long long)rr * 12 + a) * nv + m;
+            const double G = (a % 4 == 0) ? g1 : g234;
+            const double2 xv = x[o];
+            q += G * (xv.x * xv.x + xv.y * xv.y);
+            if (e) {
+                double2 t = cmuld(nx_[o], ice);
+                e[o] = make_double2((einc[o].x + t.x) / G, (einc[o].y + t.y) / G);
+            }
+        }
+        const double2 c = chi[m];
+        if (c.x != 0.0 || c.y != 0.0) {
+            // Re{ q / (c_e chi) } = q Re{ (1/c_e) / chi }
+            double2 f = cdivd(ice, c);
+            pv = 0.5 * q * f.x / dV;
+        }
+        if (pabs) pabs[(long long)rr * nv + m] = pv;
+    }
+    sh[threadIdx.x] = pv * dV;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(long long)rr * gridDim.x + blockIdx.x] = sh[0];
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk, double* out) {
+    __shared__ double sh[256];
+    const int rr = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 256) acc += partial[(long long)rr * nblk + i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[rr] = sh[0];
+}
+
+GridD gridd(const vie_handle* h) { return GridD{h->nx, h->ny, h->nz, h->dx, h->dy, h->dz}; }
+
+int ensure_rule6() {
+    if (g_rule6_ready) return VIE_OK;
+    double x[6], w[6];
+    rule6(x, w);
+    VIE_CUDA(cudaMemcpyToSymbol(c_g6x, x, sizeof(x)));
+    VIE_CUDA(cudaMemcpyToSymbol(c_g6w, w, sizeof(w)));
+    g_rule6_ready = true;
+    return VIE_OK;
+}
+
+}  // namespace
+
+int materials_device(vie_handle* h, const double* er, const double* sg, cudaStream_t s) {
+    const long long nv = (long long)h->nv;
+    VIE_KLAUNCH("materials", s, materials_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(er, sg, nv, h->omega, h->eps64, h->chi64, h->tau64,
+                                                                  h->ieps64, h->chi32, h->tau32, h->ieps32));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+int rhs_planewave_device(vie_handle* h, const double pol[3], const double dir[3], double2* e, double2* b,
+                         cudaStream_t s) {
+    double n = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(n > 0)) {
+        set_error("plane-wave direction must be non-zero");
+        return VIE_EINVAL;
+    }
+    const long long nv = (long long)h->nv;
+    const double2 ce = make_double2(0.0, h->omega * VIE_EPS0);
+    VIE_KLAUNCH("planewave", s, planewave_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(gridd(h), h->k0, pol[0], pol[1], pol[2], dir[0] / n,
+                                                                  dir[1] / n, dir[2] / n, ce, h->chi64, e, b));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+int rhs_dipoles_device(vie_handle* h, int R, const double* pos, const double* mom, double2* e, double2* b,
+                       cudaStream_t s) {
+    VIE_TRY(ensure_rule6());
+    const long long nv = (long long)h->nv;
+    double* dbuf = nullptr;
+    VIE_CUDA(cudaMalloc(&dbuf, sizeof(double) * 6 * R));
+    cudaMemcpyAsync(dbuf, pos, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dbuf + 3 * R, mom, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s);
+    const double2 ce = make_double2(0.0, h->omega * VIE_EPS0);
+    const double2 ice = make_double2(0.0, -1.0 / (h->omega * VIE_EPS0));
+    const long long th = nv * R;
+    VIE_KLAUNCH("dipole", s, dipole_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(gridd(h), h->k0, ice, R, dbuf, dbuf + 3 * R, ce,
+                                                               h->chi64, e, b));
+    cudaError_t err = cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(dbuf);
+    if (err != cudaSuccess) {
+        set_error(std::string("dipole kernel: ") + cudaGetErrorString(err));
+        return VIE_EDEVICE;
+    }
+    return VIE_OK;
+}
+
+int fields_device(vie_handle* h, int R, const double2* x, const double2* e_inc, double2* e_out, double* p_abs,
+                  double* P_abs_host, cudaStream_t s) {
+    const long long nv = (long long)h->nv;
+    const long long total = nv * 12 * R;
+    const int nblk = (int)((nv + 255) / 256);
+    double2* nx = nullptr;
+    double* part = nullptr;
+    double* tot = nullptr;
+    VIE_CUDA(cudaMalloc(&nx, sizeof(double2) * total));
+    if (cudaMalloc(&part, sizeof(double) * (size_t)nblk * R + sizeof(double) * R) != cudaSuccess) {
+        cudaFree(nx);
+        set_error("fields alloc");
+        return VIE_ENOMEM;
+    }
+    tot = part + (size_t)nblk * R;
+    int rc = VIE_OK;
+    if (e_out) rc = matvec_device(h, R, x, nx, VIE_FP64, VIE_OP_NSCAT, s);
+    if (rc == VIE_OK) {
+        const double dV = h->dx * h->dy * h->dz;
+        const double2 ice = make_double2(0.0, -1.0 / (h->omega * VIE_EPS0));
+        dim3 grid(nblk, R);
+        VIE_KLAUNCH("fields", s, fields_kernel<<<grid, 256, 0, s>>>(nv, R, x, e_inc, nx, h->chi64, ice, dV, dV / 12.0, dV, e_out, p_abs, part));
+        VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<R, 256, 0, s>>>(part, nblk, tot));
+        if (cudaGetLastError() != cudaSuccess) rc = VIE_EDEVICE;
+        if (rc == VIE_OK && P_abs_host) {
+            if (cudaMemcpyAsync(P_abs_host, tot, sizeof(double) * R, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                rc = VIE_EDEVICE;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = VIE_EDEVICE;
+    }
+    cudaFree(nx);
+    cudaFree(part);
+    if (rc != VIE_OK) set_error("fields kernels failed");
+    return rc;
+}

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated per result): FP64 Green tensors and FP64 matvec <= 1e-12 relative
+(2-norm over all entries); FP32 matvec <= 1e-5 relative; solutions <= 1e-6 relative
+in the current coefficients, fields and absorbed-power maps.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import green as OG  # noqa: E402
+from oracle import operator as O  # noqa: E402
+from oracle import post as OP  # noqa: E402
+from oracle import rhs as OR  # noqa: E402
+from oracle import solver as OS  # noqa: E402
+from synth import Grid, head_phantom, random_coefficients, random_tissue, ring_dipoles, sphere_phantom  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def vie():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1902_02196_gb300 as v
+
+    v.build()
+    return v
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def setup(vie, g, freq, eps, sig):
+    return vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), freq, eps, sig)
+
+
+def gpu_matvec(vie, h, x, precision, op):
+    dt = torch.complex128 if precision == vie.VIE_FP64 else torch.complex64
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)
+    yd = torch.empty_like(xd)
+    vie.vie_matvec(h, xd, yd, precision, op)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.complex128)
+
+
+PQ = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+LL = [(1, 1), (1, 2), (1, 3), (1, 4), (2, 2), (2, 3), (2, 4), (3, 3), (3, 4), (4, 4)]
+
+
+@pytest.mark.parametrize("shape,delta", [((5, 4, 6), (0.004, 0.005, 0.0045)), ((8, 8, 8), (0.003, 0.003, 0.003))])
+def test_green_toeplitz_parity(vie, shape, delta):
+    """The 60 unique Toeplitz tensors of N - G computed on the GPU vs all-144 oracle entries at every d >= 0."""
+    g = Grid(*shape, *delta)
+    eps = np.ones(g.shape)
+    sig = np.zeros(g.shape)
+    freq = 298e6
+    h = setup(vie, g, freq, eps, sig)
+    out = np.zeros((60,) + g.shape, dtype=np.complex128)
+    vie.vie_green_toeplitz(h, out)
+    h.close()
+    dz, dy, dx = np.meshgrid(np.arange(g.nz), np.arange(g.ny), np.arange(g.nx), indexing="ij")
+    D = np.stack([dx.ravel(), dy.ravel(), dz.ravel()], 1)
+    T = OG.n_entries(delta, O.k0_of(freq), D)
+    dV = np.prod(delta)
+    zero = np.all(D == 0, 1)
+    ref = np.zeros((60, D.shape[0]), dtype=complex)
+    for pqi, (p, q) in enumerate(PQ):
+        for lli, (la, lb) in enumerate(LL):
+            a, b = 4 * p + la - 1, 4 * q + lb - 1
+            v = T[a, b].copy()
+            if a == b:
+                v -= zero * OG.gram(la, dV)
+            ref[10 * pqi + lli] = v
+    got = out.reshape(60, -1)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+CASES = [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 10, 6), 3), ((16, 16, 16), 1)]
+
+
+@pytest.fixture(scope="module")
+def cases(vie):
+    out = {}
+    for shape, R in CASES:
+        g = Grid(*shape, 0.004, 0.005, 0.0045)
+        eps, sig = random_tissue(g, seed=sum(shape))
+        prob = O.Problem(g, 298e6, eps, sig)
+        Nop = O.NOperator(g, prob.k0)
+        h = setup(vie, g, 298e6, eps, sig)
+        x = random_coefficients(g, R, seed=7 + R)
+        out[shape] = (g, prob, Nop, h, x)
+    yield out
+    for v in out.values():
+        v[3].close()
+
+
+@pytest.mark.parametrize("shape", [c[0] for c in CASES])
+@pytest.mark.parametrize("op", ["A", "PA", "NSCAT"])
+def test_matvec_fp64_parity(vie, cases, shape, op):
+    g, prob, Nop, h, x = cases[shape]
+    G = prob.gram_vector()[:, None, None, None]
+    if op == "A":
+        ref, code = O.apply_A(prob, Nop, x), vie.VIE_OP_A
+    elif op == "PA":
+        ref, code = O.apply_PA(prob, Nop, x), vie.VIE_OP_PA
+    else:
+        ref, code = Nop.apply(x) - G * x, vie.VIE_OP_NSCAT
+    y = gpu_matvec(vie, h, x, vie.VIE_FP64, code)
+    assert rel(y, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [c[0] for c in CASES])
+def test_matvec_fp32_parity(vie, cases, shape):
+    g, prob, Nop, h, x = cases[shape]
+    for op, code in (("A", vie.VIE_OP_A), ("PA", vie.VIE_OP_PA)):
+        ref = O.apply_A(prob, Nop, x) if op == "A" else O.apply_PA(prob, Nop, x)
+        y = gpu_matvec(vie, h, x, vie.VIE_FP32, code)
+        assert rel(y, ref) <= 1e-5
+
+
+def test_matvec_host_buffers_equal_device_buffers(vie, cases):
+    g, prob, Nop, h, x = cases[(7, 5, 9)]
+    yh = np.zeros_like(x)
+    vie.vie_matvec(h, np.ascontiguousarray(x), yh, vie.VIE_FP64, vie.VIE_OP_A)
+    yd = gpu_matvec(vie, h, x, vie.VIE_FP64, vie.VIE_OP_A)
+    assert np.array_equal(yh, yd)
+
+
+def test_planewave_and_dipole_rhs_parity(vie):
+    g = Grid(6, 7, 5, 0.01, 0.009, 0.011)
+    eps, sig = random_tissue(g, seed=31)
+    prob = O.Problem(g, 128e6, eps, sig)
+    h = setup(vie, g, 128e6, eps, sig)
+    d = np.array([0.2, -0.3, 0.93])
+    d /= np.linalg.norm(d)
+    pol = np.cross(d, [0.0, 1.0, 0.0])
+    e = np.zeros((12,) + g.shape, dtype=complex)
+    b = np.zeros_like(e)
+    vie.vie_rhs_planewave(h, pol, d, e, b)
+    e_ref = OR.planewave_tested(g, prob.k0, pol, d)
+    assert rel(e, e_ref) <= 1e-12
+    assert rel(b, OR.rhs(prob, e_ref)) <= 1e-12
+    pos, mom = ring_dipoles(3, 0.06, z=0.01)
+    mom[1] = [0.3, -0.2, 0.5]
+    ed = np.zeros((3, 12) + g.shape, dtype=complex)
+    bd = np.zeros_like(ed)
+    vie.vie_rhs_dipoles(h, pos, mom, ed, bd)
+    ed_ref = OR.dipoles_tested(g, prob.k0, prob.ce, pos, mom)
+    assert rel(ed, ed_ref) <= 1e-12
+    assert rel(bd, OR.rhs(prob, ed_ref)) <= 1e-12
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def sphere(vie):
+    """Config of the Mie check: 16^3 sphere r = 0.1 m, 12.5 mm voxels, eps' = 50, sigma = 0.5, 298 MHz, plane wave."""
+    g = Grid(16, 16, 16, 0.0125, 0.0125, 0.0125)
+    eps, sig = sphere_phantom(g, 0.1, 50.0, 0.5)
+    prob = O.Problem(g, 298e6, eps, sig)
+    Nop = O.NOperator(g, prob.k0)
+    e_inc = OR.planewave_tested(g, prob.k0)
+    b = OR.rhs(prob, e_inc)
+    xo, info = OS.gmres(lambda v: O.apply_PA(prob, Nop, v), O.apply_Pinv(prob, b), tol=1e-11, restart=100, maxit=40)
+    h = setup(vie, g, 298e6, eps, sig)
+    yield g, prob, Nop, e_inc, b, xo, h
+    h.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_solve_parity_sphere(vie, sphere, mode):
+    g, prob, Nop, e_inc, b, xo, h = sphere
+    bd = torch.from_numpy(b[None].copy()).cuda()
+    xd = torch.empty_like(bd)
+    m = vie.VIE_SOLVE_FP64 if mode == "fp64" else vie.VIE_SOLVE_FP32_REFINE
+    rc, info = vie.vie_solve(h, bd, xd, tol=1e-8, restart=50, maxit=40, mode=m)
+    assert rc == vie.VIE_OK, info
+    assert info[0]["resid"] <= 1e-8
+    x = xd.cpu().numpy()[0]
+    assert rel(x, xo) <= 1e-6
+    # fields and absorbed power of the GPU solution vs the oracle post-processing of the same solution
+    ed = torch.from_numpy(e_inc[None].copy()).cuda()
+    ef = torch.empty_like(ed)
+    pa = torch.empty((1,) + g.shape, dtype=torch.float64, device="cuda")
+    P = vie.vie_fields(h, xd, ed, ef, pa)
+    e_ref = OP.fields(prob, Nop, x, e_inc)
+    p_ref, P_ref = OP.absorbed_power(prob, x)
+    assert rel(ef.cpu().numpy()[0], e_ref) <= 1e-12
+    assert rel(pa.cpu().numpy()[0], p_ref) <= 1e-12
+    assert abs(P[0] - P_ref) <= 1e-12 * abs(P_ref)
+    # and the solution's physics against the oracle solution's
+    _, P_or = OP.absorbed_power(prob, xo)
+    assert abs(P[0] - P_or) <= 1e-6 * abs(P_or)
+
+
+def test_batch_independence_and_guess(vie):
+    """A right-hand side gives the same bits alone and inside a batch; a converged guess returns at once."""
+    g = Grid(8, 8, 8, 0.005, 0.005, 0.005)
+    eps, sig = random_tissue(g, seed=41, air_fraction=0.3)
+    h = setup(vie, g, 128e6, eps, sig)
+    prob = O.Problem(g, 128e6, eps, sig)
+    pos, mom = ring_dipoles(3, 0.05)
+    b = np.zeros((3, 12) + g.shape, dtype=complex)
+    vie.vie_rhs_dipoles(h, pos, mom, None, b)
+    bd = torch.from_numpy(b).cuda()
+    xb = torch.empty_like(bd)
+    rc, info = vie.vie_solve(h, bd, xb, tol=1e-7, restart=30, maxit=30, mode=vie.VIE_SOLVE_FP32_REFINE)
+    assert rc == vie.VIE_OK
+    x1 = torch.empty_like(bd[1:2])
+    rc1, info1 = vie.vie_solve(h, bd[1:2].contiguous(), x1, tol=1e-7, restart=30, maxit=30,
+                               mode=vie.VIE_SOLVE_FP32_REFINE)
+    assert torch.equal(x1[0], xb[1])
+    rc2, info2 = vie.vie_solve(h, bd, xb, tol=1e-6, restart=30, maxit=30, mode=vie.VIE_SOLVE_FP32_REFINE, guess=True)
+    assert rc2 == vie.VIE_OK and all(i["iterations"] == 0 for i in info2)
+    h.close()
+
+
+def test_full_size_fp32_matvec_sampled(vie):
+    """64^3 head phantom, 3 mm, 298 MHz, 16 right-hand sides (the benchmark's batched FP32 matvec):
+    x has a few non-zero voxels per right-hand side; y at sampled voxels from oracle Galerkin entries."""
+    g = Grid(64, 64, 64, 0.003, 0.003, 0.003)
+    eps, sig = head_phantom(g)
+    prob = O.Problem(g, 298e6, eps, sig)
+    h = setup(vie, g, 298e6, eps, sig)
+    rng = np.random.Generator(np.random.PCG64(99))
+    R = 16
+    x = np.zeros((R, 12) + g.shape, dtype=np.complex64)
+    src = []
+    for r in range(R):
+        vox = rng.integers(0, 64, size=(2, 3))
+        src.append(vox)
+        for v in vox:
+            x[r, :, v[2], v[1], v[0]] = (rng.standard_normal(12) + 1j * rng.standard_normal(12)).astype(np.complex64)
+    y = gpu_matvec(vie, h, x, vie.VIE_FP32, vie.VIE_OP_A)
+    h.close()
+    G = prob.gram_vector()
+    for r in (0, 7, 15):
+        ms = rng.integers(0, 64, size=(12, 3))
+        ms = np.concatenate([ms, src[r][:1]])  # include a source voxel (self term)
+        D = np.array([m - n for m in ms for n in src[r]])
+        T = OG.n_entries((g.dx, g.dy, g.dz), prob.k0, D).reshape(12, 12, len(ms), len(src[r]))
+        ref = np.zeros((len(ms), 12), dtype=complex)
+        for i, m in enumerate(ms):
+            nx = sum(T[:, :, i, k] @ x[r, :, n[2], n[1], n[0]].astype(complex) for k, n in enumerate(src[r]))
+            xm = x[r, :, m[2], m[1], m[0]].astype(complex)
+            ref[i] = prob.eps[m[2], m[1], m[0]] * G * xm - prob.chi[m[2], m[1], m[0]] * nx
+        got = np.array([y[r, :, m[2], m[1], m[0]] for m in ms])
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_invalid_arguments(vie):
+    g = Grid(3, 3, 3, 0.01, 0.01, 0.01)
+    eps, sig = random_tissue(g, seed=1)
+    with pytest.raises(vie.VieError) as e:
+        vie.vie_setup((3, 3, 0, 0.01, 0.01, 0.01), 1e8, eps, sig)
+    assert e.value.code == vie.VIE_EINVAL
+    bad = eps.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(vie.VieError):
+        vie.vie_setup((3, 3, 3, 0.01, 0.01, 0.01), 1e8, bad, sig)
+    h = setup(vie, g, 1e8, eps, sig)
+    x = np.zeros((1, 12) + g.shape, dtype=complex)
+    with pytest.raises(vie.VieError):
+        vie.vie_matvec(h, x, x, vie.VIE_FP64, vie.VIE_OP_A)
+    with pytest.raises(vie.VieError):
+        vie.vie_matvec(h, x, np.zeros_like(x), 7, vie.VIE_OP_A)
+    with pytest.raises(vie.VieError):
+        vie.vie_solve(h, x, np.zeros_like(x), tol=2.0)
+    h.close()
