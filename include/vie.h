@@ -73,7 +73,7 @@ typedef struct {
     int fp32_matvecs;    /* FP32 operator applications */
     int refinements;     /* outer refinement sweeps (mode VIE_SOLVE_FP32_REFINE) */
     double resid;        /* final ||P^-1 (b - A x)|| / ||P^-1 b||, recomputed in FP64 */
-    double true_resid;   /* final ||b - A x|| / ||b||, recomputed in FP64 */
+    double true_resid;   /* final ||b - A x|| / ||b|| in FP64 when requested (flags bit 1), else -1 */
 } vie_solve_info;
 
 /*
@@ -137,10 +137,14 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *   b       : [nrhs][12][nz][ny][nx] C128
  *   x       : [nrhs][12][nz][ny][nx] C128; on entry the initial guess when
  *             (flags & 1), else ignored (zero guess); on exit the solution
- *   restart : Krylov dimension m >= 1;  maxit: cycles (plain) or refinement sweeps x cycles
+ *   restart : Krylov dimension m in [1, 128];  maxit: cap on restart cycles (plain
+ *             mode) or on refinement sweeps of one FP32 cycle each (mixed mode)
  *   mode    : VIE_SOLVE_FP64 (plain FP64) or VIE_SOLVE_FP32_REFINE (FP32 GMRES with
- *             FP64 iterative refinement; inner products, Hessenberg and Givens
- *             rotations in FP64, Krylov basis stored in FP32)
+ *             FP64 iterative refinement: every cycle starts from the residual
+ *             recomputed with the FP64 matvec; Hessenberg matrix, rotations and
+ *             the solution in FP64, Krylov vectors in FP32)
+ *   flags   : bit 0 = use x as initial guess; bit 1 = also compute true_resid
+ *             (one more FP64 matvec), else true_resid = -1
  *   info    : vie_solve_info[nrhs] host array or NULL
  * Synchronous.  Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
  */
@@ -181,11 +185,13 @@ int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes);
  * vie_stats_reset clears the counters and switches timing on (1) or off (0).
  * vie_stats_read synchronises on the recorded events and returns up to
  * max_entries rows: names (max_entries x 48 chars, NUL-terminated), launch
- * counts, milliseconds (0 without timing); *n_entries rows written and
- * *total_launches over all names.  Any output pointer may be NULL.  Host memory.
+ * counts, milliseconds (0 without timing) and algorithmic bytes (the bytes
+ * each launch must read and write at minimum: its inputs once, its outputs
+ * once); *n_entries rows written and *total_launches over all names.  Any
+ * output pointer may be NULL.  Host memory.  Counters are process-wide.
  */
 int vie_stats_reset(int enable_timing);
-int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, int* n_entries,
+int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, double* bytes, int* n_entries,
                    long long* total_launches);
 
 /* Static description of an error code. */

@@ -82,7 +82,7 @@ def _lib():
     lib.vie_strerror.argtypes = [I]
     lib.vie_strerror.restype = ctypes.c_char_p
     lib.vie_stats_reset.argtypes = [I]
-    lib.vie_stats_read.argtypes = [I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]
+    lib.vie_stats_read.argtypes = [I, P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]
     lib.vie_last_error.argtypes = []
     lib.vie_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -103,10 +103,11 @@ def _ptr(a):
 
 
 def _stream(s):
+    """cudaStream_t of a torch stream (its legacy default stream maps to cudaStreamLegacy), or None."""
     if s is None:
         return None
     if hasattr(s, "cuda_stream"):
-        return s.cuda_stream
+        return s.cuda_stream or 1
     return int(s)
 
 
@@ -181,12 +182,14 @@ def vie_rhs_dipoles(h, pos, mom, e_inc=None, b=None, stream=None):
                                          _ptr(e_inc), _ptr(b), _stream(stream)), "vie_rhs_dipoles")
 
 
-def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFINE, guess=False, stream=None):
+def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFINE, guess=False, true_resid=False,
+              stream=None):
     """Returns (rc, [info dict per right-hand side]); rc is VIE_OK or VIE_NOT_CONVERGED."""
     n = _nrhs(b, h.nv)
     info = (vie_solve_info * n)()
+    flags = (1 if guess else 0) | (2 if true_resid else 0)
     rc = _check(_lib().vie_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
-                                 1 if guess else 0, info, _stream(stream)), "vie_solve")
+                                 flags, info, _stream(stream)), "vie_solve")
     return rc, [i.as_dict() for i in info]
 
 
@@ -219,16 +222,18 @@ def vie_stats_reset(timing=False):
 
 
 def vie_stats_read(max_entries=256):
-    """Returns (total_launches, {kernel name: (launches, device ms)})."""
+    """Returns (total_launches, {kernel name: (launches, device ms, algorithmic bytes)})."""
     names = ctypes.create_string_buffer(48 * max_entries)
     launches = (ctypes.c_longlong * max_entries)()
     ms = (ctypes.c_double * max_entries)()
+    nbytes = (ctypes.c_double * max_entries)()
     n = ctypes.c_int()
     tot = ctypes.c_longlong()
     _check(_lib().vie_stats_read(max_entries, ctypes.addressof(names), ctypes.addressof(launches),
-                                 ctypes.addressof(ms), ctypes.byref(n), ctypes.byref(tot)), "vie_stats_read")
+                                 ctypes.addressof(ms), ctypes.addressof(nbytes), ctypes.byref(n), ctypes.byref(tot)),
+           "vie_stats_read")
     out = {}
     for i in range(n.value):
         nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
-        out[nm] = (launches[i], ms[i])
+        out[nm] = (launches[i], ms[i], nbytes[i])
     return tot.value, out

@@ -308,10 +308,10 @@ int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int r
     REQUIRE(h && b && x, "NULL argument");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     REQUIRE(std::isfinite(tol) && tol > 0 && tol < 1, "tol must be in (0, 1)");
-    REQUIRE(restart >= 1 && restart <= 1000, "restart must be in [1, 1000]");
+    REQUIRE(restart >= 1 && restart <= 128, "restart must be in [1, 128]");
     REQUIRE(maxit >= 1, "maxit must be >= 1");
     REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE, "unknown mode");
-    REQUIRE((flags & ~1) == 0, "unknown flags");
+    REQUIRE((flags & ~3) == 0, "unknown flags");
     const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
@@ -320,7 +320,7 @@ int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int r
     std::vector<void*> d;
     VIE_TRY(sg.bind(d));
     sg.items[1].is_out = true;  // x is returned even when it carried the initial guess
-    int rc = solve_device(h, nrhs, (const double2*)d[0], (double2*)d[1], tol, restart, maxit, mode, flags & 1, info, st);
+    int rc = solve_device(h, nrhs, (const double2*)d[0], (double2*)d[1], tol, restart, maxit, mode, flags, info, st);
     if (rc < 0) return rc;
     VIE_TRY(sg.finish(d));
     VIE_CUDA(cudaStreamSynchronize(st));

@@ -148,7 +148,7 @@ int ws_reserve(vie_handle* h, Workspace& w, size_t bytes);
 // around each launch give its device duration.
 // ---------------------------------------------------------------------------
 struct LaunchScope {
-    LaunchScope(const char* name, cudaStream_t s);
+    LaunchScope(const char* name, cudaStream_t s, double alg_bytes = 0.0);
     ~LaunchScope();
     const char* name;
     cudaStream_t stream;
@@ -160,6 +160,15 @@ struct LaunchScope {
         LaunchScope ls_(name, stream);  \
         __VA_ARGS__;                    \
     } while (0)
+// same, recording the launch's algorithmic bytes (known on the host)
+#define VIE_KLAUNCH_B(name, stream, bytes, ...) \
+    do {                                         \
+        LaunchScope ls_(name, stream, bytes);    \
+        __VA_ARGS__;                             \
+    } while (0)
+// algorithmic bytes counted on the device by the Gram-Schmidt kernels (solve.cu):
+// [0] gs_dots, [1] gs_update, [2] solution_update; optionally reset
+int solve_device_bytes(double out[3], bool reset);
 
 // ---------------------------------------------------------------------------
 // Entry points between translation units
@@ -171,7 +180,7 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);
 // full 3-D FFT of `batch` complex double volumes [batch][Lz][Ly][Lx] in place (forward, unscaled)
 int fft3d_inplace64(vie_handle* h, double2* data, int batch, cudaStream_t s);
 int solve_device(vie_handle* h, int nrhs, const double2* b, double2* x, double tol, int restart, int maxit,
-                 int mode, int use_guess, vie_solve_info* info, cudaStream_t s);
+                 int mode, int flags, vie_solve_info* info, cudaStream_t s);
 int rhs_planewave_device(vie_handle* h, const double pol[3], const double dir[3], double2* e, double2* b,
                          cudaStream_t s);
 int rhs_dipoles_device(vie_handle* h, int nrhs, const double* pos, const double* mom, double2* e, double2* b,

@@ -150,6 +150,74 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
 }
 
 // ---------------------------------------------------------------------------
+// Fused plane kernels (FP32, Lx = Ly = L <= 128): a whole L x L plane of one
+// component grid in shared memory, so the x and y transforms cost one HBM pass.
+// Since L >= 2N - 1, at most L/2 rows are non-zero before the y transform and at
+// most L/2 rows are needed after the inverse one.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(512) xy_fwd_kernel(const float2* __restrict__ x, float2* __restrict__ w, int nx,
+                                                     int ny, const float2* __restrict__ twg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* s = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = s + L * L;
+    const int tid = threadIdx.x;
+    for (int m = tid; m < L; m += 512) tw[m] = twg[m];
+    const long long p = blockIdx.x;  // plane (component, z)
+    const float2* src = x + p * (long long)ny * nx;
+    for (int idx = tid; idx < L * L; idx += 512) {
+        const int yy = idx / L, xx = idx % L;
+        float2 v = make_float2(0.f, 0.f);
+        if (yy < ny && xx < nx) v = src[yy * nx + xx];
+        s[idx] = v;
+    }
+    __syncthreads();
+    fft_smem<float2, L, L / 2, 1, 1, L, 512>(s, tw, -1);  // rows 0..L/2-1 along x
+    fft_smem<float2, L, 1, L, L, 0, 512>(s, tw, -1);      // L columns along y
+    float2* dst = w + p * (long long)L * L;
+    for (int idx = tid; idx < L * L; idx += 512) dst[idx] = s[idx];
+}
+
+template <int L>
+__global__ void __launch_bounds__(512) xy_inv_kernel(const float2* __restrict__ w, float2* __restrict__ y,
+                                                     MatvecEpi epi, const float2* __restrict__ twg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* s = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = s + L * L;
+    const int tid = threadIdx.x;
+    for (int m = tid; m < L; m += 512) tw[m] = twg[m];
+    const long long p = blockIdx.x;  // plane (r * 12 + alpha) * nz + z
+    const float2* src = w + p * (long long)L * L;
+    for (int idx = tid; idx < L * L; idx += 512) s[idx] = src[idx];
+    __syncthreads();
+    fft_smem<float2, L, 1, L, L, 0, 512>(s, tw, +1);      // L columns along y
+    fft_smem<float2, L, L / 2, 1, 1, L, 512>(s, tw, +1);  // rows 0..L/2-1 along x
+    const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
+    const int alpha = (int)((p / nz) % 12);
+    const long long zoff = (p % nz) * (long long)ny * nx;
+    const long long base = p * (long long)ny * nx;
+    const float gl = (float)((alpha % 4) == 0 ? epi.g1 : epi.g234);
+    const float2* xin = reinterpret_cast<const float2*>(epi.x);
+    const float2* c1 = reinterpret_cast<const float2*>(epi.c1);
+    const float2* c2 = reinterpret_cast<const float2*>(epi.c2);
+    for (int idx = tid; idx < ny * nx; idx += 512) {
+        const int yy = idx / nx, xx = idx % nx;
+        float2 v = s[yy * L + xx];
+        const long long vox = zoff + idx;
+        if (epi.op == VIE_OP_A) {
+            float2 xv = xin[base + idx];
+            v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[vox], v));
+        } else if (epi.op == VIE_OP_PA) {
+            float2 xv = xin[base + idx];
+            float2 t = cmul(c2[vox], v);
+            const float ig = 1.0f / gl;
+            v = csub(cmul(c1[vox], xv), mk(ig * t.x, ig * t.y));
+        }
+        y[base + idx] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -180,7 +248,13 @@ static int launch_line_L(const char* name, const vie_handle* h, const LineArgs& 
         set_error("line FFT grid too large");
         return VIE_EINVAL;
     }
-    VIE_KLAUNCH(name, s, line_fft_kernel<T, L, EPI><<<(unsigned)blocks, NT, smem, s>>>(a, twiddles<T>(h, L), e));
+    // algorithmic bytes: inputs read once, outputs written once (+ x and the coefficient maps in the epilogue)
+    double bytes = (double)sizeof(typename CT<T>::C) * (double)a.na * a.nb * (a.n_in + a.n_out);
+    if (EPI && e.op != VIE_OP_NSCAT)
+        bytes += (double)sizeof(typename CT<T>::C) *
+                 ((double)a.na * a.nb * a.n_out + (double)h->nv * (e.op == VIE_OP_PA ? 2 : 1));
+    VIE_KLAUNCH_B(name, s, bytes,
+                  line_fft_kernel<T, L, EPI><<<(unsigned)blocks, NT, smem, s>>>(a, twiddles<T>(h, L), e));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
@@ -215,7 +289,9 @@ static int launch_z_L(const char* name, const vie_handle* h, const ZArgs& z, cud
         configured = true;
     }
     long long blocks = (long long)z.Ly * ((z.Lx + TB - 1) / TB);
-    VIE_KLAUNCH(name, s, zpass_kernel<T, L><<<(unsigned)blocks, ZCfg<T, L>::NT, smem, s>>>(z, twiddles<T>(h, L)));
+    const double bytes = (double)sizeof(C) * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
+    VIE_KLAUNCH_B(name, s, bytes,
+                  zpass_kernel<T, L><<<(unsigned)blocks, ZCfg<T, L>::NT, smem, s>>>(z, twiddles<T>(h, L)));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
@@ -238,6 +314,46 @@ static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z
     return VIE_EINVAL;
 }
 
+template <int L>
+static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
+                       const MatvecEpi& e, cudaStream_t s) {
+    const size_t smem = sizeof(float2) * (size_t)(L * L + L);
+    static bool configured = false;
+    if (!configured) {
+        VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    const double plane_in = (double)nx * ny, plane_full = (double)L * L;
+    if (fwd)
+        VIE_KLAUNCH_B("fft_xy_f32", s, 8.0 * planes * (plane_in + plane_full),
+                    xy_fwd_kernel<L><<<(unsigned)planes, 512, smem, s>>>((const float2*)in, (float2*)out, nx, ny,
+                                                                        h->tw32 + L));
+    else
+        VIE_KLAUNCH_B("ifft_xy_epilogue_f32", s,
+                      8.0 * (planes * (plane_full + plane_in * (e.op == VIE_OP_NSCAT ? 1 : 2)) +
+                             (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0)),
+                    xy_inv_kernel<L><<<(unsigned)planes, 512, smem, s>>>((const float2*)in, (float2*)out, e,
+                                                                        h->tw32 + L));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+static bool fused_xy_ok(const vie_handle* h) { return h->L[0] == h->L[1] && h->L[0] >= 8 && h->L[0] <= 128; }
+
+static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
+                     const MatvecEpi& e, cudaStream_t s) {
+    switch (h->L[0]) {
+        case 8: return launch_xy_L<8>(fwd, h, in, out, planes, nx, ny, e, s);
+        case 16: return launch_xy_L<16>(fwd, h, in, out, planes, nx, ny, e, s);
+        case 32: return launch_xy_L<32>(fwd, h, in, out, planes, nx, ny, e, s);
+        case 64: return launch_xy_L<64>(fwd, h, in, out, planes, nx, ny, e, s);
+        case 128: return launch_xy_L<128>(fwd, h, in, out, planes, nx, ny, e, s);
+    }
+    set_error("fused xy path: unsupported length");
+    return VIE_EINVAL;
+}
+
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
     size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     size_t comps = (size_t)nrhs * 12 * h->nz;
@@ -255,26 +371,31 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     C* W1 = reinterpret_cast<C*>(h->fft_ws.ptr);
     C* W2 = W1 + comps * ny * Lx;
     MatvecEpi noepi{};
-    // x-pass: lines along x, contiguous
-    LineArgs a{};
-    a.in = x;
-    a.out = W1;
-    a.na = 1;
-    a.nb = (int)(comps * ny);
-    a.ia = 0, a.il = 1, a.ib = nx;
-    a.oa = 0, a.ol = 1, a.ob = Lx;
-    a.n_in = nx, a.n_out = Lx, a.dir = -1;
-    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
-    // y-pass
-    a = LineArgs{};
-    a.in = W1;
-    a.out = W2;
-    a.na = (int)comps;
-    a.nb = Lx;
-    a.ia = (long long)ny * Lx, a.il = Lx, a.ib = 1;
-    a.oa = (long long)Ly * Lx, a.ol = Lx, a.ob = 1;
-    a.n_in = ny, a.n_out = Ly, a.dir = -1;
-    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
+    const bool fused = sizeof(T) == 4 && fused_xy_ok(h);
+    if (fused) {
+        VIE_TRY(launch_xy(true, h, x, W2, comps, nx, ny, noepi, s));
+    } else {
+        // x-pass: lines along x, contiguous
+        LineArgs a{};
+        a.in = x;
+        a.out = W1;
+        a.na = 1;
+        a.nb = (int)(comps * ny);
+        a.ia = 0, a.il = 1, a.ib = nx;
+        a.oa = 0, a.ol = 1, a.ob = Lx;
+        a.n_in = nx, a.n_out = Lx, a.dir = -1;
+        VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
+        // y-pass
+        a = LineArgs{};
+        a.in = W1;
+        a.out = W2;
+        a.na = (int)comps;
+        a.nb = Lx;
+        a.ia = (long long)ny * Lx, a.il = Lx, a.ib = 1;
+        a.oa = (long long)Ly * Lx, a.ol = Lx, a.ob = 1;
+        a.n_in = ny, a.n_out = Ly, a.dir = -1;
+        VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
+    }
     // z-pass with block product
     ZArgs z{};
     z.w = W2;
@@ -284,8 +405,26 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
     z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
     VIE_TRY(launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s));
+    MatvecEpi e{};
+    e.x = x;
+    e.op = op;
+    e.nx = nx, e.ny = ny, e.nz = nz;
+    const double dV = h->dx * h->dy * h->dz;
+    e.g1 = dV;
+    e.g234 = dV / 12.0;
+    if (sizeof(T) == 8) {
+        e.c1 = h->ieps64;
+        e.c2 = op == VIE_OP_A ? (const void*)h->chi64 : (const void*)h->tau64;
+    } else {
+        e.c1 = h->ieps32;
+        e.c2 = op == VIE_OP_A ? (const void*)h->chi32 : (const void*)h->tau32;
+    }
+    if (fused) {
+        VIE_TRY(launch_xy(false, h, W2, y, comps, nx, ny, e, s));
+        return VIE_OK;
+    }
     // y-inverse
-    a = LineArgs{};
+    LineArgs a{};
     a.in = W2;
     a.out = W1;
     a.na = (int)comps;
@@ -303,20 +442,6 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.ia = 0, a.il = 1, a.ib = Lx;
     a.oa = 0, a.ol = 1, a.ob = nx;
     a.n_in = Lx, a.n_out = nx, a.dir = +1;
-    MatvecEpi e{};
-    e.x = x;
-    e.op = op;
-    e.nx = nx, e.ny = ny, e.nz = nz;
-    double dV = h->dx * h->dy * h->dz;
-    e.g1 = dV;
-    e.g234 = dV / 12.0;
-    if (sizeof(T) == 8) {
-        e.c1 = h->ieps64;
-        e.c2 = op == VIE_OP_A ? (const void*)h->chi64 : (const void*)h->tau64;
-    } else {
-        e.c1 = h->ieps32;
-        e.c2 = op == VIE_OP_A ? (const void*)h->chi32 : (const void*)h->tau32;
-    }
     VIE_TRY((launch_line<T, true>(sizeof(T) == 8 ? "ifft_x_epilogue_f64" : "ifft_x_epilogue_f32", h, Lx, a, e, s)));
     return VIE_OK;
 }

@@ -1,26 +1,51 @@
 // Restarted, left-preconditioned GMRES on the device, batched over right-hand sides
 // (Section IV-B: preconditioner P = M_eps G; Section V: GMRES with restart and a cap
-// on outer iterations), with an FP32 variant wrapped in FP64 iterative refinement.
+// on the number of cycles), with an FP32 variant wrapped in FP64 iterative refinement.
 //
-// Per cycle and right-hand side r: v_0 = r/||r||; for j = 0..m-1 the Arnoldi step
-// w = P^-1 A v_j, h = V^H w (classical Gram-Schmidt, a second pass when the norm
-// drops by more than a factor 1/sqrt2), h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j};
-// complex Givens rotations keep the Hessenberg matrix triangular and give the
-// residual estimate |g_{j+1}|; at the end H y = g is solved and x += V y.
-// Inner products, norms, the Hessenberg matrix, the rotations and the solution
-// update are FP64 in both modes; only the Krylov vectors and the matvec are FP32
-// in the mixed mode.  Reductions use a fixed partition of each vector, so the
-// result for one right-hand side does not depend on the others in the batch.
+// Arnoldi with classical Gram-Schmidt and a second pass where the new vector lost
+// more than half of its squared norm; complex Givens rotations keep the Hessenberg
+// matrix triangular and give the residual estimate |g_{j+1}|; at the end of a cycle
+// H y = g is solved and x += V y.
+//
+// Memory traffic: the Krylov vectors are stored as u_i = n_i v_i with v_i orthonormal
+// and n_i = ||u_i|| (close to 1) kept in FP64, so no separate normalisation pass is
+// needed: the matvec writes op(u_j) straight into slot j+1, one pass computes every
+// inner product u_i^H w and ||w||^2, and one pass subtracts the projections, rescales
+// by 1/||w|| and returns the new squared norm.  The Hessenberg entries follow from
+// those scalars: h_ij = (u_i^H w)/(n_i n_j), h_{j+1,j} = n_{j+1}/(sigma n_j) with sigma
+// the rescale factor applied to the stored vector.
+//
+// Arithmetic: in the mixed mode the per-thread products and warp sums use FP32 (the
+// Krylov vectors are FP32), block and grid reductions, the Hessenberg matrix, the
+// rotations, the solution and every residual are FP64.  The plain mode is FP64
+// throughout.  Every reduction uses a fixed partition of each right-hand side's
+// vector, so one right-hand side's result does not depend on the others in a batch.
 #include <cmath>
 #include <vector>
 
 #include "common.cuh"
 
+// algorithmic bytes moved by the Gram-Schmidt kernels: [0] dots, [1] update, [2] solution update
+__device__ unsigned long long g_gs_bytes[3];
+
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPer = 8;  // elements per thread per reduction block
-constexpr int kSeg = kThreads * kPer;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxV = 130;  // basis vectors per pass (restart <= 128)
+
+template <typename VC>
+struct Prec;
+template <>
+struct Prec<float2> {
+    using R = float;
+    static constexpr int K = 4;  // complex values per thread per pass (32 bytes)
+};
+template <>
+struct Prec<double2> {
+    using R = double;
+    static constexpr int K = 2;
+};
 
 __device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
@@ -35,131 +60,252 @@ __device__ __forceinline__ double2 from_d<double2>(double2 v) {
     return v;
 }
 
-__device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double2 s = make_double2(0, 0);
-    if (threadIdx.x == 0)
-        for (int i = 0; i < kThreads / 32; ++i) s.x += sh[i].x, s.y += sh[i].y;
-    return s;  // valid in thread 0
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// partial[r][blk][i] = sum_{e in block} conj(V_i[r][e]) w[r][e], i < nvec
-template <typename VC, typename WC>
-__global__ void __launch_bounds__(kThreads) dots_kernel(const VC* __restrict__ V, long long vstride, const WC* __restrict__ w,
-                                                        long long n, int nvec, double2* __restrict__ partial, int nblk,
-                                                        const int* __restrict__ flag) {
-    __shared__ double2 sh[kThreads / 32];
+// K consecutive complex values starting at element e0 of p (zero past n); 16-byte loads
+// when the chunk is complete (vectors start on even elements, so float pairs are aligned).
+template <typename C, int K>
+__device__ __forceinline__ void load_chunk(const C* __restrict__ p, long long e0, long long n, C* v) {
+    if (e0 + K <= n) {
+        if constexpr (sizeof(C) == 8) {
+            const float4* q = reinterpret_cast<const float4*>(p + e0);
+#pragma unroll
+            for (int k = 0; k < K / 2; ++k) {
+                const float4 t = q[k];
+                v[2 * k] = make_float2(t.x, t.y);
+                v[2 * k + 1] = make_float2(t.z, t.w);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = p[e0 + k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = e0 + k < n ? p[e0 + k] : C{};
+    }
+}
+template <typename C, int K>
+__device__ __forceinline__ void store_chunk(C* __restrict__ p, long long e0, long long n, const C* v) {
+    if (e0 + K <= n) {
+        if constexpr (sizeof(C) == 8) {
+            float4* q = reinterpret_cast<float4*>(p + e0);
+#pragma unroll
+            for (int k = 0; k < K / 2; ++k) q[k] = make_float4(v[2 * k].x, v[2 * k].y, v[2 * k + 1].x, v[2 * k + 1].y);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) p[e0 + k] = v[k];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (e0 + k < n) p[e0 + k] = v[k];
+    }
+}
+
+// partial[r][blk][i] = sum over the block's elements of conj(U_i) w (i < nvec) and, at i = nvec, |w|^2
+template <typename VC>
+__global__ void __launch_bounds__(kThreads) gs_dots_kernel(const VC* __restrict__ U, long long ustride,
+                                                           const VC* __restrict__ w, long long n, int nvec,
+                                                           double2* __restrict__ partial, int nblk,
+                                                           const int* __restrict__ flag) {
+    using R = typename Prec<VC>::R;
+    constexpr int K = Prec<VC>::K;
+    __shared__ double2 sh[kWarps][kMaxV + 1];
     const int r = blockIdx.y, blk = blockIdx.x;
     if (flag && !flag[r]) return;
-    const long long base = (long long)r * n + (long long)blk * kSeg;
-    double2 wv[kPer];
+    if (blk == 0 && threadIdx.x == 0) atomicAdd(&g_gs_bytes[0], (unsigned long long)(n * sizeof(VC) * (nvec + 1)));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long e0 = (long long)blk * (kThreads * K) + (long long)threadIdx.x * K;
+    const long long roff = (long long)r * n;
+    VC wv[K];
+    load_chunk<VC, K>(w + roff, e0, n, wv);
+    {
+        R a = 0;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        long long e = (long long)blk * kSeg + threadIdx.x + k * kThreads;
-        wv[k] = e < n ? to_d(w[base + threadIdx.x + k * kThreads]) : make_double2(0, 0);
+        for (int k = 0; k < K; ++k) a += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
+        a = warp_sum(a);
+        if (lane == 0) sh[wid][nvec] = make_double2((double)a, 0.0);
     }
+#pragma unroll 2
     for (int i = 0; i < nvec; ++i) {
-        const VC* vi = V + i * vstride + base;
-        double2 acc = make_double2(0, 0);
+        VC uv[K];
+        load_chunk<VC, K>(U + i * ustride + roff, e0, n, uv);
+        R ar = 0, ai = 0;
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            long long e = (long long)blk * kSeg + threadIdx.x + k * kThreads;
-            if (e < n) {
-                double2 a = to_d(vi[threadIdx.x + k * kThreads]);
-                acc.x += a.x * wv[k].x + a.y * wv[k].y;
-                acc.y += a.x * wv[k].y - a.y * wv[k].x;
-            }
+        for (int k = 0; k < K; ++k) {
+            ar += uv[k].x * wv[k].x + uv[k].y * wv[k].y;
+            ai += uv[k].x * wv[k].y - uv[k].y * wv[k].x;
         }
-        double2 s = block_sum(acc, sh);
-        if (threadIdx.x == 0) partial[((long long)r * nblk + blk) * nvec + i] = s;
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if (lane == 0) sh[wid][i] = make_double2((double)ar, (double)ai);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= nvec; i += kThreads) {
+        double2 s = make_double2(0, 0);
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) s.x += sh[q][i].x, s.y += sh[q][i].y;
+        partial[((long long)r * nblk + blk) * (nvec + 1) + i] = s;
     }
 }
 
-// out[r * rs + i * is] (+)= sum_blk partial[r][blk][i]; one block per (i, r), fixed order.
-__global__ void __launch_bounds__(kThreads) finalize_kernel(const double2* __restrict__ partial, int nblk, int nvec,
-                                                            double2* out, long long rs, long long is, int accumulate,
-                                                            const int* __restrict__ flag) {
-    __shared__ double2 sh[kThreads / 32];
+// w <- scale * (w - sum_i coef_i U_i), in place; npart[r][blk] = |new w|^2 over the block
+template <typename VC>
+__global__ void __launch_bounds__(kThreads) gs_update_kernel(const VC* __restrict__ U, long long ustride, VC* w,
+                                                             long long n, int nvec, const double2* __restrict__ coef,
+                                                             int ldc, const double* __restrict__ scale,
+                                                             double* __restrict__ npart, int nblk,
+                                                             const int* __restrict__ flag) {
+    using R = typename Prec<VC>::R;
+    constexpr int K = Prec<VC>::K;
+    __shared__ VC c[kMaxV];
+    __shared__ double shn[kWarps];
+    const int r = blockIdx.y, blk = blockIdx.x;
+    if (flag && !flag[r]) return;
+    if (blk == 0 && threadIdx.x == 0) atomicAdd(&g_gs_bytes[1], (unsigned long long)(n * sizeof(VC) * (nvec + 2)));
+    for (int i = threadIdx.x; i < nvec; i += kThreads) c[i] = from_d<VC>(coef[(long long)r * ldc + i]);
+    __syncthreads();
+    const long long e0 = (long long)blk * (kThreads * K) + (long long)threadIdx.x * K;
+    const long long roff = (long long)r * n;
+    VC acc[K];
+    load_chunk<VC, K>(w + roff, e0, n, acc);
+#pragma unroll 2
+    for (int i = 0; i < nvec; ++i) {
+        VC uv[K];
+        load_chunk<VC, K>(U + i * ustride + roff, e0, n, uv);
+        const VC ci = c[i];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            acc[k].x -= ci.x * uv[k].x - ci.y * uv[k].y;
+            acc[k].y -= ci.x * uv[k].y + ci.y * uv[k].x;
+        }
+    }
+    const R s = (R)scale[r];
+    R a = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        acc[k].x *= s;
+        acc[k].y *= s;
+        a += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
+    }
+    store_chunk<VC, K>(w + roff, e0, n, acc);
+    a = warp_sum(a);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) shn[wid] = (double)a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) t += shn[q];
+        npart[(long long)r * nblk + blk] = t;
+    }
+}
+
+// out[r * ldo + i] = sum_blk partial[r][blk][i] for i < nv (fixed order); one block per (i, r)
+__global__ void __launch_bounds__(kThreads) finalize2_kernel(const double2* __restrict__ partial, int nblk, int nv,
+                                                             double2* __restrict__ out, int ldo,
+                                                             const int* __restrict__ flag) {
+    __shared__ double2 sh[kWarps];
     const int i = blockIdx.x, r = blockIdx.y;
     if (flag && !flag[r]) return;
-    double2 acc = make_double2(0, 0);
+    double2 a = make_double2(0, 0);
     for (int b = threadIdx.x; b < nblk; b += kThreads) {
-        double2 v = partial[((long long)r * nblk + b) * nvec + i];
-        acc.x += v.x, acc.y += v.y;
+        const double2 v = partial[((long long)r * nblk + b) * nv + i];
+        a.x += v.x, a.y += v.y;
     }
-    double2 s = block_sum(acc, sh);
+    a.x = warp_sum(a.x);
+    a.y = warp_sum(a.y);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double2* o = out + r * rs + i * is;
-        if (accumulate) {
-            o->x += s.x;
-            o->y += s.y;
-        } else {
-            *o = s;
-        }
+        double2 s = make_double2(0, 0);
+        for (int q = 0; q < kWarps; ++q) s.x += sh[q].x, s.y += sh[q].y;
+        out[(long long)r * ldo + i] = s;
     }
 }
 
-// w[r] -= sum_i h[r][i] V_i[r]   (h read from H column j: H[r][i][j] at hbase + r*hstride + i*hcol)
-template <typename VC, typename WC>
-__global__ void update_kernel(const VC* __restrict__ V, long long vstride, WC* __restrict__ w, long long n, int nvec,
-                              const double2* __restrict__ h, long long hstride, long long hcol,
-                              const int* __restrict__ flag) {
-    const int r = blockIdx.y;
+__global__ void __launch_bounds__(kThreads) finalize1_kernel(const double* __restrict__ part, int nblk,
+                                                             double* __restrict__ out, const int* __restrict__ flag) {
+    __shared__ double sh[kWarps];
+    const int r = blockIdx.x;
     if (flag && !flag[r]) return;
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const long long o = (long long)r * n + e;
-    double2 acc = to_d(w[o]);
-    for (int i = 0; i < nvec; ++i) {
-        double2 hv = h[r * hstride + i * hcol];
-        double2 v = to_d(V[i * vstride + o]);
-        acc.x -= hv.x * v.x - hv.y * v.y;
-        acc.y -= hv.x * v.y + hv.y * v.x;
+    double a = 0;
+    for (int b = threadIdx.x; b < nblk; b += kThreads) a += part[(long long)r * nblk + b];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int q = 0; q < kWarps; ++q) s += sh[q];
+        out[r] = s;
     }
-    w[o] = from_d<WC>(acc);
 }
 
-// x[r] += scale[r] * sum_i y[r][i] V_i[r] for i < k[r]
+__global__ void copy_norm_kernel(const double2* __restrict__ D, int ldd, double* out, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) out[r] = D[(long long)r * ldd].x;
+}
+
+// x[r] += sum_i c[r][i] U_i[r] (i < k[r]); the sum in the basis precision, the update in FP64
 template <typename VC>
-__global__ void xupdate_kernel(const VC* __restrict__ V, long long vstride, double2* __restrict__ x, long long n,
-                               const double2* __restrict__ y, int ystride, const int* __restrict__ k) {
+__global__ void __launch_bounds__(kThreads) xupdate_kernel(const VC* __restrict__ U, long long ustride,
+                                                           double2* __restrict__ x, long long n,
+                                                           const double2* __restrict__ c, int ldc,
+                                                           const int* __restrict__ k) {
+    constexpr int K = Prec<VC>::K;
+    __shared__ VC cs[kMaxV];
     const int r = blockIdx.y;
     const int kr = k[r];
     if (kr == 0) return;
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const long long o = (long long)r * n + e;
-    double2 acc = x[o];
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(&g_gs_bytes[2], (unsigned long long)(n * (sizeof(VC) * kr + 2 * sizeof(double2))));
+    for (int i = threadIdx.x; i < kr; i += kThreads) cs[i] = from_d<VC>(c[(long long)r * ldc + i]);
+    __syncthreads();
+    const long long e0 = (long long)blockIdx.x * (kThreads * K) + (long long)threadIdx.x * K;
+    const long long roff = (long long)r * n;
+    VC acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = VC{};
     for (int i = 0; i < kr; ++i) {
-        double2 yv = y[r * ystride + i];
-        double2 v = to_d(V[i * vstride + o]);
-        acc.x += yv.x * v.x - yv.y * v.y;
-        acc.y += yv.x * v.y + yv.y * v.x;
+        VC uv[K];
+        load_chunk<VC, K>(U + i * ustride + roff, e0, n, uv);
+        const VC ci = cs[i];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            acc[q].x += ci.x * uv[q].x - ci.y * uv[q].y;
+            acc[q].y += ci.x * uv[q].y + ci.y * uv[q].x;
+        }
     }
-    x[o] = acc;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const long long e = e0 + q;
+        if (e < n) {
+            double2 xv = x[roff + e];
+            xv.x += (double)acc[q].x;
+            xv.y += (double)acc[q].y;
+            x[roff + e] = xv;
+        }
+    }
 }
 
-// dst[r] = src[r] * s[r] (s real), types may differ
-template <typename SC, typename DC>
-__global__ void scale_kernel(const SC* __restrict__ src, DC* __restrict__ dst, long long n,
-                             const double* __restrict__ s) {
+// dst[r] = src[r] * s[r] (FP64 source), any destination precision
+template <typename DC>
+__global__ void scale_from64_kernel(const double2* __restrict__ src, DC* __restrict__ dst, long long n,
+                                    const double* __restrict__ s) {
     const int r = blockIdx.y;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const long long o = (long long)r * n + e;
-    double2 v = to_d(src[o]);
+    const double2 v = src[o];
     const double f = s[r];
     dst[o] = from_d<DC>(make_double2(v.x * f, v.y * f));
 }
 
-// out = a - b (FP64)
 __global__ void sub_kernel(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out,
                            long long total) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,63 +321,114 @@ __global__ void precond_rhs_kernel(const double2* __restrict__ b, const double2*
     const long long vox = e % nv;
     const int alpha = (int)((e / nv) % 12);
     const double ig = 1.0 / (alpha % 4 == 0 ? g1 : g234);
-    double2 v = b[e], c = ieps[vox];
+    const double2 v = b[e], c = ieps[vox];
     out[e] = make_double2(ig * (v.x * c.x - v.y * c.y), ig * (v.x * c.y + v.y * c.x));
 }
 
 struct GState {
-    double2* H;    // [R][m+1][m]
-    double2* cs;   // [R][m]   (real part used)
-    double2* sn;   // [R][m]
-    double2* g;    // [R][m+1]
-    double2* y;    // [R][m]
-    double2* tmp;  // [R] scratch (norms)
-    double* beta;  // [R]
-    double* target;  // [R] absolute target for |g_{j+1}|
-    double* sc;    // [R] scale factors
-    int* active;   // [R]
-    int* k;        // [R] Arnoldi steps of the current cycle
-    int* nactive;  // [1]
     int m;
+    double2* H;      // [R][m+1][m]
+    double2* cs;     // [R][m]  (real part used)
+    double2* sn;     // [R][m]
+    double2* g;      // [R][m+1]
+    double2* y;      // [R][m]
+    double2* D;      // [R][m+2]  inner products of the current pass, last = |w|^2
+    double2* coef;   // [R][m+1]  projection coefficients of the current pass
+    double* nrm;     // [R][m+1]  norms n_i of the stored vectors
+    double* beta;    // [R]
+    double* target;  // [R] absolute target for |g_{j+1}|
+    double* scale;   // [R] rescale factor of the current pass
+    double* sigma;   // [R] product of the rescale factors applied in this step
+    double* F;       // [R] squared norm of the stored new vector
+    int* active;     // [R]
+    int* reflag;     // [R] second Gram-Schmidt pass needed
+    int* k;          // [R] Arnoldi steps of the current cycle
+    int* nactive;    // [1]
 };
 
-// start of a cycle: beta = ||r||, g = (beta, 0...), active = beta > target, scale = 1/beta
-__global__ void cycle_init_kernel(GState s, int R, const double2* __restrict__ nrm2) {
+// start of a cycle: beta = ||r||, g = (beta, 0...), u_0 = r / beta (n_0 = 1), active = beta > target
+__global__ void cycle_init_kernel(GState s, int R, const double* __restrict__ rn2) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    const double beta = sqrt(fmax(nrm2[r].x, 0.0));
+    const double beta = sqrt(fmax(rn2[r], 0.0));
     s.beta[r] = beta;
     for (int i = 0; i <= s.m; ++i) s.g[r * (s.m + 1) + i] = make_double2(0, 0);
     s.g[r * (s.m + 1)] = make_double2(beta, 0);
     s.k[r] = 0;
     const int act = (beta > s.target[r]) && beta > 0.0 && isfinite(beta);
     s.active[r] = act;
-    s.sc[r] = act ? 1.0 / beta : 0.0;
+    s.scale[r] = act ? 1.0 / beta : 0.0;
+    s.nrm[r * (s.m + 1)] = 1.0;
 }
 
-// Givens step j for every active RHS; nrm2 = ||w||^2 after orthogonalisation.
-__global__ void givens_kernel(GState s, int R, int j, const double2* __restrict__ nrm2) {
+// after the first projection pass: H[:, j], coefficients, rescale 1/|w|
+__global__ void coef1_kernel(GState s, int R, int j) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !s.active[r]) return;
+    const int m = s.m;
+    const double2* D = s.D + (long long)r * (m + 2);
+    const double* n = s.nrm + (long long)r * (m + 1);
+    double2* H = s.H + (long long)r * (m + 1) * m;
+    const double nj = n[j];
+    for (int i = 0; i <= j; ++i) {
+        const double2 d = D[i];
+        H[i * m + j] = make_double2(d.x / (n[i] * nj), d.y / (n[i] * nj));
+        s.coef[(long long)r * (m + 1) + i] = make_double2(d.x / (n[i] * n[i]), d.y / (n[i] * n[i]));
+    }
+    const double e = D[j + 1].x;
+    const double sc = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
+    s.scale[r] = sc;
+    s.sigma[r] = sc;
+}
+
+// second pass where the rescaled new vector has squared length below 1/2
+__global__ void reorth_kernel(GState s, int R) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    if (!s.active[r]) {
-        s.sc[r] = 0.0;
-        return;
+    const double f = s.F[r];
+    const int fl = s.active[r] && f > 0.0 && f < 0.5;
+    s.reflag[r] = fl;
+    if (fl) s.scale[r] = 1.0 / sqrt(f);
+}
+
+// after the second projection pass: correction of H[:, j], coefficients, cumulative rescale
+__global__ void coef2_kernel(GState s, int R, int j) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !s.reflag[r]) return;
+    const int m = s.m;
+    const double2* D = s.D + (long long)r * (m + 2);
+    const double* n = s.nrm + (long long)r * (m + 1);
+    double2* H = s.H + (long long)r * (m + 1) * m;
+    const double f = n[j] * s.sigma[r];
+    for (int i = 0; i <= j; ++i) {
+        const double2 d = D[i];
+        H[i * m + j].x += d.x / (n[i] * f);
+        H[i * m + j].y += d.y / (n[i] * f);
+        s.coef[(long long)r * (m + 1) + i] = make_double2(d.x / (n[i] * n[i]), d.y / (n[i] * n[i]));
     }
+    s.sigma[r] *= s.scale[r];
+}
+
+// Givens step j for every active right-hand side
+__global__ void givens_kernel(GState s, int R, int j) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || !s.active[r]) return;
     const int m = s.m;
     double2* H = s.H + (long long)r * (m + 1) * m;
-    const double hnext = sqrt(fmax(nrm2[r].x, 0.0));
-    H[(j + 1) * m + j] = make_double2(hnext, 0);
+    double* n = s.nrm + (long long)r * (m + 1);
+    const double nn = sqrt(fmax(s.F[r], 0.0));
+    n[j + 1] = nn;
+    const double hnext = (s.sigma[r] > 0.0 && n[j] > 0.0) ? nn / (s.sigma[r] * n[j]) : 0.0;
     for (int i = 0; i < j; ++i) {
-        double2 a = H[i * m + j], b = H[(i + 1) * m + j];
-        double c = s.cs[r * m + i].x;
-        double2 sn = s.sn[r * m + i];
-        // t = c a + sn b ; b' = -conj(sn) a + c b
-        double2 t = make_double2(c * a.x + sn.x * b.x - sn.y * b.y, c * a.y + sn.x * b.y + sn.y * b.x);
-        double2 bb = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
+        const double2 a = H[i * m + j], b = H[(i + 1) * m + j];
+        const double c = s.cs[r * m + i].x;
+        const double2 sn = s.sn[r * m + i];
+        const double2 t = make_double2(c * a.x + sn.x * b.x - sn.y * b.y, c * a.y + sn.x * b.y + sn.y * b.x);
+        const double2 bb = make_double2(-(sn.x * a.x + sn.y * a.y) + c * b.x, -(sn.x * a.y - sn.y * a.x) + c * b.y);
         H[i * m + j] = t;
         H[(i + 1) * m + j] = bb;
     }
-    double2 a = H[j * m + j];
+    const double2 a = H[j * m + j];
     const double b = hnext;
     const double aa = hypot(a.x, a.y);
     const double den = hypot(aa, b);
@@ -250,16 +447,13 @@ __global__ void givens_kernel(GState s, int R, int j, const double2* __restrict_
     s.cs[r * m + j] = make_double2(c, 0);
     s.sn[r * m + j] = sn;
     H[j * m + j] = make_double2(c * a.x + sn.x * b, c * a.y + sn.y * b);
-    H[(j + 1) * m + j] = make_double2(0, 0);
     double2* g = s.g + r * (m + 1);
-    double2 gj = g[j];
+    const double2 gj = g[j];
     g[j + 1] = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));
     g[j] = make_double2(c * gj.x, c * gj.y);
     s.k[r] = j + 1;
     const double res = hypot(g[j + 1].x, g[j + 1].y);
-    const bool done = res <= s.target[r] || hnext == 0.0 || !isfinite(res);
-    s.sc[r] = (hnext > 0.0 && isfinite(hnext)) ? 1.0 / hnext : 0.0;
-    if (done) s.active[r] = 0;
+    if (res <= s.target[r] || hnext == 0.0 || !isfinite(res)) s.active[r] = 0;
 }
 
 __global__ void count_active_kernel(const int* __restrict__ active, int R, int* out) {
@@ -268,65 +462,46 @@ __global__ void count_active_kernel(const int* __restrict__ active, int R, int* 
     *out = c;
 }
 
-// reorthogonalisation flag: second Gram-Schmidt pass where ||w_after||^2 < 0.5 ||w_before||^2
-__global__ void reorth_flag_kernel(const double2* __restrict__ before, const double2* __restrict__ after,
-                                   const int* __restrict__ active, int* flag, int R) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    flag[r] = active[r] && (after[r].x < 0.5 * before[r].x);
-}
-
-// back substitution H(0:k,0:k) y = g(0:k) per RHS
+// back substitution H(0:k,0:k) y = g(0:k), then the update coefficients y_i / n_i
 __global__ void trisolve_kernel(GState s, int R) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const int m = s.m, k = s.k[r];
     const double2* H = s.H + (long long)r * (m + 1) * m;
     const double2* g = s.g + r * (m + 1);
+    const double* n = s.nrm + (long long)r * (m + 1);
     double2* y = s.y + r * m;
     for (int i = k - 1; i >= 0; --i) {
         double2 acc = g[i];
         for (int q = i + 1; q < k; ++q) {
-            double2 h = H[i * m + q], yv = y[q];
-            acc.x -= h.x * yv.x - h.y * yv.y;
-            acc.y -= h.x * yv.y + h.y * yv.x;
+            const double2 hq = H[i * m + q], yv = y[q];
+            acc.x -= hq.x * yv.x - hq.y * yv.y;
+            acc.y -= hq.x * yv.y + hq.y * yv.x;
         }
-        double2 d = H[i * m + i];
-        double dd = d.x * d.x + d.y * d.y;
+        const double2 d = H[i * m + i];
+        const double dd = d.x * d.x + d.y * d.y;
         y[i] = dd > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
                       : make_double2(0, 0);
     }
-}
-
-}  // namespace
-
-
-namespace {
-
-// H[r][i][j] += c[r][i] for the right-hand sides that took a second Gram-Schmidt pass
-__global__ void add_col_kernel(double2* H, long long rs, long long is, const double2* __restrict__ c, long long cs,
-                               int nvec, const int* __restrict__ flag, int R) {
-    const int r = blockIdx.x;
-    if (r >= R || !flag[r]) return;
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-        double2* o = H + r * rs + i * is;
-        double2 v = c[r * cs + i];
-        o->x += v.x;
-        o->y += v.y;
+    for (int i = 0; i < k; ++i) {
+        const double ni = n[i];
+        y[i] = make_double2(y[i].x / ni, y[i].y / ni);
     }
 }
 
-__global__ void check_kernel(const double2* __restrict__ rn2, const double2* __restrict__ bn2, double tol,
+// residual check of the outer loop; converged right-hand sides stay idle in later cycles
+__global__ void check_kernel(const double* __restrict__ rn2, const double* __restrict__ bn2, double tol,
                              double eta_min, double* target, int* done, double* rel, int R) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    const double rn = sqrt(fmax(rn2[r].x, 0.0)), bn = sqrt(fmax(bn2[r].x, 0.0));
+    const double rn = sqrt(fmax(rn2[r], 0.0)), bn = sqrt(fmax(bn2[r], 0.0));
     const double rr = bn > 0 ? rn / bn : 0.0;
     rel[r] = rr;
     done[r] = rr <= tol;
-    // inner target: the absolute residual this cycle must reach; converged right-hand sides stay idle
     target[r] = rr <= tol ? INFINITY : fmax(eta_min * rn, 0.5 * tol * bn);
 }
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Solver {
     vie_handle* h;
@@ -334,68 +509,82 @@ struct Solver {
     int R, m;
     long long n;
     int nblk;
-    double2* partial;
+    double2* partial;  // [R][nblk][m+2]
+    double* npart;     // [R][nblk]
     GState gs;
-    int* reflag;
-    double2* nrm_before;
-    double2* nrm_after;
-    double2* ctmp;  // [R][m+1]
-    int* host_i;    // pinned scratch
 
-    template <typename VC, typename WC>
-    int dots(const VC* V, long long vstride, const WC* w, int nvec, double2* out, long long rs, long long is,
-             int accumulate, const int* flag) {
-        dim3 g1(nblk, R);
-        VIE_KLAUNCH("dots", st, dots_kernel<VC, WC><<<g1, kThreads, 0, st>>>(V, vstride, w, n, nvec, partial, nblk, flag));
-        dim3 g2(nvec, R);
-        VIE_KLAUNCH("finalize", st, finalize_kernel<<<g2, kThreads, 0, st>>>(partial, nblk, nvec, out, rs, is, accumulate, flag));
+    template <typename VC>
+    int dots(const VC* U, long long ustride, const VC* w, int nvec, const int* flag) {
+        const dim3 g1(nblk, R);
+        VIE_KLAUNCH("gs_dots", st,
+                    gs_dots_kernel<VC><<<g1, kThreads, 0, st>>>(U, ustride, w, n, nvec, partial, nblk, flag));
+        const dim3 g2(nvec + 1, R);
+        VIE_KLAUNCH("gs_finalize", st,
+                    finalize2_kernel<<<g2, kThreads, 0, st>>>(partial, nblk, nvec + 1, gs.D, m + 2, flag));
         VIE_CHECK_LAUNCH();
         return VIE_OK;
     }
-    template <typename C>
-    int norm2(const C* w, double2* out, const int* flag) {
-        return dots<C, C>(w, 0, w, 1, out, 1, 0, 0, flag);
+    template <typename VC>
+    int update(const VC* U, long long ustride, VC* w, int nvec, const int* flag) {
+        const dim3 g1(nblk, R);
+        VIE_KLAUNCH("gs_update", st,
+                    gs_update_kernel<VC><<<g1, kThreads, 0, st>>>(U, ustride, w, n, nvec, gs.coef, m + 1, gs.scale,
+                                                                 npart, nblk, flag));
+        VIE_KLAUNCH("gs_norm", st, finalize1_kernel<<<R, kThreads, 0, st>>>(npart, nblk, gs.F, flag));
+        VIE_CHECK_LAUNCH();
+        return VIE_OK;
+    }
+    int nblk64() const { return (int)((n + kThreads * Prec<double2>::K - 1) / (kThreads * Prec<double2>::K)); }
+    // squared 2-norm per right-hand side of an FP64 vector batch into out[R]
+    int norm2_64(const double2* v, double* out) {
+        const int nb = nblk64();
+        const dim3 g1(nb, R);
+        VIE_KLAUNCH("norm64", st,
+                    gs_dots_kernel<double2><<<g1, kThreads, 0, st>>>(nullptr, 0, v, n, 0, partial, nb, nullptr));
+        const dim3 g2(1, R);
+        VIE_KLAUNCH("norm64_finalize", st,
+                    finalize2_kernel<<<g2, kThreads, 0, st>>>(partial, nb, 1, gs.D, m + 2, nullptr));
+        VIE_KLAUNCH("norm64_copy", st, copy_norm_kernel<<<(R + 127) / 128, 128, 0, st>>>(gs.D, m + 2, out, R));
+        VIE_CHECK_LAUNCH();
+        return VIE_OK;
     }
 };
 
 template <typename VC>
-int run_cycle(Solver& S, VC* V, VC* W, double2* x64, const double2* r64, int precision, int* it_rhs, int* mv_count) {
+int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* rn2, int precision, int* it_rhs,
+              int* mv_count, int* host_i) {
     vie_handle* h = S.h;
     const int R = S.R, m = S.m;
-    const long long n = S.n, vstride = (long long)R * n;
+    const long long n = S.n, ustride = (long long)R * n;
     cudaStream_t st = S.st;
+    VIE_KLAUNCH("cycle_init", st, cycle_init_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R, rn2));
     const dim3 ge((unsigned)((n + 255) / 256), R);
-    const long long hrs = (long long)(m + 1) * m;
-    VIE_TRY(S.norm2(r64, S.gs.tmp, nullptr));
-    VIE_KLAUNCH("cycle_init", st, cycle_init_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R, S.gs.tmp));
-    VIE_KLAUNCH("scale", st, scale_kernel<double2, VC><<<ge, 256, 0, st>>>(r64, V, n, S.gs.sc));
+    VIE_KLAUNCH("basis_init", st, scale_from64_kernel<VC><<<ge, 256, 0, st>>>(r64, U, n, S.gs.scale));
     VIE_CHECK_LAUNCH();
+    const unsigned gr = (unsigned)((R + 127) / 128);
     for (int j = 0; j < m; ++j) {
         VIE_KLAUNCH("count_active", st, count_active_kernel<<<1, 1, 0, st>>>(S.gs.active, R, S.gs.nactive));
-        VIE_CUDA(cudaMemcpyAsync(S.host_i, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaMemcpyAsync(host_i, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
         VIE_CUDA(cudaStreamSynchronize(st));
-        if (*S.host_i == 0) break;
-        VC* vj = V + j * vstride;
-        VIE_TRY(matvec_device(h, R, vj, W, precision, VIE_OP_PA, st));
+        if (*host_i == 0) break;
+        VC* uj = U + j * ustride;
+        VC* w = U + (j + 1) * ustride;
+        VIE_TRY(matvec_device(h, R, uj, w, precision, VIE_OP_PA, st));
         ++*mv_count;
-        // first classical Gram-Schmidt pass: H[:, j] = V^H w ; w -= V H[:, j]
-        VIE_TRY(S.norm2(W, S.nrm_before, S.gs.active));
-        VIE_TRY((S.dots<VC, VC>(V, vstride, W, j + 1, S.gs.H + j, hrs, m, 0, S.gs.active)));
-        VIE_KLAUNCH("update", st, update_kernel<VC, VC><<<ge, 256, 0, st>>>(V, vstride, W, n, j + 1, S.gs.H + j, hrs, m, S.gs.active));
-        VIE_CHECK_LAUNCH();
-        VIE_TRY(S.norm2(W, S.nrm_after, S.gs.active));
-        // second pass only where the norm dropped below 1/sqrt2 of its value
-        VIE_KLAUNCH("reorth_flag", st, reorth_flag_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.nrm_before, S.nrm_after, S.gs.active, S.reflag, R));
-        VIE_TRY((S.dots<VC, VC>(V, vstride, W, j + 1, S.ctmp, m + 1, 1, 0, S.reflag)));
-        VIE_KLAUNCH("update", st, update_kernel<VC, VC><<<ge, 256, 0, st>>>(V, vstride, W, n, j + 1, S.ctmp, m + 1, 1, S.reflag));
-        VIE_KLAUNCH("add_col", st, add_col_kernel<<<R, 64, 0, st>>>(S.gs.H + j, hrs, m, S.ctmp, m + 1, j + 1, S.reflag, R));
-        VIE_TRY(S.norm2(W, S.nrm_after, S.reflag));
-        VIE_KLAUNCH("givens", st, givens_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R, j, S.nrm_after));
-        VIE_KLAUNCH("scale", st, scale_kernel<VC, VC><<<ge, 256, 0, st>>>(W, V + (j + 1) * vstride, n, S.gs.sc));
+        VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
+        VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
+        VIE_TRY(S.update<VC>(U, ustride, w, j + 1, S.gs.active));
+        VIE_KLAUNCH("arnoldi_reorth", st, reorth_kernel<<<gr, 128, 0, st>>>(S.gs, R));
+        VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.reflag));
+        VIE_KLAUNCH("arnoldi_coef", st, coef2_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
+        VIE_TRY(S.update<VC>(U, ustride, w, j + 1, S.gs.reflag));
+        VIE_KLAUNCH("givens", st, givens_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
         VIE_CHECK_LAUNCH();
     }
-    VIE_KLAUNCH("trisolve", st, trisolve_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R));
-    VIE_KLAUNCH("xupdate", st, xupdate_kernel<VC><<<ge, 256, 0, st>>>(V, vstride, x64, n, S.gs.y, m, S.gs.k));
+    VIE_KLAUNCH("trisolve", st, trisolve_kernel<<<gr, 128, 0, st>>>(S.gs, R));
+    const dim3 gx((unsigned)((n + kThreads * Prec<VC>::K - 1) / (kThreads * Prec<VC>::K)), R);
+    VIE_KLAUNCH("solution_update", st,
+                xupdate_kernel<VC><<<gx, kThreads, 0, st>>>(U, ustride, x64, n, S.gs.y, m, S.gs.k));
     VIE_CHECK_LAUNCH();
     std::vector<int> k(R);
     VIE_CUDA(cudaMemcpyAsync(k.data(), S.gs.k, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
@@ -404,46 +593,52 @@ int run_cycle(Solver& S, VC* V, VC* W, double2* x64, const double2* r64, int pre
     return VIE_OK;
 }
 
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
 }  // namespace
 
 int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol, int m, int maxit, int mode,
-                 int use_guess, vie_solve_info* info, cudaStream_t st) {
+                 int flags, vie_solve_info* info, cudaStream_t st) {
+    if (m + 2 > kMaxV) {
+        set_error("restart above 128 is not supported");
+        return VIE_EINVAL;
+    }
     const long long n = 12LL * (long long)h->nv;
     const bool mixed = mode == VIE_SOLVE_FP32_REFINE;
     const size_t vc = mixed ? sizeof(float2) : sizeof(double2);
-    const int nblk = (int)((n + kSeg - 1) / kSeg);
-    // carve the workspace
+    const int kpt = mixed ? Prec<float2>::K : Prec<double2>::K;
+    const int nblk = (int)((n + kThreads * kpt - 1) / (kThreads * kpt));
+    const int nblk64 = (int)((n + kThreads * Prec<double2>::K - 1) / (kThreads * Prec<double2>::K));
+    const int nbmax = nblk > nblk64 ? nblk : nblk64;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off += align256(bytes);
         return o;
     };
-    const size_t oV = take(vc * (size_t)(m + 1) * R * n);
-    const size_t oW = take(vc * (size_t)R * n);
-    const size_t oR = take(sizeof(double2) * R * n);
-    const size_t oBt = take(sizeof(double2) * R * n);
-    const size_t oT = take(sizeof(double2) * R * n);
-    const size_t oPart = take(sizeof(double2) * (size_t)R * nblk * (m + 1));
+    const size_t oU = take(vc * (size_t)(m + 1) * R * n);
+    const size_t oR = take(sizeof(double2) * (size_t)R * n);
+    const size_t oBt = take(sizeof(double2) * (size_t)R * n);
+    const size_t oT = take(sizeof(double2) * (size_t)R * n);
+    const size_t oPart = take(sizeof(double2) * (size_t)R * nbmax * (m + 2));
+    const size_t oNp = take(sizeof(double) * (size_t)R * nbmax);
     const size_t oH = take(sizeof(double2) * (size_t)R * (m + 1) * m);
     const size_t oCs = take(sizeof(double2) * (size_t)R * m);
     const size_t oSn = take(sizeof(double2) * (size_t)R * m);
     const size_t oG = take(sizeof(double2) * (size_t)R * (m + 1));
     const size_t oY = take(sizeof(double2) * (size_t)R * m);
-    const size_t oTmp = take(sizeof(double2) * R);
+    const size_t oD = take(sizeof(double2) * (size_t)R * (m + 2));
+    const size_t oCo = take(sizeof(double2) * (size_t)R * (m + 1));
+    const size_t oNrm = take(sizeof(double) * (size_t)R * (m + 1));
     const size_t oBeta = take(sizeof(double) * R);
     const size_t oTarget = take(sizeof(double) * R);
-    const size_t oSc = take(sizeof(double) * R);
+    const size_t oScale = take(sizeof(double) * R);
+    const size_t oSigma = take(sizeof(double) * R);
+    const size_t oF = take(sizeof(double) * R);
     const size_t oAct = take(sizeof(int) * R);
+    const size_t oRe = take(sizeof(int) * R);
     const size_t oK = take(sizeof(int) * R);
     const size_t oNact = take(sizeof(int));
-    const size_t oRe = take(sizeof(int) * R);
-    const size_t oNb = take(sizeof(double2) * R);
-    const size_t oNa = take(sizeof(double2) * R);
-    const size_t oC = take(sizeof(double2) * (size_t)R * (m + 1));
-    const size_t oBn = take(sizeof(double2) * R);
+    const size_t oBn = take(sizeof(double) * R);
+    const size_t oRn = take(sizeof(double) * R);
     const size_t oDone = take(sizeof(int) * R);
     const size_t oRel = take(sizeof(double) * R);
     VIE_TRY(ws_reserve(h, h->solve_ws, off));
@@ -456,32 +651,34 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     S.n = n;
     S.nblk = nblk;
     S.partial = reinterpret_cast<double2*>(base + oPart);
+    S.npart = reinterpret_cast<double*>(base + oNp);
+    S.gs.m = m;
     S.gs.H = reinterpret_cast<double2*>(base + oH);
     S.gs.cs = reinterpret_cast<double2*>(base + oCs);
     S.gs.sn = reinterpret_cast<double2*>(base + oSn);
     S.gs.g = reinterpret_cast<double2*>(base + oG);
     S.gs.y = reinterpret_cast<double2*>(base + oY);
-    S.gs.tmp = reinterpret_cast<double2*>(base + oTmp);
+    S.gs.D = reinterpret_cast<double2*>(base + oD);
+    S.gs.coef = reinterpret_cast<double2*>(base + oCo);
+    S.gs.nrm = reinterpret_cast<double*>(base + oNrm);
     S.gs.beta = reinterpret_cast<double*>(base + oBeta);
     S.gs.target = reinterpret_cast<double*>(base + oTarget);
-    S.gs.sc = reinterpret_cast<double*>(base + oSc);
+    S.gs.scale = reinterpret_cast<double*>(base + oScale);
+    S.gs.sigma = reinterpret_cast<double*>(base + oSigma);
+    S.gs.F = reinterpret_cast<double*>(base + oF);
     S.gs.active = reinterpret_cast<int*>(base + oAct);
+    S.gs.reflag = reinterpret_cast<int*>(base + oRe);
     S.gs.k = reinterpret_cast<int*>(base + oK);
     S.gs.nactive = reinterpret_cast<int*>(base + oNact);
-    S.gs.m = m;
-    S.reflag = reinterpret_cast<int*>(base + oRe);
-    S.nrm_before = reinterpret_cast<double2*>(base + oNb);
-    S.nrm_after = reinterpret_cast<double2*>(base + oNa);
-    S.ctmp = reinterpret_cast<double2*>(base + oC);
     double2* r64 = reinterpret_cast<double2*>(base + oR);
     double2* bt = reinterpret_cast<double2*>(base + oBt);
     double2* t64 = reinterpret_cast<double2*>(base + oT);
-    double2* bn2 = reinterpret_cast<double2*>(base + oBn);
+    double* bn2 = reinterpret_cast<double*>(base + oBn);
+    double* rn2 = reinterpret_cast<double*>(base + oRn);
     int* done = reinterpret_cast<int*>(base + oDone);
     double* rel = reinterpret_cast<double*>(base + oRel);
     int* pinned = nullptr;
     VIE_CUDA(cudaMallocHost(&pinned, sizeof(int) * 4));
-    S.host_i = pinned;
     struct PinGuard {
         int* p;
         ~PinGuard() { cudaFreeHost(p); }
@@ -489,60 +686,65 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
 
     const long long total = (long long)R * n;
     const unsigned gt = (unsigned)((total + 255) / 256);
+    const unsigned gr = (unsigned)((R + 127) / 128);
     const double dV = h->dx * h->dy * h->dz;
-    VIE_KLAUNCH("precond_rhs", st, precond_rhs_kernel<<<gt, 256, 0, st>>>(b, h->ieps64, bt, (long long)h->nv, R, dV, dV / 12.0));
+    VIE_KLAUNCH("precond_rhs", st,
+                precond_rhs_kernel<<<gt, 256, 0, st>>>(b, h->ieps64, bt, (long long)h->nv, R, dV, dV / 12.0));
     VIE_CHECK_LAUNCH();
-    VIE_TRY(S.norm2(bt, bn2, nullptr));
-    if (!use_guess) VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * total, st));
+    VIE_TRY(S.norm2_64(bt, bn2));
+    if (!(flags & 1)) VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * total, st));
 
-    std::vector<int> it_rhs(R, 0);
+    std::vector<int> it_rhs(R, 0), hdone(R, 0);
+    std::vector<double> hrel(R, 0.0), htrue(R, -1.0);
     int mv64 = 0, mv32 = 0, sweeps = 0;
-    std::vector<int> hdone(R, 0);
     const double eta_min = mixed ? 2e-5 : 0.0;
-    bool x_is_zero = !use_guess;
-    for (int cyc = 0; cyc < maxit; ++cyc) {
+    bool x_is_zero = !(flags & 1);
+    bool all = false;
+    auto residual = [&]() -> int {
         if (x_is_zero) {
             VIE_CUDA(cudaMemcpyAsync(r64, bt, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
         } else {
             VIE_TRY(matvec_device(h, R, x, t64, VIE_FP64, VIE_OP_PA, st));
             ++mv64;
-            VIE_KLAUNCH("sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
+            VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
         }
-        VIE_TRY(S.norm2(r64, S.gs.tmp, nullptr));
-        VIE_KLAUNCH("check", st, check_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs.tmp, bn2, tol, eta_min, S.gs.target, done, rel, R));
+        VIE_TRY(S.norm2_64(r64, rn2));
+        VIE_KLAUNCH("residual_check", st,
+                    check_kernel<<<gr, 128, 0, st>>>(rn2, bn2, tol, eta_min, S.gs.target, done, rel, R));
         VIE_CHECK_LAUNCH();
         VIE_CUDA(cudaMemcpyAsync(hdone.data(), done, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaMemcpyAsync(hrel.data(), rel, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         VIE_CUDA(cudaStreamSynchronize(st));
-        bool all = true;
+        all = true;
         for (int r = 0; r < R; ++r) all = all && hdone[r];
+        return VIE_OK;
+    };
+    for (int cyc = 0; cyc < maxit; ++cyc) {
+        VIE_TRY(residual());
         if (all) break;
         if (mixed) {
-            float2* V = reinterpret_cast<float2*>(base + oV);
-            float2* W = reinterpret_cast<float2*>(base + oW);
-            VIE_TRY(run_cycle<float2>(S, V, W, x, r64, VIE_FP32, it_rhs.data(), &mv32));
+            VIE_TRY(run_cycle<float2>(S, reinterpret_cast<float2*>(base + oU), x, r64, rn2, VIE_FP32, it_rhs.data(),
+                                      &mv32, pinned));
             ++sweeps;
         } else {
-            double2* V = reinterpret_cast<double2*>(base + oV);
-            double2* W = reinterpret_cast<double2*>(base + oW);
-            VIE_TRY(run_cycle<double2>(S, V, W, x, r64, VIE_FP64, it_rhs.data(), &mv64));
+            VIE_TRY(run_cycle<double2>(S, reinterpret_cast<double2*>(base + oU), x, r64, rn2, VIE_FP64,
+                                       it_rhs.data(), &mv64, pinned));
         }
         x_is_zero = false;
     }
-    // final residuals in FP64: preconditioned and unpreconditioned
-    std::vector<double> hrel(R), htrue(R);
-    {
-        VIE_TRY(matvec_device(h, R, x, t64, VIE_FP64, VIE_OP_PA, st));
-        VIE_KLAUNCH("sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
-        VIE_TRY(S.norm2(r64, S.gs.tmp, nullptr));
-        VIE_KLAUNCH("check", st, check_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs.tmp, bn2, tol, eta_min, S.gs.target, done, rel, R));
-        VIE_CUDA(cudaMemcpyAsync(hrel.data(), rel, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    if (!all) VIE_TRY(residual());  // residual of the last iterate when the cycle cap was hit
+    if (flags & 2) {
+        // unpreconditioned residual ||b - A x|| / ||b||
         VIE_TRY(matvec_device(h, R, x, t64, VIE_FP64, VIE_OP_A, st));
-        VIE_KLAUNCH("sub", st, sub_kernel<<<gt, 256, 0, st>>>(b, t64, r64, total));
-        VIE_TRY(S.norm2(r64, S.gs.tmp, nullptr));
-        VIE_TRY(S.norm2(b, bn2, nullptr));
-        VIE_KLAUNCH("check", st, check_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs.tmp, bn2, tol, eta_min, S.gs.target, done, rel, R));
-        VIE_CUDA(cudaMemcpyAsync(htrue.data(), rel, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        ++mv64;
+        VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(b, t64, r64, total));
+        VIE_TRY(S.norm2_64(r64, rn2));
+        VIE_TRY(S.norm2_64(b, bn2));
+        std::vector<double> a(R), c(R);
+        VIE_CUDA(cudaMemcpyAsync(a.data(), rn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaMemcpyAsync(c.data(), bn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         VIE_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r) htrue[r] = c[r] > 0 ? std::sqrt(a[r] / c[r]) : 0.0;
     }
     int rc = VIE_OK;
     for (int r = 0; r < R; ++r) {
@@ -551,7 +753,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         if (info) {
             info[r].converged = conv;
             info[r].iterations = it_rhs[r];
-            info[r].fp64_matvecs = mv64 + 2;
+            info[r].fp64_matvecs = mv64;
             info[r].fp32_matvecs = mv32;
             info[r].refinements = sweeps;
             info[r].resid = hrel[r];
@@ -559,4 +761,22 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         }
     }
     return rc;
+}
+
+int solve_device_bytes(double out[3], bool reset) {
+    unsigned long long v[3] = {0, 0, 0};
+    if (cudaMemcpyFromSymbol(v, g_gs_bytes, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        out[0] = out[1] = out[2] = 0;
+        return VIE_EDEVICE;
+    }
+    for (int i = 0; i < 3; ++i) out[i] = (double)v[i];
+    if (reset) {
+        const unsigned long long z[3] = {0, 0, 0};
+        if (cudaMemcpyToSymbol(g_gs_bytes, z, sizeof(z)) != cudaSuccess) {
+            cudaGetLastError();
+            return VIE_EDEVICE;
+        }
+    }
+    return VIE_OK;
 }

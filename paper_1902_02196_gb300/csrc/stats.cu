@@ -11,6 +11,7 @@ namespace {
 struct Entry {
     long long launches = 0;
     double ms = 0.0;
+    double bytes = 0.0;
 };
 struct Pending {
     std::string name;
@@ -36,10 +37,13 @@ void drain_locked() {
 }
 }  // namespace
 
-LaunchScope::LaunchScope(const char* n, cudaStream_t s) : name(n), stream(s), timed(false), ev0(nullptr), ev1(nullptr) {
+LaunchScope::LaunchScope(const char* n, cudaStream_t s, double alg_bytes)
+    : name(n), stream(s), timed(false), ev0(nullptr), ev1(nullptr) {
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_total;
-    ++g_entries[name].launches;
+    Entry& e = g_entries[name];
+    ++e.launches;
+    e.bytes += alg_bytes;
     if (!g_timing) return;
     if (!g_pool.empty()) {
         ev0 = g_pool.back().first;
@@ -66,16 +70,24 @@ extern "C" {
 int vie_stats_reset(int enable_timing) {
     std::lock_guard<std::mutex> lk(g_mu);
     drain_locked();
+    double dummy[3];
+    solve_device_bytes(dummy, true);
     g_entries.clear();
     g_total = 0;
     g_timing = enable_timing != 0;
     return VIE_OK;
 }
 
-int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, int* n_entries,
+int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, double* bytes, int* n_entries,
                    long long* total_launches) {
     std::lock_guard<std::mutex> lk(g_mu);
     drain_locked();
+    double dev[3] = {0, 0, 0};
+    if (solve_device_bytes(dev, true) == VIE_OK) {
+        const char* nm[3] = {"gs_dots", "gs_update", "solution_update"};
+        for (int i = 0; i < 3; ++i)
+            if (g_entries.count(nm[i])) g_entries[nm[i]].bytes += dev[i];
+    }
     int i = 0;
     for (auto& kv : g_entries) {
         if (i >= max_entries) break;
@@ -85,6 +97,7 @@ int vie_stats_read(int max_entries, char* names, long long* launches, double* ms
         }
         if (launches) launches[i] = kv.second.launches;
         if (ms) ms[i] = kv.second.ms;
+        if (bytes) bytes[i] = kv.second.bytes;
         ++i;
     }
     if (n_entries) *n_entries = i;
