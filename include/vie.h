@@ -110,6 +110,35 @@ void vie_destroy(vie_handle* h);
 int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream);
 
 /*
+ * vie_matvec_noalloc -- the same operator as vie_matvec, for callers that cannot
+ * allocate GPU memory at call time: code that hands all device memory to its
+ * own pool at start-up, loops that must not stall on the device-wide
+ * synchronisation an allocation can cause, or runtimes with a fixed memory
+ * budget.  The paper has no counterpart; this is an interface choice only.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch (the spectrum buffers) is one static device array of 64 MiB
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  A call that would need more scratch
+ * (roughly nrhs * 12 * nz * L_y * L_x complex values, plus nrhs * 12 * nz *
+ * ny * L_x on the FP64 path) returns VIE_EINVAL without doing anything: use
+ * fewer right-hand sides per call, or vie_matvec.
+ *   h, nrhs, precision, op : as for vie_matvec
+ *   x, y                   : device memory only (host buffers would need
+ *                            staging memory); VIE_EINVAL otherwise
+ *   stream                 : cudaStream_t as void*, NULL = the handle's stream
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  The current device must be the handle's device.
+ * All calls share the one array, and it keeps whatever the last call left in
+ * it; no part of it needs to start at zero, since each call writes every
+ * element it reads before reading it.  Calls whose work overlaps on the GPU
+ * (on different streams, or from different host threads) race on the array:
+ * order them on one stream or serialise them.
+ */
+int vie_matvec_noalloc(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream);
+
+/*
  * vie_rhs_planewave -- tested incident field of e_inc = pol exp(-i k0 dir.r)
  * (Eq. 27, Eq. 30; Section V-A uses pol = x, dir = z) in closed form, and the
  * right-hand side b = c_e chi e_inc (Eq. 31).

@@ -25,7 +25,7 @@ VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
 EXPORTS = (
     "vie_setup", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
     "vie_fields", "vie_green_toeplitz", "vie_info", "vie_strerror", "vie_last_error",
-    "vie_stats_reset", "vie_stats_read",
+    "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc",
 )
 
 
@@ -73,6 +73,7 @@ def _lib():
     lib.vie_destroy.argtypes = [P]
     lib.vie_destroy.restype = None
     lib.vie_matvec.argtypes = [P, I, P, P, I, I, P]
+    lib.vie_matvec_noalloc.argtypes = [P, I, P, P, I, I, P]
     lib.vie_rhs_planewave.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D), P, P, P]
     lib.vie_rhs_dipoles.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D), P, P, P]
     lib.vie_solve.argtypes = [P, I, P, P, D, I, I, I, I, ctypes.POINTER(vie_solve_info), P]
@@ -164,6 +165,13 @@ def vie_destroy(h):
 def vie_matvec(h, x, y, precision=VIE_FP64, op=VIE_OP_A, stream=None):
     return _check(_lib().vie_matvec(h.ptr, _nrhs(x, h.nv), _ptr(x), _ptr(y), int(precision), int(op), _stream(stream)),
                   "vie_matvec")
+
+
+def vie_matvec_noalloc(h, x, y, precision=VIE_FP64, op=VIE_OP_A, stream=None):
+    """vie_matvec for callers that cannot allocate GPU memory: device tensors only, scratch in a fixed
+    64 MiB static device array; oversized calls raise VieError (VIE_EINVAL)."""
+    return _check(_lib().vie_matvec_noalloc(h.ptr, _nrhs(x, h.nv), _ptr(x), _ptr(y), int(precision), int(op),
+                                            _stream(stream)), "vie_matvec_noalloc")
 
 
 def vie_rhs_planewave(h, pol, direction, e_inc=None, b=None, stream=None):

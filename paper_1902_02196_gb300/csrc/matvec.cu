@@ -14,6 +14,7 @@
 // The 1/(Lx Ly Lz) normalisation is folded into the stored Green tensor.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -362,13 +363,13 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
     return c * (w1 + w2) + 256;
 }
 
+// ws: scratch of at least matvec_workspace_bytes(h, R, precision) bytes (spectrum buffers W1, W2)
 template <typename T>
-static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s) {
+static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws) {
     using C = typename CT<T>::C;
     const int nx = h->nx, ny = h->ny, nz = h->nz, Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
-    VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, sizeof(T) == 8 ? VIE_FP64 : VIE_FP32)));
     const long long comps = (long long)R * 12 * nz;
-    C* W1 = reinterpret_cast<C*>(h->fft_ws.ptr);
+    C* W1 = reinterpret_cast<C*>(ws);
     C* W2 = W1 + comps * ny * Lx;
     MatvecEpi noepi{};
     const bool fused = sizeof(T) == 4 && fused_xy_ok(h);
@@ -447,8 +448,9 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
 }
 
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s) {
-    if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s);
-    return matvec_impl<float>(h, nrhs, x, y, op, s);
+    VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, nrhs, precision)));
+    if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr);
+    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr);
 }
 
 // Full forward 3-D FFT of [batch][Lz][Ly][Lx] complex double volumes, in place.
@@ -495,4 +497,84 @@ int twiddle_setup(vie_handle* h) {
     VIE_CUDA(cudaMemcpy(h->tw64, t64.data(), total * sizeof(double2), cudaMemcpyHostToDevice));
     VIE_CUDA(cudaMemcpy(h->tw32, t32.data(), total * sizeof(float2), cudaMemcpyHostToDevice));
     return VIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// vie_matvec_noalloc: the same matvec with its spectrum buffers in a fixed,
+// file-scope device array instead of handle-owned memory from cudaMalloc.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB, held by every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 256;
+void* g_noalloc_addr[kMaxDevices];  // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device, looked up once per device.
+int noalloc_scratch(void** out) {
+    int dev = -1;
+    VIE_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal out of range for the static scratch table");
+        return VIE_EDEVICE;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_error(std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e));
+            return VIE_EDEVICE;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return VIE_OK;
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" int vie_matvec_noalloc(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op,
+                                  void* stream) {
+    if (!h || !x || !y) {
+        set_error("NULL argument");
+        return VIE_EINVAL;
+    }
+    if (nrhs < 1 || (precision != VIE_FP64 && precision != VIE_FP32) ||
+        (op != VIE_OP_A && op != VIE_OP_PA && op != VIE_OP_NSCAT) || x == y) {
+        set_error("invalid nrhs, precision, operator, or x == y");
+        return VIE_EINVAL;
+    }
+    if (!on_device(x) || !on_device(y)) {
+        set_error("vie_matvec_noalloc needs device pointers for x and y (host buffers would need staging memory)");
+        return VIE_EINVAL;
+    }
+    int dev = -1;
+    VIE_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) {
+        set_error("the current device is not the handle's device");
+        return VIE_EINVAL;
+    }
+    const size_t need = matvec_workspace_bytes(h, nrhs, precision);
+    if (need > kNoAllocScratchBytes) {
+        set_error("vie_matvec_noalloc: this call needs " + std::to_string(need) +
+                  " bytes of scratch but the static scratch holds " + std::to_string(kNoAllocScratchBytes) +
+                  " bytes; pass fewer right-hand sides per call or use vie_matvec");
+        return VIE_EINVAL;
+    }
+    void* ws = nullptr;
+    VIE_TRY(noalloc_scratch(&ws));
+    cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : h->stream;
+    if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, ws);
+    return matvec_impl<float>(h, nrhs, x, y, op, s, ws);
 }
