@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
+                    help="profiling mode: set up the head64 workload and run N batched FP32 matvecs and one FP64 "
+                         "matvec (16 RHS), print their timings; the solve benchmark is not run")
     return ap.parse_args()
 
 
@@ -472,9 +475,58 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
 
 
+def run_matvec_only(args, local):
+    """Small, bounded command for kernel profiling: N FP32 matvecs + 1 FP64 matvec on head64, 16 RHS."""
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vie.build()
+    w = workload("head64")
+    g = w["grid"]
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), w["freq"], w["eps_real"], w["sigma"])
+    L, _ = vie.vie_info(h)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    shape = (NRHS, 12) + g.shape
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    x = torch.randn(shape, dtype=torch.complex64, device=dev, generator=gen)
+    y = torch.empty_like(x)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    vie.vie_stats_reset(1)
+    for _ in range(args.matvec_only):
+        a0.record(stream)
+        vie.vie_matvec(h, x, y, vie.VIE_FP32, vie.VIE_OP_PA, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        times.append(a0.elapsed_time(a1))
+    kernels = {k: [v[0], round(v[1] / max(v[0], 1), 4), round(v[2] / max(v[1], 1e-9) / 1e6, 1)]
+               for k, v in vie.vie_stats_read()[1].items()}
+    vie.vie_stats_reset(0)
+    x64 = x.to(torch.complex128)
+    y64 = torch.empty_like(x64)
+    a0.record(stream)
+    vie.vie_matvec(h, x64, y64, vie.VIE_FP64, vie.VIE_OP_PA, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    b = matvec_alg_bytes((g.nx, g.ny, g.nz), L, NRHS, 8)
+    print(json.dumps(dict(mode="matvec-only", workload="head64, 16 RHS", fp32_ms=times,
+                          fp32_alg_gbs=b / (min(times) / 1000) / 1e9, fp64_ms=a0.elapsed_time(a1),
+                          kernels_launches_ms_gbs=kernels)), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
+    if args.matvec_only:
+        run_matvec_only(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return

@@ -93,6 +93,8 @@ void release(vie_handle* h) {
     cudaFree(h->ieps32);
     cudaFree(h->green64);
     cudaFree(h->green32);
+    cudaFree(h->green32t);
+    cudaFree(h->colmap);
     cudaFree(h->tw64);
     cudaFree(h->tw32);
     cudaFree(h->toeplitz);

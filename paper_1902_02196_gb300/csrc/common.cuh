@@ -109,6 +109,11 @@ struct vie_handle {
     // layout [60][Oz][Oy][Ox]
     double2* green64;
     float2* green32;
+    // FP32 copy in the layout of the z pass of the FP32 three-kernel path: [Oy][Ox][Oz][60]
+    float2* green32t;
+    // stored column order of that path's spectrum: [Lx] kx per stored column, then [Lx]
+    // positions of those kx in the x transform's output order (square L <= 128 only, else null)
+    unsigned char* colmap;
     // twiddle tables exp(-2 pi i m / L) for L = 2^k, k = 1..11, concatenated at offset L
     double2* tw64;
     float2* tw32;

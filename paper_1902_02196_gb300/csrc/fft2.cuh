@@ -1,0 +1,174 @@
+// Two-pass FFT of lines held in shared memory, FP32, L = A * B with A, B in {2, 4, 8, 16}.
+//
+// With l = b + B a (input index) and k = k1 + A k2 (output index), the DFT factors as
+//   X[k1 + A k2] = sum_b wB^(b k2) [ w^(b k1) sum_a wA^(a k1) x[b + B a] ],   w = exp(-2 pi i / L),
+// so a forward transform is
+//   pass 1: for every b, an A-point DFT over a, times w^(b k1), written back to the
+//           positions it was read from (b + B k1);
+//   pass 2: for every k1, a B-point DFT over b, written back to the positions b + B k1
+//           it was read from, which then hold X[k1 + A k2] at position k2 + B k1.
+// Each thread owns the positions it reads, so a pass needs no barrier inside it and every
+// element makes two round trips through shared memory (a radix-4 Stockham FFT makes
+// log4 L).  The spectrum is left in this "transposed" order: kz sits at position
+// tpos(kz) = kz / A + B (kz % A).  The inverse transform runs the passes in the
+// opposite order with conjugate twiddles and takes the transposed order to natural order:
+//   pass 1: for every k1, a B-point inverse DFT over k2 (positions k2 + B k1), times
+//           w^-(b k1), written to positions b + B k1;
+//   pass 2: for every b, an A-point inverse DFT over k1, giving x[b + B a] at b + B a.
+// Small DFTs run in registers (decimation in time down to 4-point butterflies) with the
+// twiddles of 8 and 16 points written as exact constants (cos and sin of multiples of pi/8).
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace fft2 {
+
+constexpr float kC1 = 0.92387953251128674f;  // cos(pi/8)
+constexpr float kS1 = 0.38268343236508978f;  // sin(pi/8)
+constexpr float kC2 = 0.70710678118654752f;  // cos(pi/4)
+
+__device__ __forceinline__ float2 rot(float2 a, float c, float s) {  // a * (c + i s)
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <int N>
+struct DFT;
+template <>
+struct DFT<2> {
+    static __device__ __forceinline__ void run(float2* v, int) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <>
+struct DFT<4> {
+    static __device__ __forceinline__ void run(float2* v, int dir) { dft4(v[0], v[1], v[2], v[3], dir); }
+};
+template <>
+struct DFT<8> {
+    static __device__ __forceinline__ void run(float2* v, int dir) {
+        float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+        dft4(e[0], e[1], e[2], e[3], dir);
+        dft4(o[0], o[1], o[2], o[3], dir);
+        const float d = (float)dir;
+        o[1] = rot(o[1], kC2, d * kC2);
+        o[2] = cmul_i(o[2], dir);
+        o[3] = rot(o[3], -kC2, d * kC2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+template <>
+struct DFT<16> {
+    static __device__ __forceinline__ void run(float2* v, int dir) {
+        float2 e[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        DFT<8>::run(e, dir);
+        DFT<8>::run(o, dir);
+        const float d = (float)dir;
+        o[1] = rot(o[1], kC1, d * kS1);
+        o[2] = rot(o[2], kC2, d * kC2);
+        o[3] = rot(o[3], kS1, d * kC1);
+        o[4] = cmul_i(o[4], dir);
+        o[5] = rot(o[5], -kS1, d * kC1);
+        o[6] = rot(o[6], -kC2, d * kC2);
+        o[7] = rot(o[7], -kC1, d * kS1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 8] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// factorisation L = A * B used for each length (8 <= L <= 256)
+__host__ __device__ constexpr int split_a(int L) { return L <= 16 ? 4 : (L <= 64 ? 8 : 16); }
+template <int L>
+struct Split {
+    static_assert(L >= 8 && L <= 256 && (L & (L - 1)) == 0, "two-pass FFT lengths are 8..256");
+    static constexpr int A = split_a(L), B = L / A;
+};
+
+// position of frequency k in the transposed order left by the forward transform, and back
+__host__ __device__ constexpr int tpos(int L, int k) { return k / split_a(L) + (L / split_a(L)) * (k % split_a(L)); }
+__host__ __device__ constexpr int freq_at(int L, int p) { return p / (L / split_a(L)) + split_a(L) * (p % (L / split_a(L))); }
+
+// Forward transform of NL lines, natural order in (elements l >= nin taken as zero and
+// not read), transposed order out.  Line n starts at s + off(n); elements at stride ES.
+// tw[m] = exp(-2 pi i m / L).  Called by all NT threads; ends with a barrier.
+template <int L, int NT, class Off>
+__device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, const float2* tw, int nin) {
+    constexpr int A = Split<L>::A, B = Split<L>::B;
+    for (int t = threadIdx.x; t < NL * B; t += NT) {
+        const int n = t % NL, b = t / NL;
+        float2* ln = s + off(n);
+        float2 v[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            const int l = b + B * a;
+            v[a] = l < nin ? ln[l * ES] : make_float2(0.f, 0.f);
+        }
+        DFT<A>::run(v, -1);
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) ln[(b + B * k1) * ES] = v[k1];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NL * A; t += NT) {
+        const int n = t % NL, k1 = t / NL;
+        float2* ln = s + off(n) + B * k1 * ES;
+        float2 v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) v[b] = ln[b * ES];
+        DFT<B>::run(v, -1);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) ln[k2 * ES] = v[k2];
+    }
+    __syncthreads();
+}
+
+// Inverse (unnormalised) transform of NL lines, transposed order in, natural order out;
+// only outputs l < nout are written.  Called by all NT threads; ends with a barrier.
+template <int L, int NT, class Off>
+__device__ __forceinline__ void inverse(float2* s, int NL, Off off, int ES, const float2* tw, int nout) {
+    constexpr int A = Split<L>::A, B = Split<L>::B;
+    for (int t = threadIdx.x; t < NL * A; t += NT) {
+        const int n = t % NL, k1 = t / NL;
+        float2* ln = s + off(n) + B * k1 * ES;
+        float2 v[B];
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) v[k2] = ln[k2 * ES];
+        DFT<B>::run(v, +1);
+#pragma unroll
+        for (int b = 1; b < B; ++b) v[b] = cmul(v[b], cconj(tw[b * k1]));
+#pragma unroll
+        for (int b = 0; b < B; ++b) ln[b * ES] = v[b];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NL * B; t += NT) {
+        const int n = t % NL, b = t / NL;
+        float2* ln = s + off(n);
+        float2 v[A];
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) v[k1] = ln[(b + B * k1) * ES];
+        DFT<A>::run(v, +1);
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            const int l = b + B * a;
+            if (l < nout) ln[l * ES] = v[a];
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace fft2

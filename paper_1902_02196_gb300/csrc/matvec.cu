@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft2.cuh"
 
 // ---------------------------------------------------------------------------
 // Constant table: for each unique tensor t the (alpha, beta, sign) entries of the 12x12 block
@@ -122,8 +123,8 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
         for (int p = tid; p < L * TB; p += NT) {
             int tb = p % TB;
             int kz = p / TB;
+            if (kx0 + tb >= z.Lx) continue;
             int kx = kx0 + tb;
-            if (kx >= z.Lx) continue;
             int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
             int kzo = kz <= Lz / 2 ? kz : Lz - kz;
             unsigned mask = fy ^ (kx > z.Lx / 2 ? z.mx : 0u) ^ (kz > Lz / 2 ? z.mz : 0u);
@@ -151,49 +152,165 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
 }
 
 // ---------------------------------------------------------------------------
-// Fused plane kernels (FP32, Lx = Ly = L <= 128): a whole L x L plane of one
-// component grid in shared memory, so the x and y transforms cost one HBM pass.
-// Since L >= 2N - 1, at most L/2 rows are non-zero before the y transform and at
-// most L/2 rows are needed after the inverse one.
+// FP32 three-kernel path (Lx = Ly = L and Lz in 8..128): two-pass FFTs (fft2.cuh)
+// whose spectra stay in "transposed" order, so every element makes two round trips
+// through shared memory per 1-D transform.
+//
+// Spectrum layout W2 [R*12][Nz][Ly][Lx]: row py holds ky = freq_at(Ly, py); stored
+// column sc holds kx = colkx[sc].  The column order (built on the host) keeps mirror
+// pairs (kx, Lx - kx) side by side, 4 pairs to an 8-column tile, with the self-mirrored
+// columns 0 and Lx/2 in the last two slots; within every 16 stored columns the
+// positions of the x transform differ modulo 16, which keeps the column gathers
+// and scatters of the xy kernels free of shared-memory bank conflicts.
 // ---------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(512) xy_fwd_kernel(const float2* __restrict__ x, float2* __restrict__ w, int nx,
-                                                     int ny, const float2* __restrict__ twg) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* s = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = s + L * L;
-    const int tid = threadIdx.x;
-    for (int m = tid; m < L; m += 512) tw[m] = twg[m];
-    const long long p = blockIdx.x;  // plane (component, z)
-    const float2* src = x + p * (long long)ny * nx;
-    for (int idx = tid; idx < L * L; idx += 512) {
-        const int yy = idx / L, xx = idx % L;
-        float2 v = make_float2(0.f, 0.f);
-        if (yy < ny && xx < nx) v = src[yy * nx + xx];
-        s[idx] = v;
-    }
-    __syncthreads();
-    fft_smem<float2, L, L / 2, 1, 1, L, 512>(s, tw, -1);  // rows 0..L/2-1 along x
-    fft_smem<float2, L, 1, L, L, 0, 512>(s, tw, -1);      // L columns along y
-    float2* dst = w + p * (long long)L * L;
-    for (int idx = tid; idx < L * L; idx += 512) dst[idx] = s[idx];
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+constexpr int kXYThreads = 256;
+
 template <int L>
-__global__ void __launch_bounds__(512) xy_inv_kernel(const float2* __restrict__ w, float2* __restrict__ y,
-                                                     MatvecEpi epi, const float2* __restrict__ twg) {
+struct XYCfg {
+    static constexpr int H = L / 2;                // rows that are non-zero before / needed after the y transform
+    static constexpr int RS = L + 1;               // odd row stride of the x-transform buffer
+    static constexpr int CW = L < 32 ? L : 32;     // stored columns per y-transform chunk
+    static constexpr size_t smem = sizeof(float2) * (size_t)(L * CW + H * RS + L) + L;
+};
+
+// Forward: plane (r, alpha, z) of x [Ny][Nx] -> W2 plane [Ly][Lx] (transposed ky, stored kx).
+template <int L>
+__global__ void __launch_bounds__(kXYThreads, 2)
+    xy_fwd_kernel(const float2* __restrict__ x, float2* __restrict__ w, int nx, int ny,
+                  const unsigned char* __restrict__ cpos, const float2* __restrict__ twg) {
+    using Cfg = XYCfg<L>;
+    constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* s = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = s + L * L;
+    float2* ck = reinterpret_cast<float2*>(smem_raw);  // [L][CW] chunk of stored columns
+    float2* xr = ck + L * CW;                          // [H][RS] rows after the x transform
+    float2* tw = xr + Cfg::H * RS;
+    unsigned char* pos = reinterpret_cast<unsigned char*>(tw + L);
     const int tid = threadIdx.x;
-    for (int m = tid; m < L; m += 512) tw[m] = twg[m];
+    for (int m = tid; m < L; m += NT) {
+        tw[m] = twg[m];
+        pos[m] = cpos[m];
+    }
+    const long long p = blockIdx.x;
+    const float2* src = x + p * (long long)ny * nx;
+    for (int idx = tid; idx < ny * nx; idx += NT) cp_async8(xr + (idx / nx) * RS + idx % nx, src + idx);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    fft2::forward<L, NT>(xr, ny, [](int n) { return n * RS; }, 1, tw, nx);
+    float2* dst = w + p * (long long)L * L;
+#pragma unroll 1
+    for (int k = 0; k < L / CW; ++k) {
+        // y transform, pass 1: gather stored column k*CW + c from the x-transform rows
+        for (int t = tid; t < CW * B; t += NT) {
+            const int c = t % CW, b = t / CW;
+            const float2* col = xr + pos[k * CW + c];
+            float2 v[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) {
+                const int yy = b + B * a;
+                v[a] = yy < ny ? col[yy * RS] : make_float2(0.f, 0.f);
+            }
+            fft2::DFT<A>::run(v, -1);
+#pragma unroll
+            for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) ck[(b + B * k1) * CW + c] = v[k1];
+        }
+        __syncthreads();
+        for (int t = tid; t < CW * A; t += NT) {
+            const int c = t % CW, k1 = t / CW;
+            float2* ln = ck + B * k1 * CW + c;
+            float2 v[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) v[b] = ln[b * CW];
+            fft2::DFT<B>::run(v, -1);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) ln[k2 * CW] = v[k2];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < L * CW / 2; idx += NT) {
+            const int q = idx / (CW / 2), c2 = 2 * (idx % (CW / 2));
+            *reinterpret_cast<float4*>(dst + (long long)q * L + k * CW + c2) =
+                *reinterpret_cast<const float4*>(ck + q * CW + c2);
+        }
+        __syncthreads();
+    }
+}
+
+// Inverse: W2 plane -> y plane [Ny][Nx] with the material / Gram / preconditioner epilogue.
+template <int L>
+__global__ void __launch_bounds__(kXYThreads, 2)
+    xy_inv_kernel(const float2* __restrict__ w, float2* __restrict__ y, MatvecEpi epi,
+                  const unsigned char* __restrict__ cpos, const float2* __restrict__ twg) {
+    using Cfg = XYCfg<L>;
+    constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* ck = reinterpret_cast<float2*>(smem_raw);
+    float2* xr = ck + L * CW;
+    float2* tw = xr + Cfg::H * RS;
+    unsigned char* pos = reinterpret_cast<unsigned char*>(tw + L);
+    const int tid = threadIdx.x;
+    for (int m = tid; m < L; m += NT) {
+        tw[m] = twg[m];
+        pos[m] = cpos[m];
+    }
+    const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
     const long long p = blockIdx.x;  // plane (r * 12 + alpha) * nz + z
     const float2* src = w + p * (long long)L * L;
-    for (int idx = tid; idx < L * L; idx += 512) s[idx] = src[idx];
-    __syncthreads();
-    fft_smem<float2, L, 1, L, L, 0, 512>(s, tw, +1);      // L columns along y
-    fft_smem<float2, L, L / 2, 1, 1, L, 512>(s, tw, +1);  // rows 0..L/2-1 along x
-    const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
+#pragma unroll 1
+    for (int k = 0; k < L / CW; ++k) {
+        for (int idx = tid; idx < L * CW / 2; idx += NT) {
+            const int q = idx / (CW / 2), c2 = 2 * (idx % (CW / 2));
+            cp_async16(ck + q * CW + c2, src + (long long)q * L + k * CW + c2);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        // inverse y transform, pass 1 (in place in the chunk)
+        for (int t = tid; t < CW * A; t += NT) {
+            const int c = t % CW, k1 = t / CW;
+            float2* ln = ck + B * k1 * CW + c;
+            float2 v[B];
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) v[k2] = ln[k2 * CW];
+            fft2::DFT<B>::run(v, +1);
+#pragma unroll
+            for (int b = 1; b < B; ++b) v[b] = cmul(v[b], cconj(tw[b * k1]));
+#pragma unroll
+            for (int b = 0; b < B; ++b) ln[b * CW] = v[b];
+        }
+        __syncthreads();
+        // pass 2: rows y < Ny scattered to the x-transform buffer at the column's x position
+        for (int t = tid; t < CW * B; t += NT) {
+            const int c = t % CW, b = t / CW;
+            float2 v[A];
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) v[k1] = ck[(b + B * k1) * CW + c];
+            fft2::DFT<A>::run(v, +1);
+            float2* col = xr + pos[k * CW + c];
+#pragma unroll
+            for (int a = 0; a < A; ++a) {
+                const int yy = b + B * a;
+                if (yy < ny) col[yy * RS] = v[a];
+            }
+        }
+        __syncthreads();
+    }
+    fft2::inverse<L, NT>(xr, ny, [](int n) { return n * RS; }, 1, tw, nx);
     const int alpha = (int)((p / nz) % 12);
     const long long zoff = (p % nz) * (long long)ny * nx;
     const long long base = p * (long long)ny * nx;
@@ -201,20 +318,215 @@ __global__ void __launch_bounds__(512) xy_inv_kernel(const float2* __restrict__ 
     const float2* xin = reinterpret_cast<const float2*>(epi.x);
     const float2* c1 = reinterpret_cast<const float2*>(epi.c1);
     const float2* c2 = reinterpret_cast<const float2*>(epi.c2);
-    for (int idx = tid; idx < ny * nx; idx += 512) {
-        const int yy = idx / nx, xx = idx % nx;
-        float2 v = s[yy * L + xx];
-        const long long vox = zoff + idx;
+    for (int idx = tid; idx < ny * nx; idx += NT) {
+        float2 v = xr[(idx / nx) * RS + idx % nx];
         if (epi.op == VIE_OP_A) {
-            float2 xv = xin[base + idx];
-            v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[vox], v));
+            const float2 xv = xin[base + idx];
+            v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[zoff + idx], v));
         } else if (epi.op == VIE_OP_PA) {
-            float2 xv = xin[base + idx];
-            float2 t = cmul(c2[vox], v);
+            const float2 xv = xin[base + idx];
+            const float2 t = cmul(c2[zoff + idx], v);
             const float ig = 1.0f / gl;
-            v = csub(cmul(c1[vox], xv), mk(ig * t.x, ig * t.y));
+            v = csub(cmul(c1[zoff + idx], xv), mk(ig * t.x, ig * t.y));
         }
         y[base + idx] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass (FP32, on the spectrum of xy_fwd_kernel): one CTA per (row py, tile of 8
+// stored columns = 4 mirror pairs) loops over the right-hand sides; the next one's
+// column data arrives by cp.async while the current one is transformed.  The z
+// spectrum stays in transposed order between the forward and inverse transforms.
+// A thread of the block product owns one (column pair, kz mirror pair) item: it
+// loads the 60 Green values of the octant point once (480 contiguous bytes) and
+// applies them to the four frequency points (+-kx, +-kz) they serve.
+// ---------------------------------------------------------------------------
+struct ZFArgs {
+    float2* w;                    // spectrum [R*12][Nz][Ly][Lx], in place
+    const float2* green_t;        // [Oy][Ox][Oz][60]
+    const unsigned char* colkx;   // [Lx] kx of each stored column
+    int R, nz, Lx, Ly, Ox, Oy, Oz;
+    int ay, by;                   // split of Ly: row py holds ky = py / by + ay * (py % by)
+    unsigned mx, my, mz;
+};
+
+constexpr int kZThreads = 256;
+constexpr int kZTile = 8;
+
+template <int LZ>
+struct ZFCfg {
+    static constexpr int GS = LZ * kZTile + 8;  // component stride: 8 float2 of padding keep half-warps apart
+    static constexpr int BUF = 12 * GS;
+    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ);
+};
+
+// the 60 Green values of one octant point, streamed from the [..][60] layout
+__device__ __forceinline__ void load_green(float2* u, const float2* __restrict__ gp) {
+    const float4* g4 = reinterpret_cast<const float4*>(gp);
+#pragma unroll
+    for (int q = 0; q < 30; ++q) {
+        const float4 v = __ldg(g4 + q);
+        u[2 * q] = make_float2(v.x, v.y);
+        u[2 * q + 1] = make_float2(v.z, v.w);
+    }
+}
+
+__device__ __forceinline__ float2 flip(float2 v, unsigned mask, int a) { return ((mask >> a) & 1u) ? cneg(v) : v; }
+
+// y = B x at the two mirror columns c, c + 1 of one z position (float4 accesses); m0, m1
+// are the components whose sign flips at each column's reflected frequency point.
+__device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, int off, unsigned m0, unsigned m1) {
+    float2 x0[12], x1[12];
+#pragma unroll
+    for (int b = 0; b < 12; ++b) {
+        const float4 v = *reinterpret_cast<const float4*>(s + b * gs + off);
+        x0[b] = flip(make_float2(v.x, v.y), m0, b);
+        x1[b] = flip(make_float2(v.z, v.w), m1, b);
+    }
+#pragma unroll
+    for (int H = 0; H < 2; ++H) {
+        float2 a0[6], a1[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) a0[a] = a1[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 60; ++t) {
+#pragma unroll
+            for (int i = kBlock.start[t]; i < kBlock.start[t + 1]; ++i) {
+                const int a = kBlock.e[i].a, b = kBlock.e[i].b;
+                if (a / 6 != H) continue;
+                const float2 ut = kBlock.e[i].s > 0 ? u[t] : cneg(u[t]);
+                cfma(a0[a - 6 * H], ut, x0[b]);
+                cfma(a1[a - 6 * H], ut, x1[b]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            const float2 r0 = flip(a0[a], m0, a + 6 * H), r1 = flip(a1[a], m1, a + 6 * H);
+            *reinterpret_cast<float4*>(s + (a + 6 * H) * gs + off) = make_float4(r0.x, r0.y, r1.x, r1.y);
+        }
+    }
+}
+
+// y = B x at one column of one z position
+__device__ __forceinline__ void single_point(const float2* u, float2* s, int gs, int off, unsigned m) {
+    float2 xv[12], acc[12];
+#pragma unroll
+    for (int b = 0; b < 12; ++b) xv[b] = flip(s[b * gs + off], m, b);
+#pragma unroll
+    for (int a = 0; a < 12; ++a) acc[a] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < 60; ++t) {
+#pragma unroll
+        for (int i = kBlock.start[t]; i < kBlock.start[t + 1]; ++i) {
+            const int a = kBlock.e[i].a, b = kBlock.e[i].b;
+            cfma(acc[a], kBlock.e[i].s > 0 ? u[t] : cneg(u[t]), xv[b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 12; ++a) s[a * gs + off] = flip(acc[a], m, a);
+}
+
+template <int LZ>
+__global__ void __launch_bounds__(kZThreads, 1) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
+    constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = kZThreads, TB = kZTile;
+    constexpr int GS = ZFCfg<LZ>::GS, BUF = ZFCfg<LZ>::BUF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sb = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = sb + 2 * BUF;
+    const int tid = threadIdx.x;
+    for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
+    const int ntile = z.Lx / TB;
+    const int py = blockIdx.x / ntile, ct = blockIdx.x % ntile, sc0 = ct * TB;
+    const long long plane = (long long)z.Ly * z.Lx;
+    const int ky = py / z.by + z.ay * (py % z.by);
+    const int kyo = ky <= z.Ly / 2 ? ky : z.Ly - ky;
+    const unsigned fy = ky > z.Ly / 2 ? z.my : 0u;
+    const int nz = z.nz;
+
+    auto issue = [&](int r, float2* buf) {
+        const float2* base = z.w + (long long)r * 12 * nz * plane + (long long)py * z.Lx + sc0;
+        for (int idx = tid; idx < 12 * nz * (TB / 2); idx += NT) {
+            const int q = idx % (TB / 2), l = (idx / (TB / 2)) % nz, a = idx / ((TB / 2) * nz);
+            cp_async16(buf + a * GS + l * TB + 2 * q, base + ((long long)a * nz + l) * plane + 2 * q);
+        }
+        cp_async_commit();
+    };
+    auto line = [](int n) { return (n / TB) * GS + n % TB; };
+
+    // block-product item of this thread: column pair ci, kz item j (see the decoding below)
+    const int ci = tid & 3, j = tid >> 2;
+    const bool single = ct == ntile - 1 && ci == 3;  // columns 0 and Lx/2: own octant columns
+    const int kx0 = z.colkx[sc0 + 2 * ci], kx1 = z.colkx[sc0 + 2 * ci + 1];
+    const unsigned fx0 = kx0 > z.Lx / 2 ? z.mx : 0u, fx1 = kx1 > z.Lx / 2 ? z.mx : 0u;
+    // kz items, in transposed positions p = k2 + B k1 holding kz = k1 + A k2:
+    //   rows k1 = 1..A/2-1 with their mirrors in rows A - k1, then row A/2 (its own mirror),
+    //   then row 0 (k2 = 0 pairs kz = 0 with kz = LZ/2, each with its own octant point).
+    constexpr int NREG = (A / 2 - 1) * B;
+    int pa = -1, pb = -1, pc = -1;  // pa, pb share one octant point; pc (kz = LZ/2) has its own
+    if (j < NREG) {
+        const int k1 = 1 + j / B, k2 = j % B;
+        pa = k2 + B * k1;
+        pb = (B - 1 - k2) + B * (A - k1);
+    } else if (j < NREG + B / 2) {
+        const int k2 = j - NREG;
+        pa = k2 + B * (A / 2);
+        pb = (B - 1 - k2) + B * (A / 2);
+    } else if (j < LZ / 2) {
+        const int k2 = j - NREG - B / 2;
+        pa = k2;
+        if (k2 == 0)
+            pc = B / 2;
+        else
+            pb = B - k2;
+    }
+
+    issue(0, sb);
+#pragma unroll 1
+    for (int r = 0; r < z.R; ++r) {
+        float2* s = sb + (r & 1) * BUF;
+        if (r + 1 < z.R) {
+            issue(r + 1, sb + ((r + 1) & 1) * BUF);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        fft2::forward<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
+        if (pa >= 0) {
+#pragma unroll 1
+            for (int g = 0; g < (pc >= 0 ? 2 : 1); ++g) {
+#pragma unroll 1
+                for (int col = 0; col < (single ? 2 : 1); ++col) {
+                    const int pp0 = g ? pc : pa, pp1 = g ? -1 : pb;
+                    const int kz = fft2::freq_at(LZ, pp0);
+                    const int kzo = kz <= LZ / 2 ? kz : LZ - kz;
+                    const int kx = col ? kx1 : kx0;
+                    const int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
+                    float2 u[60];
+                    load_green(u, z.green_t + (((long long)kyo * z.Ox + kxo) * z.Oz + kzo) * 60);
+#pragma unroll 1
+                    for (int e = 0; e < 2; ++e) {
+                        const int pp = e ? pp1 : pp0;
+                        if (pp < 0) break;
+                        const unsigned fz = fft2::freq_at(LZ, pp) > LZ / 2 ? z.mz : 0u;
+                        if (!single)
+                            pair_point(u, s, GS, pp * TB + 2 * ci, fy ^ fz ^ fx0, fy ^ fz ^ fx1);
+                        else
+                            single_point(u, s, GS, pp * TB + 2 * ci + col, fy ^ fz ^ (col ? fx1 : fx0));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        fft2::inverse<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
+        float2* base = z.w + (long long)r * 12 * nz * plane + (long long)py * z.Lx + sc0;
+        for (int idx = tid; idx < 12 * nz * (TB / 2); idx += NT) {
+            const int q = idx % (TB / 2), l = (idx / (TB / 2)) % nz, a = idx / ((TB / 2) * nz);
+            *reinterpret_cast<float4*>(base + ((long long)a * nz + l) * plane + 2 * q) =
+                *reinterpret_cast<const float4*>(s + a * GS + l * TB + 2 * q);
+        }
+        __syncthreads();
     }
 }
 
@@ -315,32 +627,39 @@ static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z
     return VIE_EINVAL;
 }
 
+// The FP32 three-kernel path needs a square xy circulant of 8..128 and Lz of 8..128
+// (the column map is built at setup only for such grids).
+static bool fused_ok(const vie_handle* h) { return h->colmap && h->L[2] >= 8 && h->L[2] <= 128; }
+
 template <int L>
 static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
                        const MatvecEpi& e, cudaStream_t s) {
-    const size_t smem = sizeof(float2) * (size_t)(L * L + L);
+    constexpr size_t smem = XYCfg<L>::smem;
     static bool configured = false;
     if (!configured) {
         VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
+    if (planes > 0x7fffffffLL) {
+        set_error("xy transform grid too large");
+        return VIE_EINVAL;
+    }
+    const unsigned char* cpos = h->colmap + L;
     const double plane_in = (double)nx * ny, plane_full = (double)L * L;
     if (fwd)
         VIE_KLAUNCH_B("fft_xy_f32", s, 8.0 * planes * (plane_in + plane_full),
-                    xy_fwd_kernel<L><<<(unsigned)planes, 512, smem, s>>>((const float2*)in, (float2*)out, nx, ny,
-                                                                        h->tw32 + L));
+                      xy_fwd_kernel<L><<<(unsigned)planes, kXYThreads, smem, s>>>(
+                          (const float2*)in, (float2*)out, nx, ny, cpos, h->tw32 + L));
     else
         VIE_KLAUNCH_B("ifft_xy_epilogue_f32", s,
                       8.0 * (planes * (plane_full + plane_in * (e.op == VIE_OP_NSCAT ? 1 : 2)) +
                              (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0)),
-                    xy_inv_kernel<L><<<(unsigned)planes, 512, smem, s>>>((const float2*)in, (float2*)out, e,
-                                                                        h->tw32 + L));
+                      xy_inv_kernel<L><<<(unsigned)planes, kXYThreads, smem, s>>>(
+                          (const float2*)in, (float2*)out, e, cpos, h->tw32 + L));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
-
-static bool fused_xy_ok(const vie_handle* h) { return h->L[0] == h->L[1] && h->L[0] >= 8 && h->L[0] <= 128; }
 
 static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
                      const MatvecEpi& e, cudaStream_t s) {
@@ -351,7 +670,35 @@ static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, l
         case 64: return launch_xy_L<64>(fwd, h, in, out, planes, nx, ny, e, s);
         case 128: return launch_xy_L<128>(fwd, h, in, out, planes, nx, ny, e, s);
     }
-    set_error("fused xy path: unsupported length");
+    set_error("xy transform: unsupported length");
+    return VIE_EINVAL;
+}
+
+template <int LZ>
+static int launch_zf_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    constexpr size_t smem = ZFCfg<LZ>::smem;
+    static bool configured = false;
+    if (!configured) {
+        VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    const long long blocks = (long long)z.Ly * (z.Lx / kZTile);
+    const double bytes = 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
+    VIE_KLAUNCH_B("zpass_block_f32", s, bytes,
+                  zfused_kernel<LZ><<<(unsigned)blocks, kZThreads, smem, s>>>(z, h->tw32 + LZ));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+static int launch_zf(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    switch (h->L[2]) {
+        case 8: return launch_zf_L<8>(h, z, s);
+        case 16: return launch_zf_L<16>(h, z, s);
+        case 32: return launch_zf_L<32>(h, z, s);
+        case 64: return launch_zf_L<64>(h, z, s);
+        case 128: return launch_zf_L<128>(h, z, s);
+    }
+    set_error("z pass: unsupported length");
     return VIE_EINVAL;
 }
 
@@ -371,41 +718,6 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     const long long comps = (long long)R * 12 * nz;
     C* W1 = reinterpret_cast<C*>(ws);
     C* W2 = W1 + comps * ny * Lx;
-    MatvecEpi noepi{};
-    const bool fused = sizeof(T) == 4 && fused_xy_ok(h);
-    if (fused) {
-        VIE_TRY(launch_xy(true, h, x, W2, comps, nx, ny, noepi, s));
-    } else {
-        // x-pass: lines along x, contiguous
-        LineArgs a{};
-        a.in = x;
-        a.out = W1;
-        a.na = 1;
-        a.nb = (int)(comps * ny);
-        a.ia = 0, a.il = 1, a.ib = nx;
-        a.oa = 0, a.ol = 1, a.ob = Lx;
-        a.n_in = nx, a.n_out = Lx, a.dir = -1;
-        VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
-        // y-pass
-        a = LineArgs{};
-        a.in = W1;
-        a.out = W2;
-        a.na = (int)comps;
-        a.nb = Lx;
-        a.ia = (long long)ny * Lx, a.il = Lx, a.ib = 1;
-        a.oa = (long long)Ly * Lx, a.ol = Lx, a.ob = 1;
-        a.n_in = ny, a.n_out = Ly, a.dir = -1;
-        VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
-    }
-    // z-pass with block product
-    ZArgs z{};
-    z.w = W2;
-    z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
-    z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
-    z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
-    z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
-    z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
-    VIE_TRY(launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s));
     MatvecEpi e{};
     e.x = x;
     e.op = op;
@@ -420,12 +732,51 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         e.c1 = h->ieps32;
         e.c2 = op == VIE_OP_A ? (const void*)h->chi32 : (const void*)h->tau32;
     }
-    if (fused) {
-        VIE_TRY(launch_xy(false, h, W2, y, comps, nx, ny, e, s));
-        return VIE_OK;
+    MatvecEpi noepi{};
+    if (sizeof(T) == 4 && fused_ok(h)) {
+        VIE_TRY(launch_xy(true, h, x, W2, comps, nx, ny, noepi, s));
+        ZFArgs z{};
+        z.w = reinterpret_cast<float2*>(W2);
+        z.green_t = h->green32t;
+        z.colkx = h->colmap;
+        z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+        z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+        z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
+        z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+        VIE_TRY(launch_zf(h, z, s));
+        return launch_xy(false, h, W2, y, comps, nx, ny, e, s);
     }
-    // y-inverse
+    // x-pass: lines along x, contiguous
     LineArgs a{};
+    a.in = x;
+    a.out = W1;
+    a.na = 1;
+    a.nb = (int)(comps * ny);
+    a.ia = 0, a.il = 1, a.ib = nx;
+    a.oa = 0, a.ol = 1, a.ob = Lx;
+    a.n_in = nx, a.n_out = Lx, a.dir = -1;
+    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
+    // y-pass
+    a = LineArgs{};
+    a.in = W1;
+    a.out = W2;
+    a.na = (int)comps;
+    a.nb = Lx;
+    a.ia = (long long)ny * Lx, a.il = Lx, a.ib = 1;
+    a.oa = (long long)Ly * Lx, a.ol = Lx, a.ob = 1;
+    a.n_in = ny, a.n_out = Ly, a.dir = -1;
+    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
+    // z-pass with block product
+    ZArgs z{};
+    z.w = W2;
+    z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
+    z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+    z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+    z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
+    z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+    VIE_TRY(launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s));
+    // y-inverse
+    a = LineArgs{};
     a.in = W2;
     a.out = W1;
     a.na = (int)comps;
@@ -479,6 +830,45 @@ int fft3d_inplace64(vie_handle* h, double2* data, int batch, cudaStream_t s) {
     return VIE_OK;
 }
 
+// Stored column order of the FP32 spectrum (see the three-kernel path): colkx[sc] = kx of
+// stored column sc, colkx[L + sc] = its position in the transposed order of the x transform.
+// Mirror pairs fill tiles of 8 (two to a 16-column group chosen greedily so that their
+// positions differ modulo 16); the last tile ends with the self-mirrored columns 0, L/2.
+static bool build_colmap(int L, std::vector<unsigned char>& map) {
+    map.assign(2 * L, 0);
+    std::vector<int> kx(L, -1);
+    std::vector<bool> used(L / 2, false);  // pair (j, L - j) for j = 1..L/2-1
+    unsigned mask = 0;
+    int group = -1;
+    const int ntile = L / 8;
+    for (int t = 0; t < ntile; ++t)
+        for (int i = 0; i < (t < ntile - 1 ? 4 : 3); ++i) {
+            const int sc = 8 * t + 2 * i;
+            if (sc / 16 != group) group = sc / 16, mask = 0u;
+            int pick = -1;
+            for (int j = 1; j < L / 2 && pick < 0; ++j) {
+                if (used[j]) continue;
+                const int ra = fft2::tpos(L, j) % 16, rb = fft2::tpos(L, L - j) % 16;
+                if (ra != rb && !((mask >> ra) & 1u) && !((mask >> rb) & 1u)) pick = j;
+            }
+            for (int j = 1; j < L / 2 && pick < 0; ++j)
+                if (!used[j]) pick = j;
+            if (pick < 0) return false;
+            used[pick] = true;
+            kx[sc] = pick, kx[sc + 1] = L - pick;
+            mask |= (1u << (fft2::tpos(L, pick) % 16)) | (1u << (fft2::tpos(L, L - pick) % 16));
+        }
+    kx[L - 2] = 0, kx[L - 1] = L / 2;
+    std::vector<bool> seen(L, false);
+    for (int sc = 0; sc < L; ++sc) {
+        if (kx[sc] < 0 || kx[sc] >= L || seen[kx[sc]]) return false;
+        seen[kx[sc]] = true;
+        map[sc] = (unsigned char)kx[sc];
+        map[L + sc] = (unsigned char)fft2::tpos(L, kx[sc]);
+    }
+    return true;
+}
+
 int twiddle_setup(vie_handle* h) {
     // tables for L = 2^k, k = 1..10, stored at offset L (total 2048 entries)
     const int total = 2048;
@@ -496,6 +886,18 @@ int twiddle_setup(vie_handle* h) {
     h->bytes_held += total * (sizeof(double2) + sizeof(float2));
     VIE_CUDA(cudaMemcpy(h->tw64, t64.data(), total * sizeof(double2), cudaMemcpyHostToDevice));
     VIE_CUDA(cudaMemcpy(h->tw32, t32.data(), total * sizeof(float2), cudaMemcpyHostToDevice));
+    h->colmap = nullptr;
+    const int L = h->L[0];
+    if (L == h->L[1] && L >= 8 && L <= 128) {
+        std::vector<unsigned char> map;
+        if (!build_colmap(L, map)) {
+            set_error("column map construction failed");
+            return VIE_EDEVICE;
+        }
+        VIE_CUDA(cudaMalloc(&h->colmap, map.size()));
+        h->bytes_held += map.size();
+        VIE_CUDA(cudaMemcpy(h->colmap, map.data(), map.size(), cudaMemcpyHostToDevice));
+    }
     return VIE_OK;
 }
 

@@ -79,7 +79,9 @@ def test_green_toeplitz_parity(vie, shape, delta):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-CASES = [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 10, 6), 3), ((16, 16, 16), 1)]
+# (12, 5, 6) has Lx != Ly and (5, 6, 70) has Lz = 256: the FP32 matvec of both takes the
+# line-transform path instead of the three-kernel one
+CASES = [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 10, 6), 3), ((16, 16, 16), 1), ((12, 5, 6), 2), ((5, 6, 70), 1)]
 
 
 @pytest.fixture(scope="module")
@@ -116,8 +118,14 @@ def test_matvec_fp64_parity(vie, cases, shape, op):
 @pytest.mark.parametrize("shape", [c[0] for c in CASES])
 def test_matvec_fp32_parity(vie, cases, shape):
     g, prob, Nop, h, x = cases[shape]
-    for op, code in (("A", vie.VIE_OP_A), ("PA", vie.VIE_OP_PA)):
-        ref = O.apply_A(prob, Nop, x) if op == "A" else O.apply_PA(prob, Nop, x)
+    G = prob.gram_vector()[:, None, None, None]
+    for op, code in (("A", vie.VIE_OP_A), ("PA", vie.VIE_OP_PA), ("NSCAT", vie.VIE_OP_NSCAT)):
+        if op == "A":
+            ref = O.apply_A(prob, Nop, x)
+        elif op == "PA":
+            ref = O.apply_PA(prob, Nop, x)
+        else:
+            ref = Nop.apply(x) - G * x
         y = gpu_matvec(vie, h, x, vie.VIE_FP32, code)
         assert rel(y, ref) <= 1e-5
 
