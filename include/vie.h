@@ -166,12 +166,15 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *   b       : [nrhs][12][nz][ny][nx] C128
  *   x       : [nrhs][12][nz][ny][nx] C128; on entry the initial guess when
  *             (flags & 1), else ignored (zero guess); on exit the solution
- *   restart : Krylov dimension m in [1, 128];  maxit: cap on restart cycles (plain
- *             mode) or on refinement sweeps of one FP32 cycle each (mixed mode)
- *   mode    : VIE_SOLVE_FP64 (plain FP64) or VIE_SOLVE_FP32_REFINE (FP32 GMRES with
- *             FP64 iterative refinement: every cycle starts from the residual
- *             recomputed with the FP64 matvec; Hessenberg matrix, rotations and
- *             the solution in FP64, Krylov vectors in FP32)
+ *   restart : Krylov dimension m in [1, 128];  maxit: cap on restart cycles, counted
+ *             over all refinement sweeps in mixed mode
+ *   mode    : VIE_SOLVE_FP64 (plain FP64: every restart recomputes the residual with
+ *             the FP64 matvec) or VIE_SOLVE_FP32_REFINE (FP32 GMRES with FP64 iterative
+ *             refinement: each sweep recomputes the residual with the FP64 matvec, then
+ *             runs FP32 cycles on the correction until every right-hand side is below
+ *             max(2e-5 ||r||, tol ||P^-1 b|| / 2), restarting from the residual carried
+ *             by the Krylov basis; Hessenberg matrix, rotations and the solution in
+ *             FP64, Krylov vectors in FP32)
  *   flags   : bit 0 = use x as initial guess; bit 1 = also compute true_resid
  *             (one more FP64 matvec), else true_resid = -1
  *   info    : vie_solve_info[nrhs] host array or NULL

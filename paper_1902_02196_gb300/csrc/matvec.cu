@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(kXYThreads, 2)
     const float2* xin = reinterpret_cast<const float2*>(epi.x);
     const float2* c1 = reinterpret_cast<const float2*>(epi.c1);
     const float2* c2 = reinterpret_cast<const float2*>(epi.c2);
+#pragma unroll 4
     for (int idx = tid; idx < ny * nx; idx += NT) {
         float2 v = xr[(idx / nx) * RS + idx % nx];
         if (epi.op == VIE_OP_A) {
@@ -334,13 +335,16 @@ __global__ void __launch_bounds__(kXYThreads, 2)
 }
 
 // ---------------------------------------------------------------------------
-// z pass (FP32, on the spectrum of xy_fwd_kernel): one CTA per (row py, tile of 8
-// stored columns = 4 mirror pairs) loops over the right-hand sides; the next one's
-// column data arrives by cp.async while the current one is transformed.  The z
-// spectrum stays in transposed order between the forward and inverse transforms.
-// A thread of the block product owns one (column pair, kz mirror pair) item: it
-// loads the 60 Green values of the octant point once (480 contiguous bytes) and
-// applies them to the four frequency points (+-kx, +-kz) they serve.
+// z pass (FP32, on the spectrum of xy_fwd_kernel): a CTA of 128 threads per (row py,
+// tile of 4 stored columns = 2 mirror pairs) loops over the right-hand sides, two CTAs
+// to an SM so that one's loads and stores overlap the other's arithmetic; the next
+// right-hand side's columns arrive by cp.async while the current one is transformed.
+// The z spectrum stays in transposed order between the forward and inverse transforms.
+// A thread of the block product owns one (column pair, kz mirror pair) item for the
+// whole launch: the 60 Green values of its octant point stay in registers and serve
+// the four frequency points (+-kx, +-kz) of every right-hand side.  The item that pairs
+// kz = 0 with kz = Lz/2 keeps the second point's values in shared memory; the last
+// tile's self-mirrored columns 0 and Lx/2 reload theirs for each right-hand side.
 // ---------------------------------------------------------------------------
 struct ZFArgs {
     float2* w;                    // spectrum [R*12][Nz][Ly][Lx], in place
@@ -351,14 +355,14 @@ struct ZFArgs {
     unsigned mx, my, mz;
 };
 
-constexpr int kZThreads = 256;
-constexpr int kZTile = 8;
+constexpr int kZThreads = 128;
+constexpr int kZTile = 4;
 
 template <int LZ>
 struct ZFCfg {
-    static constexpr int GS = LZ * kZTile + 8;  // component stride: 8 float2 of padding keep half-warps apart
+    static constexpr int GS = LZ * kZTile + 4;  // component stride: 4 float2 of padding keep half-warps apart
     static constexpr int BUF = 12 * GS;
-    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ);
+    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 2 * 60);
 };
 
 // the 60 Green values of one octant point, streamed from the [..][60] layout
@@ -376,6 +380,7 @@ __device__ __forceinline__ float2 flip(float2 v, unsigned mask, int a) { return 
 
 // y = B x at the two mirror columns c, c + 1 of one z position (float4 accesses); m0, m1
 // are the components whose sign flips at each column's reflected frequency point.
+// u: the 60 Green values (registers, or shared memory).
 __device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, int off, unsigned m0, unsigned m1) {
     float2 x0[12], x1[12];
 #pragma unroll
@@ -428,12 +433,13 @@ __device__ __forceinline__ void single_point(const float2* u, float2* s, int gs,
 }
 
 template <int LZ>
-__global__ void __launch_bounds__(kZThreads, 1) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
+__global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
     constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = kZThreads, TB = kZTile;
     constexpr int GS = ZFCfg<LZ>::GS, BUF = ZFCfg<LZ>::BUF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sb = reinterpret_cast<float2*>(smem_raw);
     float2* tw = sb + 2 * BUF;
+    float2* gsec = tw + LZ;  // [2][60] Green values of kz = LZ/2 for the two column pairs
     const int tid = threadIdx.x;
     for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
     const int ntile = z.Lx / TB;
@@ -454,9 +460,9 @@ __global__ void __launch_bounds__(kZThreads, 1) zfused_kernel(ZFArgs z, const fl
     };
     auto line = [](int n) { return (n / TB) * GS + n % TB; };
 
-    // block-product item of this thread: column pair ci, kz item j (see the decoding below)
-    const int ci = tid & 3, j = tid >> 2;
-    const bool single = ct == ntile - 1 && ci == 3;  // columns 0 and Lx/2: own octant columns
+    // block-product item of this thread: column pair ci, kz item j
+    const int ci = tid & 1, j = tid >> 1;
+    const bool single = ct == ntile - 1 && ci == 1;  // columns 0 and Lx/2: own octant columns
     const int kx0 = z.colkx[sc0 + 2 * ci], kx1 = z.colkx[sc0 + 2 * ci + 1];
     const unsigned fx0 = kx0 > z.Lx / 2 ? z.mx : 0u, fx1 = kx1 > z.Lx / 2 ? z.mx : 0u;
     // kz items, in transposed positions p = k2 + B k1 holding kz = k1 + A k2:
@@ -480,6 +486,18 @@ __global__ void __launch_bounds__(kZThreads, 1) zfused_kernel(ZFArgs z, const fl
         else
             pb = B - k2;
     }
+    const int kza = pa >= 0 ? fft2::freq_at(LZ, pa) : 0;
+    const int kzoa = kza <= LZ / 2 ? kza : LZ - kza;
+    const int kxo0 = kx0 <= z.Lx / 2 ? kx0 : z.Lx - kx0;
+    const float2* gcol = z.green_t + ((long long)kyo * z.Ox + kxo0) * z.Oz * 60;
+    float2 u[60];
+    if (pa >= 0 && !single) {
+        load_green(u, gcol + (long long)kzoa * 60);
+        if (pc >= 0) {
+            const float2* g2 = gcol + (long long)(LZ / 2) * 60;
+            for (int t = 0; t < 60; ++t) gsec[ci * 60 + t] = g2[t];
+        }
+    }
 
     issue(0, sb);
 #pragma unroll 1
@@ -494,26 +512,32 @@ __global__ void __launch_bounds__(kZThreads, 1) zfused_kernel(ZFArgs z, const fl
         __syncthreads();
         fft2::forward<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
         if (pa >= 0) {
+            const unsigned fza = kza > LZ / 2 ? z.mz : 0u;
+            if (!single) {
+                pair_point(u, s, GS, pa * TB + 2 * ci, fy ^ fza ^ fx0, fy ^ fza ^ fx1);
+                if (pb >= 0) {
+                    const unsigned fzb = fft2::freq_at(LZ, pb) > LZ / 2 ? z.mz : 0u;
+                    pair_point(u, s, GS, pb * TB + 2 * ci, fy ^ fzb ^ fx0, fy ^ fzb ^ fx1);
+                }
+                if (pc >= 0) pair_point(gsec + ci * 60, s, GS, pc * TB + 2 * ci, fy ^ fx0, fy ^ fx1);
+            } else {
 #pragma unroll 1
-            for (int g = 0; g < (pc >= 0 ? 2 : 1); ++g) {
+                for (int g = 0; g < (pc >= 0 ? 2 : 1); ++g) {
 #pragma unroll 1
-                for (int col = 0; col < (single ? 2 : 1); ++col) {
-                    const int pp0 = g ? pc : pa, pp1 = g ? -1 : pb;
-                    const int kz = fft2::freq_at(LZ, pp0);
-                    const int kzo = kz <= LZ / 2 ? kz : LZ - kz;
-                    const int kx = col ? kx1 : kx0;
-                    const int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
-                    float2 u[60];
-                    load_green(u, z.green_t + (((long long)kyo * z.Ox + kxo) * z.Oz + kzo) * 60);
+                    for (int col = 0; col < 2; ++col) {
+                        const int pp0 = g ? pc : pa, pp1 = g ? -1 : pb;
+                        const int kz = fft2::freq_at(LZ, pp0);
+                        const int kzo = kz <= LZ / 2 ? kz : LZ - kz;
+                        const int kx = col ? kx1 : kx0;
+                        const int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
+                        load_green(u, z.green_t + (((long long)kyo * z.Ox + kxo) * z.Oz + kzo) * 60);
 #pragma unroll 1
-                    for (int e = 0; e < 2; ++e) {
-                        const int pp = e ? pp1 : pp0;
-                        if (pp < 0) break;
-                        const unsigned fz = fft2::freq_at(LZ, pp) > LZ / 2 ? z.mz : 0u;
-                        if (!single)
-                            pair_point(u, s, GS, pp * TB + 2 * ci, fy ^ fz ^ fx0, fy ^ fz ^ fx1);
-                        else
+                        for (int e = 0; e < 2; ++e) {
+                            const int pp = e ? pp1 : pp0;
+                            if (pp < 0) break;
+                            const unsigned fz = fft2::freq_at(LZ, pp) > LZ / 2 ? z.mz : 0u;
                             single_point(u, s, GS, pp * TB + 2 * ci + col, fy ^ fz ^ (col ? fx1 : fx0));
+                        }
                     }
                 }
             }

@@ -47,8 +47,6 @@ struct Prec<double2> {
     static constexpr int K = 2;
 };
 
-__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
-__device__ __forceinline__ double2 to_d(double2 v) { return v; }
 template <typename C>
 __device__ __forceinline__ C from_d(double2 v);
 template <>
@@ -251,12 +249,13 @@ __global__ void copy_norm_kernel(const double2* __restrict__ D, int ldd, double*
     if (r < R) out[r] = D[(long long)r * ldd].x;
 }
 
-// x[r] += sum_i c[r][i] U_i[r] (i < k[r]); the sum in the basis precision, the update in FP64
+// x[r] += sum_i c[r][i] U_i[r] (i < k[r]), or x[r] = that sum when overwrite is set; the sum
+// in the basis precision, the update in FP64
 template <typename VC>
 __global__ void __launch_bounds__(kThreads) xupdate_kernel(const VC* __restrict__ U, long long ustride,
                                                            double2* __restrict__ x, long long n,
                                                            const double2* __restrict__ c, int ldc,
-                                                           const int* __restrict__ k) {
+                                                           const int* __restrict__ k, int overwrite) {
     constexpr int K = Prec<VC>::K;
     __shared__ VC cs[kMaxV];
     const int r = blockIdx.y;
@@ -285,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) xupdate_kernel(const VC* __restrict_
     for (int q = 0; q < K; ++q) {
         const long long e = e0 + q;
         if (e < n) {
-            double2 xv = x[roff + e];
+            double2 xv = overwrite ? make_double2(0.0, 0.0) : x[roff + e];
             xv.x += (double)acc[q].x;
             xv.y += (double)acc[q].y;
             x[roff + e] = xv;
@@ -489,6 +488,28 @@ __global__ void trisolve_kernel(GState s, int R) {
     }
 }
 
+// Residual of the cycle's least-squares solution in the Krylov basis: with the rotations
+// Q = G_{k-1} ... G_0, r - A V_k y = V_{k+1} Q^H (0, ..., 0, g_k), so the coefficients of the
+// stored vectors u_i = n_i v_i are t_i / n_i (i <= k); k1 = k + 1 vectors, 0 when k = 0.
+__global__ void kresid_kernel(GState s, int R, int* __restrict__ k1) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int m = s.m, k = s.k[r];
+    k1[r] = k > 0 ? k + 1 : 0;
+    if (k == 0) return;
+    double2* t = s.coef + (long long)r * (m + 1);
+    const double* n = s.nrm + (long long)r * (m + 1);
+    t[k] = s.g[r * (m + 1) + k];
+    for (int i = k - 1; i >= 0; --i) {
+        const double c = s.cs[r * m + i].x;
+        const double2 sn = s.sn[r * m + i], b = t[i + 1];
+        // (t_i, t_{i+1}) <- G_i^H (0, b) = (-sn b, c b)
+        t[i] = make_double2(-(sn.x * b.x - sn.y * b.y), -(sn.x * b.y + sn.y * b.x));
+        t[i + 1] = make_double2(c * b.x, c * b.y);
+    }
+    for (int i = 0; i <= k; ++i) t[i] = make_double2(t[i].x / n[i], t[i].y / n[i]);
+}
+
 // residual check of the outer loop; converged right-hand sides stay idle in later cycles
 __global__ void check_kernel(const double* __restrict__ rn2, const double* __restrict__ bn2, double tol,
                              double eta_min, double* target, int* done, double* rel, int R) {
@@ -550,9 +571,11 @@ struct Solver {
     }
 };
 
+// One GMRES(m) cycle from the residual r64 (squared norms rn2); x64 += V y.  *still = number
+// of right-hand sides that ended the cycle above their target.
 template <typename VC>
 int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* rn2, int precision, int* it_rhs,
-              int* mv_count, int* host_i) {
+              int* mv_count, int* host_i, int* still) {
     vie_handle* h = S.h;
     const int R = S.R, m = S.m;
     const long long n = S.n, ustride = (long long)R * n;
@@ -584,13 +607,30 @@ int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* 
     VIE_KLAUNCH("trisolve", st, trisolve_kernel<<<gr, 128, 0, st>>>(S.gs, R));
     const dim3 gx((unsigned)((n + kThreads * Prec<VC>::K - 1) / (kThreads * Prec<VC>::K)), R);
     VIE_KLAUNCH("solution_update", st,
-                xupdate_kernel<VC><<<gx, kThreads, 0, st>>>(U, ustride, x64, n, S.gs.y, m, S.gs.k));
+                xupdate_kernel<VC><<<gx, kThreads, 0, st>>>(U, ustride, x64, n, S.gs.y, m, S.gs.k, 0));
+    VIE_KLAUNCH("count_active", st, count_active_kernel<<<1, 1, 0, st>>>(S.gs.active, R, S.gs.nactive));
     VIE_CHECK_LAUNCH();
     std::vector<int> k(R);
     VIE_CUDA(cudaMemcpyAsync(k.data(), S.gs.k, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaMemcpyAsync(host_i, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     VIE_CUDA(cudaStreamSynchronize(st));
     for (int r = 0; r < R; ++r) it_rhs[r] += k[r];
+    *still = *host_i;
     return VIE_OK;
+}
+
+// r64 = residual of the last cycle from its Krylov basis (no matvec), rn2 = its squared norms
+template <typename VC>
+int krylov_residual(Solver& S, const VC* U, double2* r64, double* rn2, int* k1) {
+    const int R = S.R;
+    const long long n = S.n, ustride = (long long)R * n;
+    cudaStream_t st = S.st;
+    VIE_KLAUNCH("krylov_resid_coef", st, kresid_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R, k1));
+    const dim3 gx((unsigned)((n + kThreads * Prec<VC>::K - 1) / (kThreads * Prec<VC>::K)), R);
+    VIE_KLAUNCH("krylov_residual", st,
+                xupdate_kernel<VC><<<gx, kThreads, 0, st>>>(U, ustride, r64, n, S.gs.coef, S.m + 1, k1, 1));
+    VIE_CHECK_LAUNCH();
+    return S.norm2_64(r64, rn2);
 }
 
 }  // namespace
@@ -641,6 +681,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const size_t oRn = take(sizeof(double) * R);
     const size_t oDone = take(sizeof(int) * R);
     const size_t oRel = take(sizeof(double) * R);
+    const size_t oK1 = take(sizeof(int) * R);
     VIE_TRY(ws_reserve(h, h->solve_ws, off));
     char* base = static_cast<char*>(h->solve_ws.ptr);
     Solver S;
@@ -677,6 +718,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     double* rn2 = reinterpret_cast<double*>(base + oRn);
     int* done = reinterpret_cast<int*>(base + oDone);
     double* rel = reinterpret_cast<double*>(base + oRel);
+    int* k1 = reinterpret_cast<int*>(base + oK1);
     int* pinned = nullptr;
     VIE_CUDA(cudaMallocHost(&pinned, sizeof(int) * 4));
     struct PinGuard {
@@ -719,18 +761,32 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         for (int r = 0; r < R; ++r) all = all && hdone[r];
         return VIE_OK;
     };
-    for (int cyc = 0; cyc < maxit; ++cyc) {
+    // Plain mode: the FP64 residual is recomputed at every restart.  Mixed mode: each
+    // refinement sweep takes the FP64 residual, then runs FP32 GMRES cycles on the
+    // correction until every right-hand side is below its sweep target, restarting from
+    // the residual carried by the Krylov basis (no FP64 matvec inside a sweep).
+    int cyc = 0;
+    while (cyc < maxit) {
         VIE_TRY(residual());
         if (all) break;
         if (mixed) {
-            VIE_TRY(run_cycle<float2>(S, reinterpret_cast<float2*>(base + oU), x, r64, rn2, VIE_FP32, it_rhs.data(),
-                                      &mv32, pinned));
             ++sweeps;
+            float2* U32 = reinterpret_cast<float2*>(base + oU);
+            for (;;) {
+                int still = 0;
+                VIE_TRY(run_cycle<float2>(S, U32, x, r64, rn2, VIE_FP32, it_rhs.data(), &mv32, pinned, &still));
+                ++cyc;
+                x_is_zero = false;
+                if (still == 0 || cyc >= maxit) break;
+                VIE_TRY(krylov_residual<float2>(S, U32, r64, rn2, k1));
+            }
         } else {
+            int still = 0;
             VIE_TRY(run_cycle<double2>(S, reinterpret_cast<double2*>(base + oU), x, r64, rn2, VIE_FP64,
-                                       it_rhs.data(), &mv64, pinned));
+                                       it_rhs.data(), &mv64, pinned, &still));
+            ++cyc;
+            x_is_zero = false;
         }
-        x_is_zero = false;
     }
     if (!all) VIE_TRY(residual());  // residual of the last iterate when the cycle cap was hit
     if (flags & 2) {
