@@ -177,6 +177,10 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *             FP64, Krylov vectors in FP32)
  *   flags   : bit 0 = use x as initial guess; bit 1 = also compute true_resid
  *             (one more FP64 matvec), else true_resid = -1
+ * Where chi, b and the guess all vanish (air), the rows of P^-1 A are the identity and
+ * the solution is zero; the solver's vectors cover only each grid row's span of the
+ * other voxels (the whole grid when that span covers it), so air costs no iterations'
+ * memory traffic.  x is zero outside that span on exit.
  *   info    : vie_solve_info[nrhs] host array or NULL
  * Synchronous.  Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
  */

@@ -101,6 +101,7 @@ void release(vie_handle* h) {
     cudaFree(h->fft_ws.ptr);
     cudaFree(h->stage_ws.ptr);
     cudaFree(h->solve_ws.ptr);
+    cudaFree(h->support_ws.ptr);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

@@ -121,6 +121,7 @@ struct vie_handle {
     Workspace fft_ws;    // matvec spectrum buffers
     Workspace stage_ws;  // host-buffer staging
     Workspace solve_ws;  // solver vectors
+    Workspace support_ws;  // support rows of the current solve
     double2* toeplitz;   // [60][nz][ny][nx] Toeplitz tensors of N - G for offsets d >= 0
     size_t bytes_held;
 };
@@ -182,6 +183,25 @@ int green_setup(vie_handle* h);                 // green.cu
 int twiddle_setup(vie_handle* h);               // matvec.cu
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);
+
+// Support of a solve: per (z, y) row of the grid the voxel interval [x0, x1) whose
+// unknowns are kept and the offset of voxel (x0, y, z) within a component block of ns
+// voxels; a vector on the support is laid out [R][12][ns].  rows == NULL: the full
+// grid in its natural layout (ns = nx ny nz).
+struct Support {
+    const int4* rows = nullptr;  // [nz * ny] (x0, x1, offset, 0)
+    long long ns = 0;
+};
+// y = op(x) for vectors on a support.  tmp: scratch of 2 nrhs 12 nx ny nz complex values
+// of the precision, used only when the matvec has to run on the full grid (scatter,
+// full matvec, gather).
+int matvec_support(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, const Support& sp,
+                   void* tmp, cudaStream_t s);
+// full-grid vector <-> vector on a support (values outside the support dropped / set to zero)
+int support_gather(const vie_handle* h, int nrhs, const void* full, void* part, int precision, const Support& sp,
+                   cudaStream_t s);
+int support_scatter(const vie_handle* h, int nrhs, const void* part, void* full, int precision, const Support& sp,
+                    cudaStream_t s);
 // full 3-D FFT of `batch` complex double volumes [batch][Lz][Ly][Lx] in place (forward, unscaled)
 int fft3d_inplace64(vie_handle* h, double2* data, int batch, cudaStream_t s);
 int solve_device(vie_handle* h, int nrhs, const double2* b, double2* x, double tol, int restart, int maxit,

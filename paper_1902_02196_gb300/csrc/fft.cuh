@@ -126,12 +126,14 @@ struct LineArgs {
 
 // Optional epilogue of the last inverse pass of the matvec: crop + material and Gram terms.
 struct MatvecEpi {
-    const void* x;     // input vector [R][12][Nz][Ny][Nx]
+    const void* x;     // input vector [R][12][Nz][Ny][Nx] (or [R][12][ns] on a support, see Support)
     const void* c1;    // per-voxel complex coefficient multiplying x   (op A: none; op PA: 1/eps)
     const void* c2;    // per-voxel complex coefficient multiplying Nx  (op A: chi; op PA: tau)
     int op;            // VIE_OP_*
     int nx, ny, nz;    // grid
     double g1, g234;   // Gram entries
+    const int4* rows;  // support rows (x0, x1, offset) per (z, y) or NULL for the full grid
+    long long ns;      // support size (voxels)
 };
 
 template <int L>

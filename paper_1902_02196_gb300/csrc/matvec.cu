@@ -171,6 +171,11 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
 }
+// 8-byte copy that writes zeros when src_bytes == 0 (src must still be a valid address)
+__device__ __forceinline__ void cp_async8z(void* smem_dst, const void* gsrc, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -184,29 +189,45 @@ struct XYCfg {
     static constexpr int H = L / 2;                // rows that are non-zero before / needed after the y transform
     static constexpr int RS = L + 1;               // odd row stride of the x-transform buffer
     static constexpr int CW = L < 32 ? L : 32;     // stored columns per y-transform chunk
-    static constexpr size_t smem = sizeof(float2) * (size_t)(L * CW + H * RS + L) + L;
+    static constexpr size_t smem = sizeof(float2) * (size_t)(L * CW + H * RS + L) + sizeof(int4) * H + L;
 };
 
-// Forward: plane (r, alpha, z) of x [Ny][Nx] -> W2 plane [Ly][Lx] (transposed ky, stored kx).
+// Forward: plane (r, alpha, z) of x -> W2 plane [Ly][Lx] (transposed ky, stored kx).  x is
+// [R][12][Nz][Ny][Nx], or [R][12][ns] on a support (rows != NULL; zeros outside it).
 template <int L>
 __global__ void __launch_bounds__(kXYThreads, 2)
-    xy_fwd_kernel(const float2* __restrict__ x, float2* __restrict__ w, int nx, int ny,
-                  const unsigned char* __restrict__ cpos, const float2* __restrict__ twg) {
+    xy_fwd_kernel(const float2* __restrict__ x, float2* __restrict__ w, int nx, int ny, int nz,
+                  const int4* __restrict__ rows, long long ns, const unsigned char* __restrict__ cpos,
+                  const float2* __restrict__ twg) {
     using Cfg = XYCfg<L>;
     constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* ck = reinterpret_cast<float2*>(smem_raw);  // [L][CW] chunk of stored columns
     float2* xr = ck + L * CW;                          // [H][RS] rows after the x transform
     float2* tw = xr + Cfg::H * RS;
-    unsigned char* pos = reinterpret_cast<unsigned char*>(tw + L);
+    int4* rw = reinterpret_cast<int4*>(tw + L);        // [H] support rows of this plane
+    unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
     for (int m = tid; m < L; m += NT) {
         tw[m] = twg[m];
         pos[m] = cpos[m];
     }
     const long long p = blockIdx.x;
-    const float2* src = x + p * (long long)ny * nx;
-    for (int idx = tid; idx < ny * nx; idx += NT) cp_async8(xr + (idx / nx) * RS + idx % nx, src + idx);
+    if (rows) {
+        const int z = (int)(p % nz);
+        for (int yy = tid; yy < ny; yy += NT) rw[yy] = rows[(long long)z * ny + yy];
+        __syncthreads();
+        const float2* src = x + (p / nz) * ns;
+        for (int idx = tid; idx < ny * nx; idx += NT) {
+            const int yy = idx / nx, xx = idx % nx;
+            const int4 q = rw[yy];
+            const bool in = xx >= q.x && xx < q.y;
+            cp_async8z(xr + yy * RS + xx, in ? src + q.z + (xx - q.x) : src, in ? 8 : 0);
+        }
+    } else {
+        const float2* src = x + p * (long long)ny * nx;
+        for (int idx = tid; idx < ny * nx; idx += NT) cp_async8(xr + (idx / nx) * RS + idx % nx, src + idx);
+    }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
@@ -262,7 +283,8 @@ __global__ void __launch_bounds__(kXYThreads, 2)
     float2* ck = reinterpret_cast<float2*>(smem_raw);
     float2* xr = ck + L * CW;
     float2* tw = xr + Cfg::H * RS;
-    unsigned char* pos = reinterpret_cast<unsigned char*>(tw + L);
+    int4* rw = reinterpret_cast<int4*>(tw + L);
+    unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
     for (int m = tid; m < L; m += NT) {
         tw[m] = twg[m];
@@ -270,6 +292,8 @@ __global__ void __launch_bounds__(kXYThreads, 2)
     }
     const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
     const long long p = blockIdx.x;  // plane (r * 12 + alpha) * nz + z
+    if (epi.rows)
+        for (int yy = tid; yy < ny; yy += NT) rw[yy] = epi.rows[(p % nz) * ny + yy];
     const float2* src = w + p * (long long)L * L;
 #pragma unroll 1
     for (int k = 0; k < L / CW; ++k) {
@@ -318,19 +342,27 @@ __global__ void __launch_bounds__(kXYThreads, 2)
     const float2* xin = reinterpret_cast<const float2*>(epi.x);
     const float2* c1 = reinterpret_cast<const float2*>(epi.c1);
     const float2* c2 = reinterpret_cast<const float2*>(epi.c2);
+    const long long cbase = (p / nz) * epi.ns;  // component block on the support
 #pragma unroll 4
     for (int idx = tid; idx < ny * nx; idx += NT) {
-        float2 v = xr[(idx / nx) * RS + idx % nx];
+        const int yy = idx / nx, xx = idx % nx;
+        long long o = base + idx;
+        if (epi.rows) {
+            const int4 q = rw[yy];
+            if (xx < q.x || xx >= q.y) continue;
+            o = cbase + q.z + (xx - q.x);
+        }
+        float2 v = xr[yy * RS + xx];
         if (epi.op == VIE_OP_A) {
-            const float2 xv = xin[base + idx];
+            const float2 xv = xin[o];
             v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[zoff + idx], v));
         } else if (epi.op == VIE_OP_PA) {
-            const float2 xv = xin[base + idx];
+            const float2 xv = xin[o];
             const float2 t = cmul(c2[zoff + idx], v);
             const float ig = 1.0f / gl;
             v = csub(cmul(c1[zoff + idx], xv), mk(ig * t.x, ig * t.y));
         }
-        y[base + idx] = v;
+        y[o] = v;
     }
 }
 
@@ -655,9 +687,10 @@ static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z
 // (the column map is built at setup only for such grids).
 static bool fused_ok(const vie_handle* h) { return h->colmap && h->L[2] >= 8 && h->L[2] <= 128; }
 
+// in_elems: complex values of the matvec input (and output) vector
 template <int L>
 static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
-                       const MatvecEpi& e, cudaStream_t s) {
+                       const MatvecEpi& e, const Support& sp, double in_elems, cudaStream_t s) {
     constexpr size_t smem = XYCfg<L>::smem;
     static bool configured = false;
     if (!configured) {
@@ -670,14 +703,14 @@ static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out,
         return VIE_EINVAL;
     }
     const unsigned char* cpos = h->colmap + L;
-    const double plane_in = (double)nx * ny, plane_full = (double)L * L;
+    const double plane_full = (double)L * L;
     if (fwd)
-        VIE_KLAUNCH_B("fft_xy_f32", s, 8.0 * planes * (plane_in + plane_full),
+        VIE_KLAUNCH_B("fft_xy_f32", s, 8.0 * (in_elems + planes * plane_full),
                       xy_fwd_kernel<L><<<(unsigned)planes, kXYThreads, smem, s>>>(
-                          (const float2*)in, (float2*)out, nx, ny, cpos, h->tw32 + L));
+                          (const float2*)in, (float2*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, h->tw32 + L));
     else
         VIE_KLAUNCH_B("ifft_xy_epilogue_f32", s,
-                      8.0 * (planes * (plane_full + plane_in * (e.op == VIE_OP_NSCAT ? 1 : 2)) +
+                      8.0 * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
                              (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0)),
                       xy_inv_kernel<L><<<(unsigned)planes, kXYThreads, smem, s>>>(
                           (const float2*)in, (float2*)out, e, cpos, h->tw32 + L));
@@ -686,13 +719,13 @@ static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out,
 }
 
 static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
-                     const MatvecEpi& e, cudaStream_t s) {
+                     const MatvecEpi& e, const Support& sp, double in_elems, cudaStream_t s) {
     switch (h->L[0]) {
-        case 8: return launch_xy_L<8>(fwd, h, in, out, planes, nx, ny, e, s);
-        case 16: return launch_xy_L<16>(fwd, h, in, out, planes, nx, ny, e, s);
-        case 32: return launch_xy_L<32>(fwd, h, in, out, planes, nx, ny, e, s);
-        case 64: return launch_xy_L<64>(fwd, h, in, out, planes, nx, ny, e, s);
-        case 128: return launch_xy_L<128>(fwd, h, in, out, planes, nx, ny, e, s);
+        case 8: return launch_xy_L<8>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 16: return launch_xy_L<16>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 32: return launch_xy_L<32>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 64: return launch_xy_L<64>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 128: return launch_xy_L<128>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
     }
     set_error("xy transform: unsupported length");
     return VIE_EINVAL;
@@ -734,9 +767,11 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
     return c * (w1 + w2) + 256;
 }
 
-// ws: scratch of at least matvec_workspace_bytes(h, R, precision) bytes (spectrum buffers W1, W2)
+// ws: scratch of at least matvec_workspace_bytes(h, R, precision) bytes (spectrum buffers W1, W2);
+// sp: support of x and y (only the FP32 three-kernel path takes vectors on a support)
 template <typename T>
-static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws) {
+static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws,
+                       const Support& sp = Support{}) {
     using C = typename CT<T>::C;
     const int nx = h->nx, ny = h->ny, nz = h->nz, Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
     const long long comps = (long long)R * 12 * nz;
@@ -756,9 +791,12 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         e.c1 = h->ieps32;
         e.c2 = op == VIE_OP_A ? (const void*)h->chi32 : (const void*)h->tau32;
     }
+    e.rows = sp.rows;
+    e.ns = sp.ns;
     MatvecEpi noepi{};
     if (sizeof(T) == 4 && fused_ok(h)) {
-        VIE_TRY(launch_xy(true, h, x, W2, comps, nx, ny, noepi, s));
+        const double in_elems = sp.rows ? (double)R * 12 * sp.ns : (double)comps * ny * nx;
+        VIE_TRY(launch_xy(true, h, x, W2, comps, nx, ny, noepi, sp, in_elems, s));
         ZFArgs z{};
         z.w = reinterpret_cast<float2*>(W2);
         z.green_t = h->green32t;
@@ -768,7 +806,11 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
         z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
         VIE_TRY(launch_zf(h, z, s));
-        return launch_xy(false, h, W2, y, comps, nx, ny, e, s);
+        return launch_xy(false, h, W2, y, comps, nx, ny, e, sp, in_elems, s);
+    }
+    if (sp.rows) {
+        set_error("internal: the line-transform matvec takes full-grid vectors only");
+        return VIE_EINVAL;
     }
     // x-pass: lines along x, contiguous
     LineArgs a{};
@@ -826,6 +868,76 @@ int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, nrhs, precision)));
     if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr);
     return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr);
+}
+
+// ---------------------------------------------------------------------------
+// Vectors on a support: [R][12][ns] <-> full grid [R][12][Nz][Ny][Nx]
+// ---------------------------------------------------------------------------
+template <typename C>
+__global__ void support_gather_kernel(const C* __restrict__ full, C* __restrict__ part, const int4* __restrict__ rows,
+                                      long long ns, int nx, long long nrows, long long total) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // full-grid element
+    if (e >= total) return;
+    const int xx = (int)(e % nx);
+    const long long row = (e / nx) % nrows, comp = e / (nx * nrows);
+    const int4 q = rows[row];
+    if (xx >= q.x && xx < q.y) part[comp * ns + q.z + (xx - q.x)] = full[e];
+}
+template <typename C>
+__global__ void support_scatter_kernel(const C* __restrict__ part, C* __restrict__ full, const int4* __restrict__ rows,
+                                       long long ns, int nx, long long nrows, long long total) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int xx = (int)(e % nx);
+    const long long row = (e / nx) % nrows, comp = e / (nx * nrows);
+    const int4 q = rows[row];
+    full[e] = (xx >= q.x && xx < q.y) ? part[comp * ns + q.z + (xx - q.x)] : C{};
+}
+
+template <typename C>
+static int support_copy(const vie_handle* h, int R, const void* src, void* dst, const Support& sp, bool gather,
+                        cudaStream_t s) {
+    const long long total = (long long)R * 12 * (long long)h->nv;
+    if (!sp.rows) {
+        VIE_CUDA(cudaMemcpyAsync(dst, src, sizeof(C) * (size_t)total, cudaMemcpyDeviceToDevice, s));
+        return VIE_OK;
+    }
+    const unsigned g = (unsigned)((total + 255) / 256);
+    const long long nrows = (long long)h->ny * h->nz;
+    if (gather)
+        VIE_KLAUNCH("support_gather", s,
+                    support_gather_kernel<C><<<g, 256, 0, s>>>((const C*)src, (C*)dst, sp.rows, sp.ns, h->nx, nrows,
+                                                               total));
+    else
+        VIE_KLAUNCH("support_scatter", s,
+                    support_scatter_kernel<C><<<g, 256, 0, s>>>((const C*)src, (C*)dst, sp.rows, sp.ns, h->nx, nrows,
+                                                                total));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+int support_gather(const vie_handle* h, int R, const void* full, void* part, int precision, const Support& sp,
+                   cudaStream_t s) {
+    return precision == VIE_FP64 ? support_copy<double2>(h, R, full, part, sp, true, s)
+                                 : support_copy<float2>(h, R, full, part, sp, true, s);
+}
+int support_scatter(const vie_handle* h, int R, const void* part, void* full, int precision, const Support& sp,
+                    cudaStream_t s) {
+    return precision == VIE_FP64 ? support_copy<double2>(h, R, part, full, sp, false, s)
+                                 : support_copy<float2>(h, R, part, full, sp, false, s);
+}
+
+int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, int op, const Support& sp, void* tmp,
+                   cudaStream_t s) {
+    if (!sp.rows) return matvec_device(h, R, x, y, precision, op, s);
+    VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, precision)));
+    if (precision == VIE_FP32 && fused_ok(h)) return matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp);
+    const size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
+    void* tx = tmp;
+    void* ty = static_cast<char*>(tmp) + c * (size_t)R * 12 * h->nv;
+    VIE_TRY(support_scatter(h, R, x, tx, precision, sp, s));
+    VIE_TRY(matvec_device(h, R, tx, ty, precision, op, s));
+    return support_gather(h, R, ty, y, precision, sp, s);
 }
 
 // Full forward 3-D FFT of [batch][Lz][Ly][Lx] complex double volumes, in place.

@@ -524,6 +524,75 @@ __global__ void check_kernel(const double* __restrict__ rn2, const double* __res
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Per (z, y) row: [x0, x1) spanning the voxels where chi, any right-hand side or the
+// initial guess is non-zero ((0, 0) for a row with none).  One warp per row.
+__global__ void support_rows_kernel(const double2* __restrict__ chi, const double2* __restrict__ b,
+                                    const double2* __restrict__ guess, int ncomp, int nx, long long nrows,
+                                    long long nv, int2* __restrict__ out) {
+    const long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    int lo = nx, hi = -1;
+    for (int xx = lane; xx < nx; xx += 32) {
+        const long long v = row * nx + xx;
+        const double2 c = chi[v];
+        bool nzv = c.x != 0.0 || c.y != 0.0;
+        for (int q = 0; q < ncomp && !nzv; ++q) {
+            const double2 t = b[(long long)q * nv + v];
+            nzv = t.x != 0.0 || t.y != 0.0;
+            if (guess && !nzv) {
+                const double2 g = guess[(long long)q * nv + v];
+                nzv = g.x != 0.0 || g.y != 0.0;
+            }
+        }
+        if (nzv) {
+            lo = min(lo, xx);
+            hi = max(hi, xx);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) out[row] = hi >= lo ? make_int2(lo, hi + 1) : make_int2(0, 0);
+}
+
+// Support of a solve (Section III: unknowns where chi = 0 vanish when b does, since those
+// rows of P^-1 A are the identity): rows of the grid restricted to the voxels where chi,
+// b or the guess is non-zero; the full grid when that covers every voxel.
+int build_support(vie_handle* h, int R, const double2* b, const double2* guess, Support* sp, cudaStream_t st) {
+    const long long nrows = (long long)h->ny * h->nz;
+    VIE_TRY(ws_reserve(h, h->support_ws, sizeof(int4) * (size_t)nrows + sizeof(int2) * (size_t)nrows));
+    int4* rows = static_cast<int4*>(h->support_ws.ptr);
+    int2* span = reinterpret_cast<int2*>(rows + nrows);
+    const unsigned g = (unsigned)((nrows + 7) / 8);
+    VIE_KLAUNCH("support_rows", st,
+                support_rows_kernel<<<g, 256, 0, st>>>(h->chi64, b, guess, R * 12, h->nx, nrows, (long long)h->nv,
+                                                       span));
+    VIE_CHECK_LAUNCH();
+    std::vector<int2> hs(nrows);
+    VIE_CUDA(cudaMemcpyAsync(hs.data(), span, sizeof(int2) * nrows, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    std::vector<int4> hr(nrows);
+    long long off = 0;
+    for (long long i = 0; i < nrows; ++i) {
+        hr[i] = make_int4(hs[i].x, hs[i].y, (int)off, 0);
+        off += hs[i].y - hs[i].x;
+    }
+    sp->ns = off;
+    sp->rows = nullptr;
+    if (off == (long long)h->nv || off == 0) return VIE_OK;
+    if (off > 0x7fffffffLL) {
+        set_error("support too large");
+        return VIE_EINVAL;
+    }
+    VIE_CUDA(cudaMemcpyAsync(rows, hr.data(), sizeof(int4) * nrows, cudaMemcpyHostToDevice, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    sp->rows = rows;
+    return VIE_OK;
+}
+
 struct Solver {
     vie_handle* h;
     cudaStream_t st;
@@ -555,13 +624,15 @@ struct Solver {
         VIE_CHECK_LAUNCH();
         return VIE_OK;
     }
-    int nblk64() const { return (int)((n + kThreads * Prec<double2>::K - 1) / (kThreads * Prec<double2>::K)); }
-    // squared 2-norm per right-hand side of an FP64 vector batch into out[R]
-    int norm2_64(const double2* v, double* out) {
-        const int nb = nblk64();
+    Support sp;        // support of the solver's vectors
+    void* mv_tmp;      // full-grid scratch of matvec_support
+    // squared 2-norm per right-hand side of an FP64 vector batch of length len (default n) into out[R]
+    int norm2_64(const double2* v, double* out, long long len = 0) {
+        if (len <= 0) len = n;
+        const int nb = (int)((len + kThreads * Prec<double2>::K - 1) / (kThreads * Prec<double2>::K));
         const dim3 g1(nb, R);
         VIE_KLAUNCH("norm64", st,
-                    gs_dots_kernel<double2><<<g1, kThreads, 0, st>>>(nullptr, 0, v, n, 0, partial, nb, nullptr));
+                    gs_dots_kernel<double2><<<g1, kThreads, 0, st>>>(nullptr, 0, v, len, 0, partial, nb, nullptr));
         const dim3 g2(1, R);
         VIE_KLAUNCH("norm64_finalize", st,
                     finalize2_kernel<<<g2, kThreads, 0, st>>>(partial, nb, 1, gs.D, m + 2, nullptr));
@@ -592,7 +663,7 @@ int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* 
         if (*host_i == 0) break;
         VC* uj = U + j * ustride;
         VC* w = U + (j + 1) * ustride;
-        VIE_TRY(matvec_device(h, R, uj, w, precision, VIE_OP_PA, st));
+        VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st));
         ++*mv_count;
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
         VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
@@ -641,12 +712,22 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         set_error("restart above 128 is not supported");
         return VIE_EINVAL;
     }
-    const long long n = 12LL * (long long)h->nv;
+    // vectors live on the support of the solve: [R][12][ns]
+    Support sp;
+    VIE_TRY(build_support(h, R, b, (flags & 1) ? x : nullptr, &sp, st));
+    const long long nfull = 12LL * (long long)h->nv;
+    if (sp.ns == 0) {  // chi = 0 everywhere and b = 0: x = 0
+        VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)(R * nfull), st));
+        VIE_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; info && r < R; ++r) info[r] = vie_solve_info{1, 0, 0, 0, 0, 0.0, (flags & 2) ? 0.0 : -1.0};
+        return VIE_OK;
+    }
+    const long long n = 12LL * sp.ns;
     const bool mixed = mode == VIE_SOLVE_FP32_REFINE;
     const size_t vc = mixed ? sizeof(float2) : sizeof(double2);
     const int kpt = mixed ? Prec<float2>::K : Prec<double2>::K;
     const int nblk = (int)((n + kThreads * kpt - 1) / (kThreads * kpt));
-    const int nblk64 = (int)((n + kThreads * Prec<double2>::K - 1) / (kThreads * Prec<double2>::K));
+    const int nblk64 = (int)((nfull + kThreads * Prec<double2>::K - 1) / (kThreads * Prec<double2>::K));
     const int nbmax = nblk > nblk64 ? nblk : nblk64;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -658,6 +739,8 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const size_t oR = take(sizeof(double2) * (size_t)R * n);
     const size_t oBt = take(sizeof(double2) * (size_t)R * n);
     const size_t oT = take(sizeof(double2) * (size_t)R * n);
+    const size_t oX = take(sizeof(double2) * (size_t)R * n);
+    const size_t oFull = take(2 * sizeof(double2) * (size_t)R * nfull);  // full-grid scratch
     const size_t oPart = take(sizeof(double2) * (size_t)R * nbmax * (m + 2));
     const size_t oNp = take(sizeof(double) * (size_t)R * nbmax);
     const size_t oH = take(sizeof(double2) * (size_t)R * (m + 1) * m);
@@ -691,6 +774,8 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     S.m = m;
     S.n = n;
     S.nblk = nblk;
+    S.sp = sp;
+    S.mv_tmp = base + oFull;
     S.partial = reinterpret_cast<double2*>(base + oPart);
     S.npart = reinterpret_cast<double*>(base + oNp);
     S.gs.m = m;
@@ -714,6 +799,9 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     double2* r64 = reinterpret_cast<double2*>(base + oR);
     double2* bt = reinterpret_cast<double2*>(base + oBt);
     double2* t64 = reinterpret_cast<double2*>(base + oT);
+    double2* xs = reinterpret_cast<double2*>(base + oX);  // solution on the support
+    double2* full0 = reinterpret_cast<double2*>(base + oFull);
+    double2* full1 = full0 + (size_t)R * nfull;
     double* bn2 = reinterpret_cast<double*>(base + oBn);
     double* rn2 = reinterpret_cast<double*>(base + oRn);
     int* done = reinterpret_cast<int*>(base + oDone);
@@ -726,15 +814,20 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         ~PinGuard() { cudaFreeHost(p); }
     } guard{pinned};
 
-    const long long total = (long long)R * n;
+    const long long total = (long long)R * n, total_full = (long long)R * nfull;
     const unsigned gt = (unsigned)((total + 255) / 256);
+    const unsigned gtf = (unsigned)((total_full + 255) / 256);
     const unsigned gr = (unsigned)((R + 127) / 128);
     const double dV = h->dx * h->dy * h->dz;
     VIE_KLAUNCH("precond_rhs", st,
-                precond_rhs_kernel<<<gt, 256, 0, st>>>(b, h->ieps64, bt, (long long)h->nv, R, dV, dV / 12.0));
+                precond_rhs_kernel<<<gtf, 256, 0, st>>>(b, h->ieps64, full0, (long long)h->nv, R, dV, dV / 12.0));
     VIE_CHECK_LAUNCH();
+    VIE_TRY(support_gather(h, R, full0, bt, VIE_FP64, sp, st));
     VIE_TRY(S.norm2_64(bt, bn2));
-    if (!(flags & 1)) VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * total, st));
+    if (flags & 1)
+        VIE_TRY(support_gather(h, R, x, xs, VIE_FP64, sp, st));
+    else
+        VIE_CUDA(cudaMemsetAsync(xs, 0, sizeof(double2) * total, st));
 
     std::vector<int> it_rhs(R, 0), hdone(R, 0);
     std::vector<double> hrel(R, 0.0), htrue(R, -1.0);
@@ -746,7 +839,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         if (x_is_zero) {
             VIE_CUDA(cudaMemcpyAsync(r64, bt, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
         } else {
-            VIE_TRY(matvec_device(h, R, x, t64, VIE_FP64, VIE_OP_PA, st));
+            VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st));
             ++mv64;
             VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
         }
@@ -774,7 +867,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             float2* U32 = reinterpret_cast<float2*>(base + oU);
             for (;;) {
                 int still = 0;
-                VIE_TRY(run_cycle<float2>(S, U32, x, r64, rn2, VIE_FP32, it_rhs.data(), &mv32, pinned, &still));
+                VIE_TRY(run_cycle<float2>(S, U32, xs, r64, rn2, VIE_FP32, it_rhs.data(), &mv32, pinned, &still));
                 ++cyc;
                 x_is_zero = false;
                 if (still == 0 || cyc >= maxit) break;
@@ -782,20 +875,21 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             }
         } else {
             int still = 0;
-            VIE_TRY(run_cycle<double2>(S, reinterpret_cast<double2*>(base + oU), x, r64, rn2, VIE_FP64,
+            VIE_TRY(run_cycle<double2>(S, reinterpret_cast<double2*>(base + oU), xs, r64, rn2, VIE_FP64,
                                        it_rhs.data(), &mv64, pinned, &still));
             ++cyc;
             x_is_zero = false;
         }
     }
     if (!all) VIE_TRY(residual());  // residual of the last iterate when the cycle cap was hit
+    VIE_TRY(support_scatter(h, R, xs, x, VIE_FP64, sp, st));
     if (flags & 2) {
-        // unpreconditioned residual ||b - A x|| / ||b||
-        VIE_TRY(matvec_device(h, R, x, t64, VIE_FP64, VIE_OP_A, st));
+        // unpreconditioned residual ||b - A x|| / ||b|| on the full grid
+        VIE_TRY(matvec_device(h, R, x, full0, VIE_FP64, VIE_OP_A, st));
         ++mv64;
-        VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(b, t64, r64, total));
-        VIE_TRY(S.norm2_64(r64, rn2));
-        VIE_TRY(S.norm2_64(b, bn2));
+        VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gtf, 256, 0, st>>>(b, full0, full1, total_full));
+        VIE_TRY(S.norm2_64(full1, rn2, nfull));
+        VIE_TRY(S.norm2_64(b, bn2, nfull));
         std::vector<double> a(R), c(R);
         VIE_CUDA(cudaMemcpyAsync(a.data(), rn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
         VIE_CUDA(cudaMemcpyAsync(c.data(), bn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
