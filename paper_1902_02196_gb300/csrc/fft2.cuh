@@ -103,7 +103,8 @@ __host__ __device__ constexpr int tpos(int L, int k) { return k / split_a(L) + (
 __host__ __device__ constexpr int freq_at(int L, int p) { return p / (L / split_a(L)) + split_a(L) * (p % (L / split_a(L))); }
 
 // Forward transform of NL lines, natural order in (elements l >= nin taken as zero and
-// not read), transposed order out.  Line n starts at s + off(n); elements at stride ES.
+// not read; nin <= L/2, so the upper half of every pass-1 input is zero at compile time),
+// transposed order out.  Line n starts at s + off(n); elements at stride ES.
 // tw[m] = exp(-2 pi i m / L).  Called by all NT threads; ends with a barrier.
 template <int L, int NT, class Off>
 __device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, const float2* tw, int nin) {
@@ -115,7 +116,7 @@ __device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, cons
 #pragma unroll
         for (int a = 0; a < A; ++a) {
             const int l = b + B * a;
-            v[a] = l < nin ? ln[l * ES] : make_float2(0.f, 0.f);
+            v[a] = (a < A / 2 && l < nin) ? ln[l * ES] : make_float2(0.f, 0.f);
         }
         DFT<A>::run(v, -1);
 #pragma unroll
@@ -138,7 +139,7 @@ __device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, cons
 }
 
 // Inverse (unnormalised) transform of NL lines, transposed order in, natural order out;
-// only outputs l < nout are written.  Called by all NT threads; ends with a barrier.
+// only outputs l < nout (<= L/2) are written.  Called by all NT threads; ends with a barrier.
 template <int L, int NT, class Off>
 __device__ __forceinline__ void inverse(float2* s, int NL, Off off, int ES, const float2* tw, int nout) {
     constexpr int A = Split<L>::A, B = Split<L>::B;
@@ -163,7 +164,7 @@ __device__ __forceinline__ void inverse(float2* s, int NL, Off off, int ES, cons
         for (int k1 = 0; k1 < A; ++k1) v[k1] = ln[(b + B * k1) * ES];
         DFT<A>::run(v, +1);
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
+        for (int a = 0; a < A / 2; ++a) {
             const int l = b + B * a;
             if (l < nout) ln[l * ES] = v[a];
         }

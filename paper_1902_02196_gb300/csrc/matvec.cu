@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(kXYThreads, 2)
             float2 v[A];
 #pragma unroll
             for (int a = 0; a < A; ++a) {
-                const int yy = b + B * a;
-                v[a] = yy < ny ? col[yy * RS] : make_float2(0.f, 0.f);
+                const int yy = b + B * a;  // ny <= L/2: the upper half is zero
+                v[a] = (a < A / 2 && yy < ny) ? col[yy * RS] : make_float2(0.f, 0.f);
             }
             fft2::DFT<A>::run(v, -1);
 #pragma unroll
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kXYThreads, 2)
             fft2::DFT<A>::run(v, +1);
             float2* col = xr + pos[k * CW + c];
 #pragma unroll
-            for (int a = 0; a < A; ++a) {
+            for (int a = 0; a < A / 2; ++a) {  // ny <= L/2
                 const int yy = b + B * a;
                 if (yy < ny) col[yy * RS] = v[a];
             }
@@ -394,7 +394,7 @@ template <int LZ>
 struct ZFCfg {
     static constexpr int GS = LZ * kZTile + 4;  // component stride: 4 float2 of padding keep half-warps apart
     static constexpr int BUF = 12 * GS;
-    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 2 * 60);
+    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 4 * 60);
 };
 
 // the 60 Green values of one octant point, streamed from the [..][60] layout
@@ -408,18 +408,24 @@ __device__ __forceinline__ void load_green(float2* u, const float2* __restrict__
     }
 }
 
-__device__ __forceinline__ float2 flip(float2 v, unsigned mask, int a) { return ((mask >> a) & 1u) ? cneg(v) : v; }
+// sign flip of a complex value by XOR of the sign bits: sbit is 0 or 0x80000000
+__device__ __forceinline__ float2 xflip(float2 v, unsigned sbit) {
+    return make_float2(__uint_as_float(__float_as_uint(v.x) ^ sbit), __uint_as_float(__float_as_uint(v.y) ^ sbit));
+}
+__device__ __forceinline__ unsigned sign_bit(unsigned mask, int a) { return (mask << (31 - a)) & 0x80000000u; }
 
 // y = B x at the two mirror columns c, c + 1 of one z position (float4 accesses); m0, m1
-// are the components whose sign flips at each column's reflected frequency point.
-// u: the 60 Green values (registers, or shared memory).
-__device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, int off, unsigned m0, unsigned m1) {
+// are the components whose sign flips at each column's reflected frequency point; wmask
+// selects the columns written back (3: both; 1 or 2: one, for columns with their own
+// Green values).  u: the 60 Green values (registers).
+__device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, int off, unsigned m0, unsigned m1,
+                                           int wmask) {
     float2 x0[12], x1[12];
 #pragma unroll
     for (int b = 0; b < 12; ++b) {
         const float4 v = *reinterpret_cast<const float4*>(s + b * gs + off);
-        x0[b] = flip(make_float2(v.x, v.y), m0, b);
-        x1[b] = flip(make_float2(v.z, v.w), m1, b);
+        x0[b] = xflip(make_float2(v.x, v.y), sign_bit(m0, b));
+        x1[b] = xflip(make_float2(v.z, v.w), sign_bit(m1, b));
     }
 #pragma unroll
     for (int H = 0; H < 2; ++H) {
@@ -439,29 +445,16 @@ __device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, i
         }
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
-            const float2 r0 = flip(a0[a], m0, a + 6 * H), r1 = flip(a1[a], m1, a + 6 * H);
-            *reinterpret_cast<float4*>(s + (a + 6 * H) * gs + off) = make_float4(r0.x, r0.y, r1.x, r1.y);
+            const float2 r0 = xflip(a0[a], sign_bit(m0, a + 6 * H)), r1 = xflip(a1[a], sign_bit(m1, a + 6 * H));
+            float2* d = s + (a + 6 * H) * gs + off;
+            if (wmask == 3)
+                *reinterpret_cast<float4*>(d) = make_float4(r0.x, r0.y, r1.x, r1.y);
+            else if (wmask == 1)
+                d[0] = r0;
+            else
+                d[1] = r1;
         }
     }
-}
-
-// y = B x at one column of one z position
-__device__ __forceinline__ void single_point(const float2* u, float2* s, int gs, int off, unsigned m) {
-    float2 xv[12], acc[12];
-#pragma unroll
-    for (int b = 0; b < 12; ++b) xv[b] = flip(s[b * gs + off], m, b);
-#pragma unroll
-    for (int a = 0; a < 12; ++a) acc[a] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int t = 0; t < 60; ++t) {
-#pragma unroll
-        for (int i = kBlock.start[t]; i < kBlock.start[t + 1]; ++i) {
-            const int a = kBlock.e[i].a, b = kBlock.e[i].b;
-            cfma(acc[a], kBlock.e[i].s > 0 ? u[t] : cneg(u[t]), xv[b]);
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 12; ++a) s[a * gs + off] = flip(acc[a], m, a);
 }
 
 template <int LZ>
@@ -471,7 +464,7 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const fl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sb = reinterpret_cast<float2*>(smem_raw);
     float2* tw = sb + 2 * BUF;
-    float2* gsec = tw + LZ;  // [2][60] Green values of kz = LZ/2 for the two column pairs
+    float2* gsec = tw + LZ;  // [2 pairs][2 sets][60] Green values of the item that holds kz = LZ/2
     const int tid = threadIdx.x;
     for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
     const int ntile = z.Lx / TB;
@@ -518,17 +511,23 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const fl
         else
             pb = B - k2;
     }
+    const int kxo0 = kx0 <= z.Lx / 2 ? kx0 : z.Lx - kx0, kxo1 = kx1 <= z.Lx / 2 ? kx1 : z.Lx - kx1;
+    const float2* gcol0 = z.green_t + ((long long)kyo * z.Ox + kxo0) * z.Oz * 60;
+    const float2* gcol1 = z.green_t + ((long long)kyo * z.Ox + kxo1) * z.Oz * 60;
+    // the item's frequency points: up to two sharing one octant point (pa, pb), and pc
+    // (kz = LZ/2) with its own; its Green values go to shared memory, next to a copy of
+    // the first set, so that one register array serves all points of every item
     const int kza = pa >= 0 ? fft2::freq_at(LZ, pa) : 0;
     const int kzoa = kza <= LZ / 2 ? kza : LZ - kza;
-    const int kxo0 = kx0 <= z.Lx / 2 ? kx0 : z.Lx - kx0;
-    const float2* gcol = z.green_t + ((long long)kyo * z.Ox + kxo0) * z.Oz * 60;
     float2 u[60];
     if (pa >= 0 && !single) {
-        load_green(u, gcol + (long long)kzoa * 60);
-        if (pc >= 0) {
-            const float2* g2 = gcol + (long long)(LZ / 2) * 60;
-            for (int t = 0; t < 60; ++t) gsec[ci * 60 + t] = g2[t];
-        }
+        load_green(u, gcol0 + (long long)kzoa * 60);
+        if (pc >= 0)
+#pragma unroll
+            for (int t = 0; t < 60; ++t) {
+                gsec[(2 * ci) * 60 + t] = u[t];
+                gsec[(2 * ci + 1) * 60 + t] = gcol0[(long long)(LZ / 2) * 60 + t];
+            }
     }
 
     issue(0, sb);
@@ -544,34 +543,27 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const fl
         __syncthreads();
         fft2::forward<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
         if (pa >= 0) {
-            const unsigned fza = kza > LZ / 2 ? z.mz : 0u;
-            if (!single) {
-                pair_point(u, s, GS, pa * TB + 2 * ci, fy ^ fza ^ fx0, fy ^ fza ^ fx1);
-                if (pb >= 0) {
-                    const unsigned fzb = fft2::freq_at(LZ, pb) > LZ / 2 ? z.mz : 0u;
-                    pair_point(u, s, GS, pb * TB + 2 * ci, fy ^ fzb ^ fx0, fy ^ fzb ^ fx1);
+            // points (position, Green set): (pa, 0), (pb, 0), (pc, 1); single columns take
+            // each column in turn with its own Green values, loaded from global memory
+#pragma unroll 1
+            for (int q = 0; q < (single ? 6 : 3); ++q) {
+                const int e = single ? q % 3 : q, col = single ? q / 3 : 0;
+                const int pp = e == 0 ? pa : (e == 1 ? pb : pc);
+                if (pp < 0) continue;
+                const int kz = fft2::freq_at(LZ, pp);
+                if (single) {
+                    const int kzo = kz <= LZ / 2 ? kz : LZ - kz;
+                    load_green(u, (col ? gcol1 : gcol0) + (long long)kzo * 60);
+                } else if (e == 2) {
+#pragma unroll
+                    for (int t = 0; t < 60; ++t) u[t] = gsec[(2 * ci + 1) * 60 + t];
                 }
-                if (pc >= 0) pair_point(gsec + ci * 60, s, GS, pc * TB + 2 * ci, fy ^ fx0, fy ^ fx1);
-            } else {
-#pragma unroll 1
-                for (int g = 0; g < (pc >= 0 ? 2 : 1); ++g) {
-#pragma unroll 1
-                    for (int col = 0; col < 2; ++col) {
-                        const int pp0 = g ? pc : pa, pp1 = g ? -1 : pb;
-                        const int kz = fft2::freq_at(LZ, pp0);
-                        const int kzo = kz <= LZ / 2 ? kz : LZ - kz;
-                        const int kx = col ? kx1 : kx0;
-                        const int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
-                        load_green(u, z.green_t + (((long long)kyo * z.Ox + kxo) * z.Oz + kzo) * 60);
-#pragma unroll 1
-                        for (int e = 0; e < 2; ++e) {
-                            const int pp = e ? pp1 : pp0;
-                            if (pp < 0) break;
-                            const unsigned fz = fft2::freq_at(LZ, pp) > LZ / 2 ? z.mz : 0u;
-                            single_point(u, s, GS, pp * TB + 2 * ci + col, fy ^ fz ^ (col ? fx1 : fx0));
-                        }
-                    }
-                }
+                const unsigned fz = kz > LZ / 2 ? z.mz : 0u;
+                pair_point(u, s, GS, pp * TB + 2 * ci, fy ^ fz ^ fx0, fy ^ fz ^ fx1, single ? 1 + col : 3);
+            }
+            if (pc >= 0 && !single) {
+#pragma unroll
+                for (int t = 0; t < 60; ++t) u[t] = gsec[(2 * ci) * 60 + t];
             }
         }
         __syncthreads();
