@@ -230,6 +230,70 @@ int vie_stats_reset(int enable_timing);
 int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, double* bytes, int* n_entries,
                    long long* total_launches);
 
+/*
+ * Serving: a request loop with continuous batching (no counterpart in the paper, which
+ * runs one solve at a time).  A request is one dielectric solve of the method: setup of
+ * the grid, voxel size, frequency and material map (as vie_setup), nrhs dipole
+ * right-hand sides (as vie_rhs_dipoles), GMRES (as vie_solve, flags 0) and the fields
+ * and absorbed power (as vie_fields).  Up to max_concurrent requests run at once, each
+ * on its own host thread and CUDA stream, so their kernels overlap on the device; when
+ * one finishes, the next admissible request starts at once.  A request is admitted when
+ * its device working set, plus its Green tensors if not yet cached, fits in the budget
+ * (least recently used idle Green tensors are evicted first); requests are served in
+ * submission order, except that a later request may start ahead of one that does not
+ * fit yet (at most 4 times per waiting request).  Green tensors depend only on (grid,
+ * voxel size, frequency): each key is built once and shared by every request with it.
+ * Each result is the one the four calls above give on their own.
+ */
+typedef struct vie_server vie_server;
+
+typedef struct {
+    vie_grid grid;
+    double freq_hz;
+    const double* eps_real;  /* [nz][ny][nx] host, copied by vie_submit */
+    const double* sigma;     /* [nz][ny][nx] host (S/m), copied by vie_submit */
+    int nrhs;
+    const double* dip_pos;   /* [nrhs][3] host positions (m), copied */
+    const double* dip_mom;   /* [nrhs][3] host moments (A m), copied */
+    double tol;              /* GMRES tolerance (as vie_solve) */
+    int restart, maxit, mode;
+    /* optional caller-owned host outputs (NULL to skip), written before the result is
+       ready; they must stay valid until vie_poll has returned the result */
+    void* x_out;             /* [nrhs][12][nz][ny][nx] C128 solution */
+    double* p_abs_out;       /* [nrhs][nz][ny][nx] absorbed power density (W/m^3) */
+    double* P_abs_out;       /* [nrhs] absorbed power (W) */
+} vie_request;
+
+typedef struct {
+    int status;        /* VIE_OK, VIE_NOT_CONVERGED, or the negative error of the failed step */
+    int nrhs;
+    int iterations;    /* largest GMRES iteration count over the right-hand sides */
+    int green_cached;  /* 1 when the request found its Green tensors in the cache */
+    double queued_s;   /* seconds from vie_submit to the start of the solve */
+    double run_s;      /* seconds of setup, solve and post-processing */
+    double resid;      /* largest final relative residual */
+} vie_result;
+
+/*
+ * vie_server_create -- start a request loop on the current device.
+ *   hbm_budget_bytes : device memory the loop may use for working sets and cached
+ *                      Green tensors; 0 = 85% of the free memory now
+ *   max_concurrent   : requests in flight at once, 1..64
+ * VIE_EINVAL for a budget above the free memory or a bad count.
+ */
+int vie_server_create(size_t hbm_budget_bytes, int max_concurrent, vie_server** out);
+/* Stops the loop: queued requests are dropped, running ones finish first; frees the cache. */
+void vie_server_destroy(vie_server* s);
+/* Queue a request (its host inputs are copied); *ticket identifies it.  VIE_ENOMEM when
+   it could never fit in the budget, VIE_EINVAL for invalid fields. */
+int vie_submit(vie_server* s, const vie_request* req, unsigned long long* ticket);
+/* Wait at most timeout_us (>= 0) microseconds for the request: VIE_OK with *out filled
+   (the ticket is then retired), VIE_ETIMEOUT when it is still queued or running,
+   VIE_EINVAL for an unknown or retired ticket. */
+int vie_poll(vie_server* s, unsigned long long ticket, int timeout_us, vie_result* out);
+/* Snapshot: queued requests, requests running, device bytes reserved, cached Green keys. */
+int vie_server_stats(vie_server* s, int* queued, int* running, size_t* bytes_in_use, int* cache_entries);
+
 /* Static description of an error code. */
 const char* vie_strerror(int code);
 

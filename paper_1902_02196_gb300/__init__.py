@@ -26,6 +26,7 @@ EXPORTS = (
     "vie_setup", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
     "vie_fields", "vie_green_toeplitz", "vie_info", "vie_strerror", "vie_last_error",
     "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc",
+    "vie_server_create", "vie_server_destroy", "vie_submit", "vie_poll", "vie_server_stats",
 )
 
 
@@ -38,6 +39,23 @@ class vie_solve_info(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
                 ("fp32_matvecs", ctypes.c_int), ("refinements", ctypes.c_int), ("resid", ctypes.c_double),
                 ("true_resid", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class vie_request(ctypes.Structure):
+    _fields_ = [("grid", vie_grid), ("freq_hz", ctypes.c_double), ("eps_real", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("dip_pos", ctypes.c_void_p),
+                ("dip_mom", ctypes.c_void_p), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("mode", ctypes.c_int), ("x_out", ctypes.c_void_p),
+                ("p_abs_out", ctypes.c_void_p), ("P_abs_out", ctypes.c_void_p)]
+
+
+class vie_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nrhs", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("green_cached", ctypes.c_int), ("queued_s", ctypes.c_double), ("run_s", ctypes.c_double),
+                ("resid", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +104,12 @@ def _lib():
     lib.vie_stats_read.argtypes = [I, P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]
     lib.vie_last_error.argtypes = []
     lib.vie_last_error.restype = ctypes.c_char_p
+    lib.vie_server_create.argtypes = [S, I, ctypes.POINTER(P)]
+    lib.vie_server_destroy.argtypes = [P]
+    lib.vie_server_destroy.restype = None
+    lib.vie_submit.argtypes = [P, ctypes.POINTER(vie_request), ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.vie_poll.argtypes = [P, ctypes.c_ulonglong, I, ctypes.POINTER(vie_result)]
+    lib.vie_server_stats.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(S), ctypes.POINTER(I)]
     _LIB = lib
     return lib
 
@@ -245,3 +269,73 @@ def vie_stats_read(max_entries=256):
         nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (launches[i], ms[i], nbytes[i])
     return tot.value, out
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+class Server:
+    """The request loop of vie_server_create (arguments marshalled; the loop itself is native)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_concurrent=4):
+        p = ctypes.c_void_p()
+        _check(_lib().vie_server_create(int(hbm_budget_bytes), int(max_concurrent), ctypes.byref(p)),
+               "vie_server_create")
+        self._p = p
+        self._keep = {}
+
+    def close(self):
+        if self._p:
+            _lib().vie_server_destroy(self._p)
+            self._p = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, grid, freq_hz, eps_real, sigma, pos, mom, tol=1e-6, restart=50, maxit=30,
+               mode=VIE_SOLVE_FP32_REFINE, x_out=None, p_abs_out=None, P_abs_out=None):
+        """Queue one solve; host NumPy inputs (float64), optional host outputs.  Returns the ticket."""
+        import numpy as np
+
+        eps = np.ascontiguousarray(eps_real, dtype=np.float64)
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        mom = np.ascontiguousarray(mom, dtype=np.float64).reshape(-1, 3)
+        for o in (x_out, p_abs_out, P_abs_out):
+            if o is not None and not (isinstance(o, np.ndarray) and o.flags["C_CONTIGUOUS"]):
+                raise ValueError("outputs must be C-contiguous NumPy arrays")
+        r = vie_request()
+        r.grid = vie_grid(*grid)
+        r.freq_hz = float(freq_hz)
+        r.eps_real, r.sigma = eps.ctypes.data, sig.ctypes.data
+        r.nrhs = pos.shape[0]
+        r.dip_pos, r.dip_mom = pos.ctypes.data, mom.ctypes.data
+        r.tol, r.restart, r.maxit, r.mode = float(tol), int(restart), int(maxit), int(mode)
+        r.x_out = _ptr(x_out)
+        r.p_abs_out = _ptr(p_abs_out)
+        r.P_abs_out = _ptr(P_abs_out)
+        t = ctypes.c_ulonglong()
+        _check(_lib().vie_submit(self._p, ctypes.byref(r), ctypes.byref(t)), "vie_submit")
+        self._keep[t.value] = (x_out, p_abs_out, P_abs_out)  # outputs stay alive until polled
+        return t.value
+
+    def poll(self, ticket, timeout_us=0):
+        """Result dict when the request is done, None when it is still queued or running."""
+        res = vie_result()
+        rc = _lib().vie_poll(self._p, ctypes.c_ulonglong(ticket), int(timeout_us), ctypes.byref(res))
+        if rc == VIE_ETIMEOUT:
+            return None
+        _check(rc, "vie_poll")
+        self._keep.pop(ticket, None)
+        return res.as_dict()
+
+    def stats(self):
+        q, r, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        b = ctypes.c_size_t()
+        _check(_lib().vie_server_stats(self._p, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c)),
+               "vie_server_stats")
+        return dict(queued=q.value, running=r.value, bytes_in_use=b.value, cache_entries=c.value)

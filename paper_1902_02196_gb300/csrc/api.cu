@@ -91,13 +91,15 @@ void release(vie_handle* h) {
     cudaFree(h->chi32);
     cudaFree(h->tau32);
     cudaFree(h->ieps32);
-    cudaFree(h->green64);
-    cudaFree(h->green32);
-    cudaFree(h->green32t);
-    cudaFree(h->colmap);
-    cudaFree(h->tw64);
-    cudaFree(h->tw32);
-    cudaFree(h->toeplitz);
+    if (!h->shared_green) {
+        cudaFree(h->green64);
+        cudaFree(h->green32);
+        cudaFree(h->green32t);
+        cudaFree(h->colmap);
+        cudaFree(h->tw64);
+        cudaFree(h->tw32);
+        cudaFree(h->toeplitz);
+    }
     cudaFree(h->fft_ws.ptr);
     cudaFree(h->stage_ws.ptr);
     cudaFree(h->solve_ws.ptr);
@@ -158,6 +160,21 @@ int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, cons
     g_last_error.clear();
     REQUIRE(out, "out is NULL");
     *out = nullptr;
+    REQUIRE(flags == 0, "flags must be 0");
+    return handle_create(grid, freq_hz, eps_real, sigma, nullptr, out);
+}
+
+}  // extern "C"
+
+size_t handle_green_bytes(const vie_handle* h) {
+    const size_t ov = (size_t)h->O[0] * h->O[1] * h->O[2];
+    return 60 * ov * (sizeof(double2) + 2 * sizeof(float2)) + 60 * h->nv * sizeof(double2) +
+           2048 * (sizeof(double2) + sizeof(float2)) + 2 * (size_t)h->L[0];
+}
+
+int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
+                  const vie_handle* share, vie_handle** out) {
+    *out = nullptr;
     REQUIRE(grid && eps_real && sigma, "NULL argument");
     REQUIRE(grid->nx >= 1 && grid->ny >= 1 && grid->nz >= 1, "grid sizes must be >= 1");
     REQUIRE(grid->nx <= 512 && grid->ny <= 512 && grid->nz <= 512, "grid sizes above 512 are not supported");
@@ -165,7 +182,10 @@ int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, cons
                 grid->dy > 0 && grid->dz > 0,
             "voxel sizes must be finite and positive");
     REQUIRE(std::isfinite(freq_hz) && freq_hz > 0, "frequency must be finite and positive");
-    REQUIRE(flags == 0, "flags must be 0");
+    REQUIRE(!share || (share->nx == grid->nx && share->ny == grid->ny && share->nz == grid->nz &&
+                       share->dx == grid->dx && share->dy == grid->dy && share->dz == grid->dz &&
+                       share->freq == freq_hz),
+            "template handle has another grid, voxel size or frequency");
     vie_handle* h = new (std::nothrow) vie_handle();
     if (!h) {
         set_error("host allocation failed");
@@ -235,11 +255,25 @@ int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, cons
     cudaStreamSynchronize(h->stream);
     cudaFree(dmat);
     if (rc < 0) return fail(rc);
+    if (share) {
+        h->shared_green = 1;
+        h->green64 = share->green64;
+        h->green32 = share->green32;
+        h->green32t = share->green32t;
+        h->colmap = share->colmap;
+        h->tw64 = share->tw64;
+        h->tw32 = share->tw32;
+        h->toeplitz = share->toeplitz;
+        *out = h;
+        return VIE_OK;
+    }
     if ((rc = twiddle_setup(h)) < 0) return fail(rc);
     if ((rc = green_setup(h)) < 0) return fail(rc);
     *out = h;
     return VIE_OK;
 }
+
+extern "C" {
 
 void vie_destroy(vie_handle* h) {
     if (!h) return;

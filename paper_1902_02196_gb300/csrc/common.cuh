@@ -124,7 +124,18 @@ struct vie_handle {
     Workspace support_ws;  // support rows of the current solve
     double2* toeplitz;   // [60][nz][ny][nx] Toeplitz tensors of N - G for offsets d >= 0
     size_t bytes_held;
+    // set when green64/32/32t, toeplitz, the twiddle tables and colmap belong to another
+    // handle (a template kept in a server's Green cache) and must not be freed with this one
+    int shared_green;
 };
+
+// vie_setup with an optional template: when share != NULL the new handle takes the
+// template's Green tensors, twiddles and column map (same grid, voxel and frequency
+// required) and computes only its own material maps.
+int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
+                  const vie_handle* share, vie_handle** out);
+// device bytes held by a handle's Green tensors, twiddles and column map (shared part)
+size_t handle_green_bytes(const vie_handle* h);
 
 // ---------------------------------------------------------------------------
 // Error reporting

@@ -597,12 +597,9 @@ static int launch_line_L(const char* name, const vie_handle* h, const LineArgs& 
                          cudaStream_t s) {
     constexpr int TB = LineCfg<L>::TB, NT = LineCfg<L>::NT;
     size_t smem = line_fft_smem_bytes<T, L>();
-    static bool configured = false;
-    if (!configured) {
-        VIE_CUDA(cudaFuncSetAttribute(line_fft_kernel<T, L, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        configured = true;
-    }
+    // set on every call: the attribute is per device and launches may come from several threads
+    VIE_CUDA(cudaFuncSetAttribute(line_fft_kernel<T, L, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     long long blocks = (long long)a.na * ((a.nb + TB - 1) / TB);
     if (blocks <= 0) return VIE_OK;
     if (blocks > 0x7fffffffLL) {
@@ -644,11 +641,8 @@ static int launch_z_L(const char* name, const vie_handle* h, const ZArgs& z, cud
     using C = typename CT<T>::C;
     constexpr int TB = ZCfg<T, L>::TB;
     size_t smem = sizeof(C) * (size_t)(12 * ZCfg<T, L>::GS + L);
-    static bool configured = false;
-    if (!configured) {
-        VIE_CUDA(cudaFuncSetAttribute(zpass_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
+    // set on every call: the attribute is per device and launches may come from several threads
+    VIE_CUDA(cudaFuncSetAttribute(zpass_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     long long blocks = (long long)z.Ly * ((z.Lx + TB - 1) / TB);
     const double bytes = (double)sizeof(C) * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
     VIE_KLAUNCH_B(name, s, bytes,
@@ -684,12 +678,9 @@ template <int L>
 static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
                        const MatvecEpi& e, const Support& sp, double in_elems, cudaStream_t s) {
     constexpr size_t smem = XYCfg<L>::smem;
-    static bool configured = false;
-    if (!configured) {
-        VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
+    // set on every call: the attribute is per device and launches may come from several threads
+    VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (planes > 0x7fffffffLL) {
         set_error("xy transform grid too large");
         return VIE_EINVAL;
@@ -726,11 +717,8 @@ static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, l
 template <int LZ>
 static int launch_zf_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
     constexpr size_t smem = ZFCfg<LZ>::smem;
-    static bool configured = false;
-    if (!configured) {
-        VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
+    // set on every call: the attribute is per device and launches may come from several threads
+    VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long blocks = (long long)z.Ly * (z.Lx / kZTile);
     const double bytes = 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
     VIE_KLAUNCH_B("zpass_block_f32", s, bytes,
