@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serving", type=int, default=0, metavar="N",
+                    help="serving stream: N requests (grids from --serving-sizes, 1-32 dipoles, 64/128/298 MHz), "
+                         "first all at once (capacity), then as Poisson arrivals at 0.8x that capacity "
+                         "(p50/p99 latency); prints one JSON line")
+    ap.add_argument("--serving-sizes", default="32,48,64",
+                    help="grid sizes n of the n^3 serving requests (the stream's full set is 32,48,64,96)")
+    ap.add_argument("--serving-slots", type=int, default=4, help="requests in flight at once")
     ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
                     help="profiling mode: set up the head64 workload and run N batched FP32 matvecs and one FP64 "
                          "matvec (16 RHS), print their timings; the solve benchmark is not run")
@@ -521,9 +528,89 @@ def run_matvec_only(args, local):
     h.close()
 
 
+def run_serving(args, local):
+    """Request loop (vie_submit / vie_poll) on a stream of head-phantom solves."""
+    import numpy as np
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import serving_stream
+
+    torch.cuda.set_device(local)
+    vie.build()
+    sizes = tuple(int(v) for v in args.serving_sizes.split(","))
+    reqs = serving_stream(args.serving, seed=77, sizes=sizes)
+
+    def submit(srv, r):
+        g = r["grid"]
+        return srv.submit((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), r["freq"], r["eps_real"], r["sigma"], r["dip_pos"],
+                          r["dip_mom"], tol=TOL, restart=RESTART, maxit=MAXIT, mode=vie.VIE_SOLVE_FP32_REFINE)
+
+    def collect(srv, pending, t0, done):
+        while pending:
+            for t in list(pending):
+                res = srv.poll(t, timeout_us=2000)
+                if res is not None:
+                    done.append((pending.pop(t), res, time.perf_counter() - t0))
+
+    # warm-up: one small request (library load, kernel attributes)
+    srv = vie.Server(max_concurrent=args.serving_slots)
+    w = serving_stream(1, seed=5, sizes=(32,))[0]
+    w["dip_pos"], w["dip_mom"] = w["dip_pos"][:1], w["dip_mom"][:1]
+    collect(srv, {submit(srv, w): -1}, time.perf_counter(), [])
+    srv.close()
+    # closed loop: everything submitted at once, on a fresh loop (cold Green cache)
+    srv = vie.Server(max_concurrent=args.serving_slots)
+    t0 = time.perf_counter()
+    pending = {submit(srv, r): i for i, r in enumerate(reqs)}
+    closed = []
+    collect(srv, pending, t0, closed)
+    span = max(c[2] for c in closed)
+    srv.close()
+    cap = len(reqs) / span
+    # open loop: Poisson arrivals at 0.8 x the measured capacity, fresh loop
+    lam = 0.8 * cap
+    srv = vie.Server(max_concurrent=args.serving_slots)
+    t0 = time.perf_counter()
+    pending, opened, sub_t, tnext = {}, [], {}, 0.0
+    for i, r in enumerate(reqs):
+        tnext += r["gap"] / lam
+        while time.perf_counter() - t0 < tnext:
+            for t in list(pending):
+                res = srv.poll(t, timeout_us=0)
+                if res is not None:
+                    opened.append((pending.pop(t), res, time.perf_counter() - t0))
+            time.sleep(0.001)
+        t = submit(srv, r)
+        pending[t] = i
+        sub_t[i] = time.perf_counter() - t0
+    collect(srv, pending, t0, opened)
+    span_o = max(c[2] for c in opened)
+    srv.close()
+    lat = np.array([c[1]["queued_s"] + c[1]["run_s"] for c in opened]) * 1000.0
+    rhs = sum(int(r["dip_pos"].shape[0]) for r in reqs)
+    status = [c[1]["status"] for c in closed + opened]
+    line = dict(mode="serving", metric="serving stream: solves/s and p50/p99 request latency", unit="solves/s",
+                requests=len(reqs), right_hand_sides=rhs, slots=args.serving_slots,
+                sizes=list(sizes), freqs_mhz=[64, 128, 298], tol=TOL, data="synthetic",
+                closed_loop=dict(seconds=span, requests_per_s=cap, solves_per_s=rhs / span,
+                                 green_cache_hits=sum(c[1]["green_cached"] for c in closed)),
+                open_loop=dict(arrival_rate_per_s=lam, seconds=span_o, solves_per_s=rhs / span_o,
+                               latency_ms=dict(p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99)),
+                                               max=float(lat.max())),
+                               green_cache_hits=sum(c[1]["green_cached"] for c in opened)),
+                all_ok=all(s in (vie.VIE_OK,) for s in status),
+                max_iterations=max(c[1]["iterations"] for c in closed + opened))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
+    if args.serving:
+        if rank == 0:
+            run_serving(args, local)
+        return
     if args.matvec_only:
         run_matvec_only(args, local)
         return

@@ -21,4 +21,5 @@ from .phantoms import (  # noqa: F401
     random_coefficients,
     workload,
     WORKLOADS,
+    serving_stream,
 )

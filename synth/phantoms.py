@@ -223,3 +223,21 @@ def workload(name, n=None):
     else:
         raise KeyError(name)
     return dict(grid=g, freq=w["freq"], eps_real=eps, sigma=sig, dip_pos=pos, dip_mom=mom)
+
+
+def serving_stream(n_requests, seed=77, sizes=(32, 48, 64, 96)):
+    """Requests of the serving stream: grid n^3 from `sizes` (voxel 192 mm / n, head phantom with a
+    per-request tissue seed), 1..32 z-dipoles on the 15 cm ring, frequency from {64, 128, 298} MHz,
+    and unit-rate exponential inter-arrival gaps (scale them by 1/lambda)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_requests):
+        n = int(rng.choice(sizes))
+        R = int(rng.integers(1, 33))
+        f = float(rng.choice([64e6, 128e6, 298e6]))
+        g = _head_grid(n)
+        eps, sig = head_phantom(g, seed=int(rng.integers(0, 2**31 - 1)))
+        pos, mom = ring_dipoles(R, 0.15)
+        out.append(dict(grid=g, freq=f, eps_real=eps, sigma=sig, dip_pos=pos, dip_mom=mom,
+                        gap=float(rng.exponential(1.0))))
+    return out
