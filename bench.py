@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--serving-sizes", default="32,48,64",
                     help="grid sizes n of the n^3 serving requests (the stream's full set is 32,48,64,96)")
     ap.add_argument("--serving-slots", type=int, default=4, help="requests in flight at once")
+    ap.add_argument("--config-run", default="", metavar="NAME",
+                    help="one mixed-precision and one plain FP64 solve of a named workload (body128: the "
+                         "body-scale stack; incl64: the high-contrast inclusions), with iteration counts, "
+                         "times and the mixed-vs-FP64 difference; prints one JSON line")
     ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
                     help="profiling mode: set up the head64 workload and run N batched FP32 matvecs and one FP64 "
                          "matvec (16 RHS), print their timings; the solve benchmark is not run")
@@ -604,9 +608,80 @@ def run_serving(args, local):
     print(json.dumps(line), flush=True)
 
 
+def run_config(args, local):
+    """Mixed vs plain FP64 on one named workload (precision stress / body scale)."""
+    import numpy as np
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vie.build()
+    w = workload(args.config_run)
+    g = w["grid"]
+    R = int(w["dip_pos"].shape[0])
+    t0 = time.perf_counter()
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), w["freq"], w["eps_real"], w["sigma"])
+    setup_s = time.perf_counter() - t0
+    L, _ = vie.vie_info(h)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    shape = (R, 12) + g.shape
+    e_inc = torch.empty(shape, dtype=torch.complex128, device=dev)
+    b = torch.empty_like(e_inc)
+    vie.vie_rhs_dipoles(h, w["dip_pos"], w["dip_mom"], e_inc, b, stream=stream)
+    out = dict(mode="config-run", workload=args.config_run, grid=[g.nx, g.ny, g.nz], fft=list(L), nrhs=R,
+               freq_mhz=w["freq"] / 1e6, tol=TOL, restart=RESTART, setup_s=setup_s, data="synthetic")
+    sol = {}
+    for name, mode in (("mixed", vie.VIE_SOLVE_FP32_REFINE), ("fp64", vie.VIE_SOLVE_FP64)):
+        if name == "fp64" and args.no_fp64:
+            continue
+        x = torch.empty_like(b)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        rc, info = vie.vie_solve(h, b, x, tol=TOL, restart=RESTART, maxit=200, mode=mode, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pa = torch.empty((R,) + g.shape, dtype=torch.float64, device=dev)
+        P = vie.vie_fields(h, x, e_inc, None, pa, stream=stream)
+        sec = a0.elapsed_time(a1) / 1000.0
+        sol[name] = (x, np.asarray(P))
+        out[name] = dict(rc=rc, seconds=sec, solves_per_s=R / sec, iterations=max(i["iterations"] for i in info),
+                         fp64_matvecs=info[0]["fp64_matvecs"], fp32_matvecs=info[0]["fp32_matvecs"],
+                         max_resid=max(i["resid"] for i in info))
+    if "fp64" in sol:
+        xm, xd = sol["mixed"][0], sol["fp64"][0]
+        out["mixed_vs_fp64"] = dict(
+            x_rel=float(torch.linalg.vector_norm(xm - xd) / torch.linalg.vector_norm(xd)),
+            P_abs_rel_max=float(np.max(np.abs(sol["mixed"][1] - sol["fp64"][1]) / np.abs(sol["fp64"][1]))))
+        out["speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    x32 = torch.randn(shape, dtype=torch.complex64, device=dev)
+    y32 = torch.empty_like(x32)
+    for _ in range(2):
+        vie.vie_matvec(h, x32, y32, vie.VIE_FP32, vie.VIE_OP_PA, stream=stream)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(5):
+        vie.vie_matvec(h, x32, y32, vie.VIE_FP32, vie.VIE_OP_PA, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    mv = a0.elapsed_time(a1) / 5
+    mvb = matvec_alg_bytes((g.nx, g.ny, g.nz), L, R, 8)
+    out["matvec_fp32"] = dict(ms=mv, alg_gbs=mvb / (mv / 1000) / 1e9)
+    h.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
+    if args.config_run:
+        if rank == 0:
+            run_config(args, local)
+        return
     if args.serving:
         if rank == 0:
             run_serving(args, local)
