@@ -68,6 +68,9 @@ def parse():
                     help="one mixed-precision and one plain FP64 solve of a named workload (body128: the "
                          "body-scale stack; incl64: the high-contrast inclusions), with iteration counts, "
                          "times and the mixed-vs-FP64 difference; prints one JSON line")
+    ap.add_argument("--cufft-compare", action="store_true",
+                    help="time a matvec built from torch.fft (cuFFT) and torch.einsum on the head64 sizes beside "
+                         "vie_matvec (timing comparison only; its Green tensor is random data of the right shape)")
     ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
                     help="profiling mode: set up the head64 workload and run N batched FP32 matvecs and one FP64 "
                          "matvec (16 RHS), print their timings; the solve benchmark is not run")
@@ -675,9 +678,73 @@ def run_config(args, local):
     print(json.dumps(out), flush=True)
 
 
+def run_cufft_compare(args, local):
+    """cuFFT (torch.fft) + einsum matvec of the head64 batch, timed beside the library's FP32 matvec."""
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vie.build()
+    w = workload("head64")
+    g = w["grid"]
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), w["freq"], w["eps_real"], w["sigma"])
+    L, _ = vie.vie_info(h)
+    Lx, Ly, Lz = L
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    shape = (NRHS, 12) + g.shape
+    x = torch.randn(shape, dtype=torch.complex64, device=dev, generator=gen)
+    y = torch.empty_like(x)
+    B = torch.randn((12, 12, Lz, Ly, Lx), dtype=torch.complex64, device=dev, generator=gen)
+    c1 = torch.randn(g.shape, dtype=torch.complex64, device=dev, generator=gen)
+    c2 = torch.randn(g.shape, dtype=torch.complex64, device=dev, generator=gen)
+
+    def ours():
+        vie.vie_matvec(h, x, y, vie.VIE_FP32, vie.VIE_OP_PA, stream=stream)
+
+    xp = torch.zeros((NRHS, 12, Lz, Ly, Lx), dtype=torch.complex64, device=dev)
+
+    def cufft():
+        xp[:, :, :g.nz, :g.ny, :g.nx] = x
+        X = torch.fft.fftn(xp, dim=(-3, -2, -1))
+        Y = torch.einsum("abzyx,rbzyx->razyx", B, X)
+        yy = torch.fft.ifftn(Y, dim=(-3, -2, -1))[:, :, :g.nz, :g.ny, :g.nx]
+        return c1 * x - c2 * yy
+
+    def timeit(fn, n=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / n
+
+    t_ours = timeit(ours)
+    t_cufft = timeit(cufft)
+    # the transforms alone (pad + forward + inverse 3-D FFT of the batch)
+    t_fft = timeit(lambda: torch.fft.ifftn(torch.fft.fftn(xp, dim=(-3, -2, -1)), dim=(-3, -2, -1)))
+    h.close()
+    print(json.dumps(dict(mode="cufft-compare", workload="head64, 16 RHS", fft=list(L),
+                          ours_fp32_matvec_ms=t_ours, cufft_einsum_matvec_ms=t_cufft,
+                          cufft_fft_pair_only_ms=t_fft, ratio=t_cufft / t_ours)), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
+    if args.cufft_compare:
+        if rank == 0:
+            run_cufft_compare(args, local)
+        return
     if args.config_run:
         if rank == 0:
             run_config(args, local)

@@ -1,4 +1,4 @@
-// Two-pass FFT of lines held in shared memory, FP32, L = A * B with A, B in {2, 4, 8, 16}.
+// Two-pass FFT of lines held in shared memory (FP32 or FP64), L = A * B with A, B in {2, 4, 8, 16}.
 //
 // With l = b + B a (input index) and k = k1 + A k2 (output index), the DFT factors as
 //   X[k1 + A k2] = sum_b wB^(b k2) [ w^(b k1) sum_a wA^(a k1) x[b + B a] ],   w = exp(-2 pi i / L),
@@ -24,35 +24,38 @@
 
 namespace fft2 {
 
-constexpr float kC1 = 0.92387953251128674f;  // cos(pi/8)
-constexpr float kS1 = 0.38268343236508978f;  // sin(pi/8)
-constexpr float kC2 = 0.70710678118654752f;  // cos(pi/4)
+constexpr double kC1 = 0.92387953251128674;  // cos(pi/8)
+constexpr double kS1 = 0.38268343236508978;  // sin(pi/8)
+constexpr double kC2 = 0.70710678118654752;  // cos(pi/4)
 
-__device__ __forceinline__ float2 rot(float2 a, float c, float s) {  // a * (c + i s)
-    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+template <typename C>
+__device__ __forceinline__ C rot(C a, double c, double s) {  // a * (c + i s), in the precision of C
+    using R = decltype(a.x);
+    const R cr = (R)c, sr = (R)s;
+    return mk(a.x * cr - a.y * sr, a.x * sr + a.y * cr);
 }
 
-template <int N>
+template <int N, typename C = float2>
 struct DFT;
-template <>
-struct DFT<2> {
-    static __device__ __forceinline__ void run(float2* v, int) {
-        const float2 a = v[0], b = v[1];
+template <typename C>
+struct DFT<2, C> {
+    static __device__ __forceinline__ void run(C* v, int) {
+        const C a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     }
 };
-template <>
-struct DFT<4> {
-    static __device__ __forceinline__ void run(float2* v, int dir) { dft4(v[0], v[1], v[2], v[3], dir); }
+template <typename C>
+struct DFT<4, C> {
+    static __device__ __forceinline__ void run(C* v, int dir) { dft4(v[0], v[1], v[2], v[3], dir); }
 };
-template <>
-struct DFT<8> {
-    static __device__ __forceinline__ void run(float2* v, int dir) {
-        float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+template <typename C>
+struct DFT<8, C> {
+    static __device__ __forceinline__ void run(C* v, int dir) {
+        C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
         dft4(e[0], e[1], e[2], e[3], dir);
         dft4(o[0], o[1], o[2], o[3], dir);
-        const float d = (float)dir;
+        const double d = (double)dir;
         o[1] = rot(o[1], kC2, d * kC2);
         o[2] = cmul_i(o[2], dir);
         o[3] = rot(o[3], -kC2, d * kC2);
@@ -63,18 +66,18 @@ struct DFT<8> {
         }
     }
 };
-template <>
-struct DFT<16> {
-    static __device__ __forceinline__ void run(float2* v, int dir) {
-        float2 e[8], o[8];
+template <typename C>
+struct DFT<16, C> {
+    static __device__ __forceinline__ void run(C* v, int dir) {
+        C e[8], o[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             e[k] = v[2 * k];
             o[k] = v[2 * k + 1];
         }
-        DFT<8>::run(e, dir);
-        DFT<8>::run(o, dir);
-        const float d = (float)dir;
+        DFT<8, C>::run(e, dir);
+        DFT<8, C>::run(o, dir);
+        const double d = (double)dir;
         o[1] = rot(o[1], kC1, d * kS1);
         o[2] = rot(o[2], kC2, d * kC2);
         o[3] = rot(o[3], kS1, d * kC1);
@@ -106,19 +109,19 @@ __host__ __device__ constexpr int freq_at(int L, int p) { return p / (L / split_
 // not read; nin <= L/2, so the upper half of every pass-1 input is zero at compile time),
 // transposed order out.  Line n starts at s + off(n); elements at stride ES.
 // tw[m] = exp(-2 pi i m / L).  Called by all NT threads; ends with a barrier.
-template <int L, int NT, class Off>
-__device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, const float2* tw, int nin) {
+template <int L, int NT, class Off, typename C>
+__device__ __forceinline__ void forward(C* s, int NL, Off off, int ES, const C* tw, int nin) {
     constexpr int A = Split<L>::A, B = Split<L>::B;
     for (int t = threadIdx.x; t < NL * B; t += NT) {
         const int n = t % NL, b = t / NL;
-        float2* ln = s + off(n);
-        float2 v[A];
+        C* ln = s + off(n);
+        C v[A];
 #pragma unroll
         for (int a = 0; a < A; ++a) {
             const int l = b + B * a;
-            v[a] = (a < A / 2 && l < nin) ? ln[l * ES] : make_float2(0.f, 0.f);
+            v[a] = (a < A / 2 && l < nin) ? ln[l * ES] : C{};
         }
-        DFT<A>::run(v, -1);
+        DFT<A, C>::run(v, -1);
 #pragma unroll
         for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
 #pragma unroll
@@ -127,11 +130,11 @@ __device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, cons
     __syncthreads();
     for (int t = threadIdx.x; t < NL * A; t += NT) {
         const int n = t % NL, k1 = t / NL;
-        float2* ln = s + off(n) + B * k1 * ES;
-        float2 v[B];
+        C* ln = s + off(n) + B * k1 * ES;
+        C v[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) v[b] = ln[b * ES];
-        DFT<B>::run(v, -1);
+        DFT<B, C>::run(v, -1);
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) ln[k2 * ES] = v[k2];
     }
@@ -140,16 +143,16 @@ __device__ __forceinline__ void forward(float2* s, int NL, Off off, int ES, cons
 
 // Inverse (unnormalised) transform of NL lines, transposed order in, natural order out;
 // only outputs l < nout (<= L/2) are written.  Called by all NT threads; ends with a barrier.
-template <int L, int NT, class Off>
-__device__ __forceinline__ void inverse(float2* s, int NL, Off off, int ES, const float2* tw, int nout) {
+template <int L, int NT, class Off, typename C>
+__device__ __forceinline__ void inverse(C* s, int NL, Off off, int ES, const C* tw, int nout) {
     constexpr int A = Split<L>::A, B = Split<L>::B;
     for (int t = threadIdx.x; t < NL * A; t += NT) {
         const int n = t % NL, k1 = t / NL;
-        float2* ln = s + off(n) + B * k1 * ES;
-        float2 v[B];
+        C* ln = s + off(n) + B * k1 * ES;
+        C v[B];
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) v[k2] = ln[k2 * ES];
-        DFT<B>::run(v, +1);
+        DFT<B, C>::run(v, +1);
 #pragma unroll
         for (int b = 1; b < B; ++b) v[b] = cmul(v[b], cconj(tw[b * k1]));
 #pragma unroll
@@ -158,11 +161,11 @@ __device__ __forceinline__ void inverse(float2* s, int NL, Off off, int ES, cons
     __syncthreads();
     for (int t = threadIdx.x; t < NL * B; t += NT) {
         const int n = t % NL, b = t / NL;
-        float2* ln = s + off(n);
-        float2 v[A];
+        C* ln = s + off(n);
+        C v[A];
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) v[k1] = ln[(b + B * k1) * ES];
-        DFT<A>::run(v, +1);
+        DFT<A, C>::run(v, +1);
 #pragma unroll
         for (int a = 0; a < A / 2; ++a) {
             const int l = b + B * a;

@@ -85,6 +85,10 @@ struct ZArgs {
     int Ox, Oy, Oz;
     long long tstride;
     unsigned mx, my, mz;  // reflection flip masks per axis
+    // spectrum of the xy kernels: row py holds ky = py / by + ay * (py % by) and stored column sc
+    // holds kx = colkx[sc]; by = 0 and colkx = NULL for natural order
+    const unsigned char* colkx;
+    int ay, by;
 };
 
 template <typename T, int L>
@@ -98,7 +102,8 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
     for (int m = tid; m < L; m += NT) tw[m] = twg[m];
 
     const int ntile = (z.Lx + TB - 1) / TB;
-    const int ky = blockIdx.x / ntile;
+    const int py = blockIdx.x / ntile;
+    const int ky = z.by ? py / z.by + z.ay * (py % z.by) : py;
     const int kx0 = (blockIdx.x % ntile) * TB;
     const long long plane = (long long)z.Ly * z.Lx;
     C* w = reinterpret_cast<C*>(z.w);
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
     const unsigned fy = ky > z.Ly / 2 ? z.my : 0u;
 
     for (int r = 0; r < z.R; ++r) {
-        C* base = w + (long long)r * 12 * z.nz * plane + (long long)ky * z.Lx + kx0;
+        C* base = w + (long long)r * 12 * z.nz * plane + (long long)py * z.Lx + kx0;
         for (int idx = tid; idx < 12 * L * TB; idx += NT) {
             int tb = idx % TB;
             int l = (idx / TB) % L;
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
             int tb = p % TB;
             int kz = p / TB;
             if (kx0 + tb >= z.Lx) continue;
-            int kx = kx0 + tb;
+            const int kx = z.colkx ? (int)z.colkx[kx0 + tb] : kx0 + tb;
             int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
             int kzo = kz <= Lz / 2 ? kz : Lz - kz;
             unsigned mask = fy ^ (kx > z.Lx / 2 ? z.mx : 0u) ^ (kz > Lz / 2 ? z.mz : 0u);
@@ -182,30 +187,47 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// 16-byte zero-filling copy (src_bytes 0 or 16)
+__device__ __forceinline__ void cp_async16z(void* smem_dst, const void* gsrc, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes));
+}
+// one element of the input plane: 8-byte (FP32) or 16-byte (FP64) zero-filling copy
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C* smem_dst, const C* gsrc, bool in) {
+    if constexpr (sizeof(C) == 8)
+        cp_async8z(smem_dst, gsrc, in ? 8 : 0);
+    else
+        cp_async16z(smem_dst, gsrc, in ? 16 : 0);
+}
+
 constexpr int kXYThreads = 256;
 
-template <int L>
+template <int L, typename C>
 struct XYCfg {
-    static constexpr int H = L / 2;                // rows that are non-zero before / needed after the y transform
-    static constexpr int RS = L + 1;               // odd row stride of the x-transform buffer
-    static constexpr int CW = L < 32 ? L : 32;     // stored columns per y-transform chunk
-    static constexpr size_t smem = sizeof(float2) * (size_t)(L * CW + H * RS + L) + sizeof(int4) * H + L;
+    static constexpr int H = L / 2;   // rows that are non-zero before / needed after the y transform
+    static constexpr int RS = L + 1;  // odd row stride of the x-transform buffer
+    static constexpr int CW0 = sizeof(C) == 8 ? 32 : 16;
+    static constexpr int CW = L < CW0 ? L : CW0;  // stored columns per y-transform chunk
+    static constexpr int EPV = 16 / (int)sizeof(C);  // elements per 16-byte vector
+    static constexpr int MINB = sizeof(C) == 8 ? 2 : 1;  // CTAs per SM
+    static constexpr size_t smem = sizeof(C) * (size_t)(L * CW + H * RS + L) + sizeof(int4) * H + L;
 };
 
 // Forward: plane (r, alpha, z) of x -> W2 plane [Ly][Lx] (transposed ky, stored kx).  x is
 // [R][12][Nz][Ny][Nx], or [R][12][ns] on a support (rows != NULL; zeros outside it).
-template <int L>
-__global__ void __launch_bounds__(kXYThreads, 2)
-    xy_fwd_kernel(const float2* __restrict__ x, float2* __restrict__ w, int nx, int ny, int nz,
-                  const int4* __restrict__ rows, long long ns, const unsigned char* __restrict__ cpos,
-                  const float2* __restrict__ twg) {
-    using Cfg = XYCfg<L>;
+template <int L, typename C>
+__global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
+    xy_fwd_kernel(const C* __restrict__ x, C* __restrict__ w, int nx, int ny, int nz, const int4* __restrict__ rows,
+                  long long ns, const unsigned char* __restrict__ cpos, const C* __restrict__ twg) {
+    using Cfg = XYCfg<L, C>;
     constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
+    constexpr int EPV = Cfg::EPV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* ck = reinterpret_cast<float2*>(smem_raw);  // [L][CW] chunk of stored columns
-    float2* xr = ck + L * CW;                          // [H][RS] rows after the x transform
-    float2* tw = xr + Cfg::H * RS;
-    int4* rw = reinterpret_cast<int4*>(tw + L);        // [H] support rows of this plane
+    C* ck = reinterpret_cast<C*>(smem_raw);  // [L][CW] chunk of stored columns
+    C* xr = ck + L * CW;                     // [H][RS] rows after the x transform
+    C* tw = xr + Cfg::H * RS;
+    int4* rw = reinterpret_cast<int4*>(tw + L);  // [H] support rows of this plane
     unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
     for (int m = tid; m < L; m += NT) {
@@ -217,35 +239,35 @@ __global__ void __launch_bounds__(kXYThreads, 2)
         const int z = (int)(p % nz);
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = rows[(long long)z * ny + yy];
         __syncthreads();
-        const float2* src = x + (p / nz) * ns;
+        const C* src = x + (p / nz) * ns;
         for (int idx = tid; idx < ny * nx; idx += NT) {
             const int yy = idx / nx, xx = idx % nx;
             const int4 q = rw[yy];
             const bool in = xx >= q.x && xx < q.y;
-            cp_async8z(xr + yy * RS + xx, in ? src + q.z + (xx - q.x) : src, in ? 8 : 0);
+            cp_async_elem(xr + yy * RS + xx, in ? src + q.z + (xx - q.x) : src, in);
         }
     } else {
-        const float2* src = x + p * (long long)ny * nx;
-        for (int idx = tid; idx < ny * nx; idx += NT) cp_async8(xr + (idx / nx) * RS + idx % nx, src + idx);
+        const C* src = x + p * (long long)ny * nx;
+        for (int idx = tid; idx < ny * nx; idx += NT) cp_async_elem(xr + (idx / nx) * RS + idx % nx, src + idx, true);
     }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
     fft2::forward<L, NT>(xr, ny, [](int n) { return n * RS; }, 1, tw, nx);
-    float2* dst = w + p * (long long)L * L;
+    C* dst = w + p * (long long)L * L;
 #pragma unroll 1
     for (int k = 0; k < L / CW; ++k) {
         // y transform, pass 1: gather stored column k*CW + c from the x-transform rows
         for (int t = tid; t < CW * B; t += NT) {
             const int c = t % CW, b = t / CW;
-            const float2* col = xr + pos[k * CW + c];
-            float2 v[A];
+            const C* col = xr + pos[k * CW + c];
+            C v[A];
 #pragma unroll
             for (int a = 0; a < A; ++a) {
                 const int yy = b + B * a;  // ny <= L/2: the upper half is zero
-                v[a] = (a < A / 2 && yy < ny) ? col[yy * RS] : make_float2(0.f, 0.f);
+                v[a] = (a < A / 2 && yy < ny) ? col[yy * RS] : C{};
             }
-            fft2::DFT<A>::run(v, -1);
+            fft2::DFT<A, C>::run(v, -1);
 #pragma unroll
             for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
 #pragma unroll
@@ -254,17 +276,17 @@ __global__ void __launch_bounds__(kXYThreads, 2)
         __syncthreads();
         for (int t = tid; t < CW * A; t += NT) {
             const int c = t % CW, k1 = t / CW;
-            float2* ln = ck + B * k1 * CW + c;
-            float2 v[B];
+            C* ln = ck + B * k1 * CW + c;
+            C v[B];
 #pragma unroll
             for (int b = 0; b < B; ++b) v[b] = ln[b * CW];
-            fft2::DFT<B>::run(v, -1);
+            fft2::DFT<B, C>::run(v, -1);
 #pragma unroll
             for (int k2 = 0; k2 < B; ++k2) ln[k2 * CW] = v[k2];
         }
         __syncthreads();
-        for (int idx = tid; idx < L * CW / 2; idx += NT) {
-            const int q = idx / (CW / 2), c2 = 2 * (idx % (CW / 2));
+        for (int idx = tid; idx < L * CW / EPV; idx += NT) {
+            const int q = idx / (CW / EPV), c2 = EPV * (idx % (CW / EPV));
             *reinterpret_cast<float4*>(dst + (long long)q * L + k * CW + c2) =
                 *reinterpret_cast<const float4*>(ck + q * CW + c2);
         }
@@ -273,16 +295,18 @@ __global__ void __launch_bounds__(kXYThreads, 2)
 }
 
 // Inverse: W2 plane -> y plane [Ny][Nx] with the material / Gram / preconditioner epilogue.
-template <int L>
-__global__ void __launch_bounds__(kXYThreads, 2)
-    xy_inv_kernel(const float2* __restrict__ w, float2* __restrict__ y, MatvecEpi epi,
-                  const unsigned char* __restrict__ cpos, const float2* __restrict__ twg) {
-    using Cfg = XYCfg<L>;
+template <int L, typename C>
+__global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
+    xy_inv_kernel(const C* __restrict__ w, C* __restrict__ y, MatvecEpi epi, const unsigned char* __restrict__ cpos,
+                  const C* __restrict__ twg) {
+    using Cfg = XYCfg<L, C>;
+    using R = decltype(C{}.x);
     constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
+    constexpr int EPV = Cfg::EPV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* ck = reinterpret_cast<float2*>(smem_raw);
-    float2* xr = ck + L * CW;
-    float2* tw = xr + Cfg::H * RS;
+    C* ck = reinterpret_cast<C*>(smem_raw);
+    C* xr = ck + L * CW;
+    C* tw = xr + Cfg::H * RS;
     int4* rw = reinterpret_cast<int4*>(tw + L);
     unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
@@ -294,11 +318,11 @@ __global__ void __launch_bounds__(kXYThreads, 2)
     const long long p = blockIdx.x;  // plane (r * 12 + alpha) * nz + z
     if (epi.rows)
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = epi.rows[(p % nz) * ny + yy];
-    const float2* src = w + p * (long long)L * L;
+    const C* src = w + p * (long long)L * L;
 #pragma unroll 1
     for (int k = 0; k < L / CW; ++k) {
-        for (int idx = tid; idx < L * CW / 2; idx += NT) {
-            const int q = idx / (CW / 2), c2 = 2 * (idx % (CW / 2));
+        for (int idx = tid; idx < L * CW / EPV; idx += NT) {
+            const int q = idx / (CW / EPV), c2 = EPV * (idx % (CW / EPV));
             cp_async16(ck + q * CW + c2, src + (long long)q * L + k * CW + c2);
         }
         cp_async_commit();
@@ -307,11 +331,11 @@ __global__ void __launch_bounds__(kXYThreads, 2)
         // inverse y transform, pass 1 (in place in the chunk)
         for (int t = tid; t < CW * A; t += NT) {
             const int c = t % CW, k1 = t / CW;
-            float2* ln = ck + B * k1 * CW + c;
-            float2 v[B];
+            C* ln = ck + B * k1 * CW + c;
+            C v[B];
 #pragma unroll
             for (int k2 = 0; k2 < B; ++k2) v[k2] = ln[k2 * CW];
-            fft2::DFT<B>::run(v, +1);
+            fft2::DFT<B, C>::run(v, +1);
 #pragma unroll
             for (int b = 1; b < B; ++b) v[b] = cmul(v[b], cconj(tw[b * k1]));
 #pragma unroll
@@ -321,11 +345,11 @@ __global__ void __launch_bounds__(kXYThreads, 2)
         // pass 2: rows y < Ny scattered to the x-transform buffer at the column's x position
         for (int t = tid; t < CW * B; t += NT) {
             const int c = t % CW, b = t / CW;
-            float2 v[A];
+            C v[A];
 #pragma unroll
             for (int k1 = 0; k1 < A; ++k1) v[k1] = ck[(b + B * k1) * CW + c];
-            fft2::DFT<A>::run(v, +1);
-            float2* col = xr + pos[k * CW + c];
+            fft2::DFT<A, C>::run(v, +1);
+            C* col = xr + pos[k * CW + c];
 #pragma unroll
             for (int a = 0; a < A / 2; ++a) {  // ny <= L/2
                 const int yy = b + B * a;
@@ -338,10 +362,11 @@ __global__ void __launch_bounds__(kXYThreads, 2)
     const int alpha = (int)((p / nz) % 12);
     const long long zoff = (p % nz) * (long long)ny * nx;
     const long long base = p * (long long)ny * nx;
-    const float gl = (float)((alpha % 4) == 0 ? epi.g1 : epi.g234);
-    const float2* xin = reinterpret_cast<const float2*>(epi.x);
-    const float2* c1 = reinterpret_cast<const float2*>(epi.c1);
-    const float2* c2 = reinterpret_cast<const float2*>(epi.c2);
+    const R gl = (R)((alpha % 4) == 0 ? epi.g1 : epi.g234);
+    const R ig = (R)1 / gl;
+    const C* xin = reinterpret_cast<const C*>(epi.x);
+    const C* c1 = reinterpret_cast<const C*>(epi.c1);
+    const C* c2 = reinterpret_cast<const C*>(epi.c2);
     const long long cbase = (p / nz) * epi.ns;  // component block on the support
 #pragma unroll 4
     for (int idx = tid; idx < ny * nx; idx += NT) {
@@ -352,14 +377,13 @@ __global__ void __launch_bounds__(kXYThreads, 2)
             if (xx < q.x || xx >= q.y) continue;
             o = cbase + q.z + (xx - q.x);
         }
-        float2 v = xr[yy * RS + xx];
+        C v = xr[yy * RS + xx];
         if (epi.op == VIE_OP_A) {
-            const float2 xv = xin[o];
+            const C xv = xin[o];
             v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[zoff + idx], v));
         } else if (epi.op == VIE_OP_PA) {
-            const float2 xv = xin[o];
-            const float2 t = cmul(c2[zoff + idx], v);
-            const float ig = 1.0f / gl;
+            const C xv = xin[o];
+            const C t = cmul(c2[zoff + idx], v);
             v = csub(cmul(c1[zoff + idx], xv), mk(ig * t.x, ig * t.y));
         }
         y[o] = v;
@@ -669,46 +693,50 @@ static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z
     return VIE_EINVAL;
 }
 
-// The FP32 three-kernel path needs a square xy circulant of 8..128 and Lz of 8..128
-// (the column map is built at setup only for such grids).
-static bool fused_ok(const vie_handle* h) { return h->colmap && h->L[2] >= 8 && h->L[2] <= 128; }
+// The fused xy kernels need a square xy circulant of 8..128 (the column map is built at
+// setup only for such grids); the FP32 z pass with the block product needs Lz of 8..128.
+static bool xy_ok(const vie_handle* h) { return h->colmap != nullptr; }
+static bool zfused_ok(const vie_handle* h) { return h->L[2] >= 8 && h->L[2] <= 128; }
 
 // in_elems: complex values of the matvec input (and output) vector
-template <int L>
+template <int L, typename C>
 static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
                        const MatvecEpi& e, const Support& sp, double in_elems, cudaStream_t s) {
-    constexpr size_t smem = XYCfg<L>::smem;
+    constexpr size_t smem = XYCfg<L, C>::smem;
+    constexpr bool f32 = sizeof(C) == 8;
     // set on every call: the attribute is per device and launches may come from several threads
-    VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (planes > 0x7fffffffLL) {
         set_error("xy transform grid too large");
         return VIE_EINVAL;
     }
     const unsigned char* cpos = h->colmap + L;
-    const double plane_full = (double)L * L;
+    const C* tw = reinterpret_cast<const C*>(f32 ? (const void*)(h->tw32 + L) : (const void*)(h->tw64 + L));
+    const double c = sizeof(C), plane_full = (double)L * L;
     if (fwd)
-        VIE_KLAUNCH_B("fft_xy_f32", s, 8.0 * (in_elems + planes * plane_full),
-                      xy_fwd_kernel<L><<<(unsigned)planes, kXYThreads, smem, s>>>(
-                          (const float2*)in, (float2*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, h->tw32 + L));
+        VIE_KLAUNCH_B(f32 ? "fft_xy_f32" : "fft_xy_f64", s, c * (in_elems + planes * plane_full),
+                      xy_fwd_kernel<L, C><<<(unsigned)planes, kXYThreads, smem, s>>>(
+                          (const C*)in, (C*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, tw));
     else
-        VIE_KLAUNCH_B("ifft_xy_epilogue_f32", s,
-                      8.0 * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
-                             (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0)),
-                      xy_inv_kernel<L><<<(unsigned)planes, kXYThreads, smem, s>>>(
-                          (const float2*)in, (float2*)out, e, cpos, h->tw32 + L));
+        VIE_KLAUNCH_B(f32 ? "ifft_xy_epilogue_f32" : "ifft_xy_epilogue_f64", s,
+                      c * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
+                           (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0)),
+                      xy_inv_kernel<L, C><<<(unsigned)planes, kXYThreads, smem, s>>>((const C*)in, (C*)out, e, cpos,
+                                                                                    tw));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
 
+template <typename C>
 static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, long long planes, int nx, int ny,
                      const MatvecEpi& e, const Support& sp, double in_elems, cudaStream_t s) {
     switch (h->L[0]) {
-        case 8: return launch_xy_L<8>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
-        case 16: return launch_xy_L<16>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
-        case 32: return launch_xy_L<32>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
-        case 64: return launch_xy_L<64>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
-        case 128: return launch_xy_L<128>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 8: return launch_xy_L<8, C>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 16: return launch_xy_L<16, C>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 32: return launch_xy_L<32, C>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 64: return launch_xy_L<64, C>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
+        case 128: return launch_xy_L<128, C>(fwd, h, in, out, planes, nx, ny, e, sp, in_elems, s);
     }
     set_error("xy transform: unsupported length");
     return VIE_EINVAL;
@@ -774,19 +802,32 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     e.rows = sp.rows;
     e.ns = sp.ns;
     MatvecEpi noepi{};
-    if (sizeof(T) == 4 && fused_ok(h)) {
+    if (xy_ok(h)) {
         const double in_elems = sp.rows ? (double)R * 12 * sp.ns : (double)comps * ny * nx;
-        VIE_TRY(launch_xy(true, h, x, W2, comps, nx, ny, noepi, sp, in_elems, s));
-        ZFArgs z{};
-        z.w = reinterpret_cast<float2*>(W2);
-        z.green_t = h->green32t;
-        z.colkx = h->colmap;
-        z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
-        z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
-        z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
-        z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
-        VIE_TRY(launch_zf(h, z, s));
-        return launch_xy(false, h, W2, y, comps, nx, ny, e, sp, in_elems, s);
+        VIE_TRY(launch_xy<C>(true, h, x, W2, comps, nx, ny, noepi, sp, in_elems, s));
+        if (sizeof(T) == 4 && zfused_ok(h)) {
+            ZFArgs z{};
+            z.w = reinterpret_cast<float2*>(W2);
+            z.green_t = h->green32t;
+            z.colkx = h->colmap;
+            z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+            z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
+            z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            VIE_TRY(launch_zf(h, z, s));
+        } else {
+            ZArgs z{};
+            z.w = W2;
+            z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
+            z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+            z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
+            z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            z.colkx = h->colmap;
+            z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
+            VIE_TRY(launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s));
+        }
+        return launch_xy<C>(false, h, W2, y, comps, nx, ny, e, sp, in_elems, s);
     }
     if (sp.rows) {
         set_error("internal: the line-transform matvec takes full-grid vectors only");
@@ -911,7 +952,9 @@ int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, 
                    cudaStream_t s) {
     if (!sp.rows) return matvec_device(h, R, x, y, precision, op, s);
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, precision)));
-    if (precision == VIE_FP32 && fused_ok(h)) return matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp);
+    if (xy_ok(h))
+        return precision == VIE_FP64 ? matvec_impl<double>(h, R, x, y, op, s, h->fft_ws.ptr, sp)
+                                     : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp);
     const size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     void* tx = tmp;
     void* ty = static_cast<char*>(tmp) + c * (size_t)R * 12 * h->nv;
