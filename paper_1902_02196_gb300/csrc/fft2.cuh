@@ -93,6 +93,56 @@ struct DFT<16, C> {
     }
 };
 
+// a * w^n, w = exp(dir 2 pi i / N), N in {4, 8, 16}, n < N/2 a compile-time constant after unrolling
+template <int N, typename C>
+__device__ __forceinline__ C twist(C a, int n, int dir) {
+    const double d = (double)dir;
+    switch (n * (16 / N)) {  // the same angle in sixteenths of a turn
+        case 0: return a;
+        case 1: return rot(a, kC1, d * kS1);
+        case 2: return rot(a, kC2, d * kC2);
+        case 3: return rot(a, kS1, d * kC1);
+        case 4: return cmul_i(a, dir);
+        case 5: return rot(a, -kS1, d * kC1);
+        case 6: return rot(a, -kC2, d * kC2);
+        default: return rot(a, -kC1, d * kS1);
+    }
+}
+
+// N-point DFT of v[0..N/2) with v[N/2..N) taken as zero (not read): split in frequency,
+// X[2k] = DFT_{N/2}(x)[k], X[2k+1] = DFT_{N/2}(x w^n)[k]; all N outputs written to v.
+template <int N, typename C>
+__device__ __forceinline__ void dft_half_in(C* v, int dir) {
+    C e[N / 2], o[N / 2];
+#pragma unroll
+    for (int n = 0; n < N / 2; ++n) {
+        e[n] = v[n];
+        o[n] = twist<N>(v[n], n, dir);
+    }
+    DFT<N / 2, C>::run(e, dir);
+    DFT<N / 2, C>::run(o, dir);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+        v[2 * k] = e[k];
+        v[2 * k + 1] = o[k];
+    }
+}
+
+// first N/2 outputs of the N-point DFT of v (split in time): X[k] = E[k] + w^k O[k], k < N/2
+template <int N, typename C>
+__device__ __forceinline__ void dft_half_out(C* v, int dir) {
+    C e[N / 2], o[N / 2];
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+        e[k] = v[2 * k];
+        o[k] = v[2 * k + 1];
+    }
+    DFT<N / 2, C>::run(e, dir);
+    DFT<N / 2, C>::run(o, dir);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) v[k] = cadd(e[k], twist<N>(o[k], k, dir));
+}
+
 // factorisation L = A * B used for each length (8 <= L <= 256)
 __host__ __device__ constexpr int split_a(int L) { return L <= 16 ? 4 : (L <= 64 ? 8 : 16); }
 template <int L>
@@ -117,11 +167,11 @@ __device__ __forceinline__ void forward(C* s, int NL, Off off, int ES, const C* 
         C* ln = s + off(n);
         C v[A];
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
+        for (int a = 0; a < A / 2; ++a) {
             const int l = b + B * a;
-            v[a] = (a < A / 2 && l < nin) ? ln[l * ES] : C{};
+            v[a] = l < nin ? ln[l * ES] : C{};
         }
-        DFT<A, C>::run(v, -1);
+        dft_half_in<A>(v, -1);
 #pragma unroll
         for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
 #pragma unroll
@@ -165,7 +215,7 @@ __device__ __forceinline__ void inverse(C* s, int NL, Off off, int ES, const C* 
         C v[A];
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) v[k1] = ln[(b + B * k1) * ES];
-        DFT<A, C>::run(v, +1);
+        dft_half_out<A>(v, +1);
 #pragma unroll
         for (int a = 0; a < A / 2; ++a) {
             const int l = b + B * a;

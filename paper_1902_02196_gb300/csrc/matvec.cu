@@ -263,11 +263,11 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
             const C* col = xr + pos[k * CW + c];
             C v[A];
 #pragma unroll
-            for (int a = 0; a < A; ++a) {
-                const int yy = b + B * a;  // ny <= L/2: the upper half is zero
-                v[a] = (a < A / 2 && yy < ny) ? col[yy * RS] : C{};
+            for (int a = 0; a < A / 2; ++a) {  // ny <= L/2: the upper half is zero
+                const int yy = b + B * a;
+                v[a] = yy < ny ? col[yy * RS] : C{};
             }
-            fft2::DFT<A, C>::run(v, -1);
+            fft2::dft_half_in<A>(v, -1);
 #pragma unroll
             for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
 #pragma unroll
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
             C v[A];
 #pragma unroll
             for (int k1 = 0; k1 < A; ++k1) v[k1] = ck[(b + B * k1) * CW + c];
-            fft2::DFT<A, C>::run(v, +1);
+            fft2::dft_half_out<A>(v, +1);
             C* col = xr + pos[k * CW + c];
 #pragma unroll
             for (int a = 0; a < A / 2; ++a) {  // ny <= L/2
