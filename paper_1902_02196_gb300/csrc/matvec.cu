@@ -358,16 +358,36 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         }
         __syncthreads();
     }
+    const long long base = p * (long long)ny * nx;
+    const long long cbase = (p / nz) * epi.ns;  // component block on the support
+    const C* xin = reinterpret_cast<const C*>(epi.x);
+    // the epilogue's x values of this plane arrive in the free chunk buffer during the x transform
+    const bool pre = epi.op != VIE_OP_NSCAT && L * CW >= ny * nx;
+    if (pre) {
+        for (int idx = tid; idx < ny * nx; idx += NT) {
+            const int yy = idx / nx, xx = idx % nx;
+            long long o = base + idx;
+            bool in = true;
+            if (epi.rows) {
+                const int4 q = rw[yy];
+                in = xx >= q.x && xx < q.y;
+                o = in ? cbase + q.z + (xx - q.x) : cbase;
+            }
+            cp_async_elem(ck + idx, xin + o, in);
+        }
+        cp_async_commit();
+    }
     fft2::inverse<L, NT>(xr, ny, [](int n) { return n * RS; }, 1, tw, nx);
+    if (pre) {
+        cp_async_wait<0>();
+        __syncthreads();
+    }
     const int alpha = (int)((p / nz) % 12);
     const long long zoff = (p % nz) * (long long)ny * nx;
-    const long long base = p * (long long)ny * nx;
     const R gl = (R)((alpha % 4) == 0 ? epi.g1 : epi.g234);
     const R ig = (R)1 / gl;
-    const C* xin = reinterpret_cast<const C*>(epi.x);
     const C* c1 = reinterpret_cast<const C*>(epi.c1);
     const C* c2 = reinterpret_cast<const C*>(epi.c2);
-    const long long cbase = (p / nz) * epi.ns;  // component block on the support
 #pragma unroll 4
     for (int idx = tid; idx < ny * nx; idx += NT) {
         const int yy = idx / nx, xx = idx % nx;
@@ -379,10 +399,10 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         }
         C v = xr[yy * RS + xx];
         if (epi.op == VIE_OP_A) {
-            const C xv = xin[o];
+            const C xv = pre ? ck[idx] : xin[o];
             v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[zoff + idx], v));
         } else if (epi.op == VIE_OP_PA) {
-            const C xv = xin[o];
+            const C xv = pre ? ck[idx] : xin[o];
             const C t = cmul(c2[zoff + idx], v);
             v = csub(cmul(c1[zoff + idx], xv), mk(ig * t.x, ig * t.y));
         }
