@@ -266,17 +266,22 @@ def matvec_alg_bytes(grid, L, R, c):
     return C * nx * ny * nz * c * 3 + 4 * spec + 60 * (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1) * c
 
 
-def source_hash():
+def source_hash(files):
+    """Hash of the kernel sources a recorded ncu measurement was taken on (paths relative to csrc/)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1902_02196_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in sorted(files):
+        p = os.path.join(d, f)
+        if not os.path.exists(p):
+            return None
+        h.update(f.encode())
+        h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel sources."""
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json), when it was taken
+    on the current sources of that kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -285,7 +290,7 @@ def measured_traffic(kernel):
     except ValueError:
         return None
     e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(e.get("sources", [])):
         return None
     return e.get("dram_bytes_per_launch")
 

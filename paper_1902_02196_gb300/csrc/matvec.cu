@@ -18,38 +18,10 @@
 #include <vector>
 
 #include "common.cuh"
+#include "block.cuh"
 #include "fft.cuh"
 #include "fft2.cuh"
-
-// ---------------------------------------------------------------------------
-// Constant table: for each unique tensor t the (alpha, beta, sign) entries of the 12x12 block
-// ---------------------------------------------------------------------------
-struct BlockEntry {
-    signed char a, b, s;
-};
-struct BlockTable {
-    BlockEntry e[144];
-    int start[61];
-};
-constexpr BlockTable make_block_table() {
-    BlockTable T{};
-    int n = 0;
-    for (int t = 0; t < 60; ++t) {
-        T.start[t] = n;
-        for (int a = 0; a < 12; ++a)
-            for (int b = 0; b < 12; ++b)
-                if (tensor_of(a, b) == t) {
-                    T.e[n].a = (signed char)a;
-                    T.e[n].b = (signed char)b;
-                    T.e[n].s = (signed char)sign_of(a, b);
-                    ++n;
-                }
-    }
-    T.start[60] = n;
-    return T;
-}
-__device__ constexpr BlockTable kBlock = make_block_table();
-static_assert(make_block_table().start[60] == 144, "every block entry maps to one of the 60 tensors");
+#include "zpass_f32.cuh"
 
 // y[12] = B(k) x[12] at one frequency point; xv/acc in registers, Green values streamed once.
 template <typename C>
@@ -168,39 +140,6 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
 // positions of the x transform differ modulo 16, which keeps the column gathers
 // and scatters of the xy kernels free of shared-memory bank conflicts.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc));
-}
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc));
-}
-// 8-byte copy that writes zeros when src_bytes == 0 (src must still be a valid address)
-__device__ __forceinline__ void cp_async8z(void* smem_dst, const void* gsrc, int src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-// 16-byte zero-filling copy (src_bytes 0 or 16)
-__device__ __forceinline__ void cp_async16z(void* smem_dst, const void* gsrc, int src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes));
-}
-// one element of the input plane: 8-byte (FP32) or 16-byte (FP64) zero-filling copy
-template <typename C>
-__device__ __forceinline__ void cp_async_elem(C* smem_dst, const C* gsrc, bool in) {
-    if constexpr (sizeof(C) == 8)
-        cp_async8z(smem_dst, gsrc, in ? 8 : 0);
-    else
-        cp_async16z(smem_dst, gsrc, in ? 16 : 0);
-}
-
 constexpr int kXYThreads = 256;
 
 template <int L, typename C>
@@ -411,218 +350,6 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
 }
 
 // ---------------------------------------------------------------------------
-// z pass (FP32, on the spectrum of xy_fwd_kernel): a CTA of 128 threads per (row py,
-// tile of 4 stored columns = 2 mirror pairs) loops over the right-hand sides, two CTAs
-// to an SM so that one's loads and stores overlap the other's arithmetic; the next
-// right-hand side's columns arrive by cp.async while the current one is transformed.
-// The z spectrum stays in transposed order between the forward and inverse transforms.
-// A thread of the block product owns one (column pair, kz mirror pair) item for the
-// whole launch: the 60 Green values of its octant point stay in registers and serve
-// the four frequency points (+-kx, +-kz) of every right-hand side.  The item that pairs
-// kz = 0 with kz = Lz/2 keeps the second point's values in shared memory; the last
-// tile's self-mirrored columns 0 and Lx/2 reload theirs for each right-hand side.
-// ---------------------------------------------------------------------------
-struct ZFArgs {
-    float2* w;                    // spectrum [R*12][Nz][Ly][Lx], in place
-    const float2* green_t;        // [Oy][Ox][Oz][60]
-    const unsigned char* colkx;   // [Lx] kx of each stored column
-    int R, nz, Lx, Ly, Ox, Oy, Oz;
-    int ay, by;                   // split of Ly: row py holds ky = py / by + ay * (py % by)
-    unsigned mx, my, mz;
-};
-
-constexpr int kZThreads = 128;
-constexpr int kZTile = 4;
-
-template <int LZ>
-struct ZFCfg {
-    static constexpr int GS = LZ * kZTile + 4;  // component stride: 4 float2 of padding keep half-warps apart
-    static constexpr int BUF = 12 * GS;
-    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 4 * 60);
-};
-
-// the 60 Green values of one octant point, streamed from the [..][60] layout
-__device__ __forceinline__ void load_green(float2* u, const float2* __restrict__ gp) {
-    const float4* g4 = reinterpret_cast<const float4*>(gp);
-#pragma unroll
-    for (int q = 0; q < 30; ++q) {
-        const float4 v = __ldg(g4 + q);
-        u[2 * q] = make_float2(v.x, v.y);
-        u[2 * q + 1] = make_float2(v.z, v.w);
-    }
-}
-
-// sign flip of a complex value by XOR of the sign bits: sbit is 0 or 0x80000000
-__device__ __forceinline__ float2 xflip(float2 v, unsigned sbit) {
-    return make_float2(__uint_as_float(__float_as_uint(v.x) ^ sbit), __uint_as_float(__float_as_uint(v.y) ^ sbit));
-}
-__device__ __forceinline__ unsigned sign_bit(unsigned mask, int a) { return (mask << (31 - a)) & 0x80000000u; }
-
-// y = B x at the two mirror columns c, c + 1 of one z position (float4 accesses); m0, m1
-// are the components whose sign flips at each column's reflected frequency point; wmask
-// selects the columns written back (3: both; 1 or 2: one, for columns with their own
-// Green values).  u: the 60 Green values (registers).
-__device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, int off, unsigned m0, unsigned m1,
-                                           int wmask) {
-    float2 x0[12], x1[12];
-#pragma unroll
-    for (int b = 0; b < 12; ++b) {
-        const float4 v = *reinterpret_cast<const float4*>(s + b * gs + off);
-        x0[b] = xflip(make_float2(v.x, v.y), sign_bit(m0, b));
-        x1[b] = xflip(make_float2(v.z, v.w), sign_bit(m1, b));
-    }
-#pragma unroll
-    for (int H = 0; H < 2; ++H) {
-        float2 a0[6], a1[6];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) a0[a] = a1[a] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int t = 0; t < 60; ++t) {
-#pragma unroll
-            for (int i = kBlock.start[t]; i < kBlock.start[t + 1]; ++i) {
-                const int a = kBlock.e[i].a, b = kBlock.e[i].b;
-                if (a / 6 != H) continue;
-                const float2 ut = kBlock.e[i].s > 0 ? u[t] : cneg(u[t]);
-                cfma(a0[a - 6 * H], ut, x0[b]);
-                cfma(a1[a - 6 * H], ut, x1[b]);
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            const float2 r0 = xflip(a0[a], sign_bit(m0, a + 6 * H)), r1 = xflip(a1[a], sign_bit(m1, a + 6 * H));
-            float2* d = s + (a + 6 * H) * gs + off;
-            if (wmask == 3)
-                *reinterpret_cast<float4*>(d) = make_float4(r0.x, r0.y, r1.x, r1.y);
-            else if (wmask == 1)
-                d[0] = r0;
-            else
-                d[1] = r1;
-        }
-    }
-}
-
-template <int LZ>
-__global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
-    constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = kZThreads, TB = kZTile;
-    constexpr int GS = ZFCfg<LZ>::GS, BUF = ZFCfg<LZ>::BUF;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sb = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = sb + 2 * BUF;
-    float2* gsec = tw + LZ;  // [2 pairs][2 sets][60] Green values of the item that holds kz = LZ/2
-    const int tid = threadIdx.x;
-    for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
-    const int ntile = z.Lx / TB;
-    const int py = blockIdx.x / ntile, ct = blockIdx.x % ntile, sc0 = ct * TB;
-    const long long plane = (long long)z.Ly * z.Lx;
-    const int ky = py / z.by + z.ay * (py % z.by);
-    const int kyo = ky <= z.Ly / 2 ? ky : z.Ly - ky;
-    const unsigned fy = ky > z.Ly / 2 ? z.my : 0u;
-    const int nz = z.nz;
-
-    auto issue = [&](int r, float2* buf) {
-        const float2* base = z.w + (long long)r * 12 * nz * plane + (long long)py * z.Lx + sc0;
-        for (int idx = tid; idx < 12 * nz * (TB / 2); idx += NT) {
-            const int q = idx % (TB / 2), l = (idx / (TB / 2)) % nz, a = idx / ((TB / 2) * nz);
-            cp_async16(buf + a * GS + l * TB + 2 * q, base + ((long long)a * nz + l) * plane + 2 * q);
-        }
-        cp_async_commit();
-    };
-    auto line = [](int n) { return (n / TB) * GS + n % TB; };
-
-    // block-product item of this thread: column pair ci, kz item j
-    const int ci = tid & 1, j = tid >> 1;
-    const bool single = ct == ntile - 1 && ci == 1;  // columns 0 and Lx/2: own octant columns
-    const int kx0 = z.colkx[sc0 + 2 * ci], kx1 = z.colkx[sc0 + 2 * ci + 1];
-    const unsigned fx0 = kx0 > z.Lx / 2 ? z.mx : 0u, fx1 = kx1 > z.Lx / 2 ? z.mx : 0u;
-    // kz items, in transposed positions p = k2 + B k1 holding kz = k1 + A k2:
-    //   rows k1 = 1..A/2-1 with their mirrors in rows A - k1, then row A/2 (its own mirror),
-    //   then row 0 (k2 = 0 pairs kz = 0 with kz = LZ/2, each with its own octant point).
-    constexpr int NREG = (A / 2 - 1) * B;
-    int pa = -1, pb = -1, pc = -1;  // pa, pb share one octant point; pc (kz = LZ/2) has its own
-    if (j < NREG) {
-        const int k1 = 1 + j / B, k2 = j % B;
-        pa = k2 + B * k1;
-        pb = (B - 1 - k2) + B * (A - k1);
-    } else if (j < NREG + B / 2) {
-        const int k2 = j - NREG;
-        pa = k2 + B * (A / 2);
-        pb = (B - 1 - k2) + B * (A / 2);
-    } else if (j < LZ / 2) {
-        const int k2 = j - NREG - B / 2;
-        pa = k2;
-        if (k2 == 0)
-            pc = B / 2;
-        else
-            pb = B - k2;
-    }
-    const int kxo0 = kx0 <= z.Lx / 2 ? kx0 : z.Lx - kx0, kxo1 = kx1 <= z.Lx / 2 ? kx1 : z.Lx - kx1;
-    const float2* gcol0 = z.green_t + ((long long)kyo * z.Ox + kxo0) * z.Oz * 60;
-    const float2* gcol1 = z.green_t + ((long long)kyo * z.Ox + kxo1) * z.Oz * 60;
-    // the item's frequency points: up to two sharing one octant point (pa, pb), and pc
-    // (kz = LZ/2) with its own; its Green values go to shared memory, next to a copy of
-    // the first set, so that one register array serves all points of every item
-    const int kza = pa >= 0 ? fft2::freq_at(LZ, pa) : 0;
-    const int kzoa = kza <= LZ / 2 ? kza : LZ - kza;
-    float2 u[60];
-    if (pa >= 0 && !single) {
-        load_green(u, gcol0 + (long long)kzoa * 60);
-        if (pc >= 0)
-#pragma unroll
-            for (int t = 0; t < 60; ++t) {
-                gsec[(2 * ci) * 60 + t] = u[t];
-                gsec[(2 * ci + 1) * 60 + t] = gcol0[(long long)(LZ / 2) * 60 + t];
-            }
-    }
-
-    issue(0, sb);
-#pragma unroll 1
-    for (int r = 0; r < z.R; ++r) {
-        float2* s = sb + (r & 1) * BUF;
-        if (r + 1 < z.R) {
-            issue(r + 1, sb + ((r + 1) & 1) * BUF);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        fft2::forward<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
-        if (pa >= 0) {
-            // points (position, Green set): (pa, 0), (pb, 0), (pc, 1); single columns take
-            // each column in turn with its own Green values, loaded from global memory
-#pragma unroll 1
-            for (int q = 0; q < (single ? 6 : 3); ++q) {
-                const int e = single ? q % 3 : q, col = single ? q / 3 : 0;
-                const int pp = e == 0 ? pa : (e == 1 ? pb : pc);
-                if (pp < 0) continue;
-                const int kz = fft2::freq_at(LZ, pp);
-                if (single) {
-                    const int kzo = kz <= LZ / 2 ? kz : LZ - kz;
-                    load_green(u, (col ? gcol1 : gcol0) + (long long)kzo * 60);
-                } else if (e == 2) {
-#pragma unroll
-                    for (int t = 0; t < 60; ++t) u[t] = gsec[(2 * ci + 1) * 60 + t];
-                }
-                const unsigned fz = kz > LZ / 2 ? z.mz : 0u;
-                pair_point(u, s, GS, pp * TB + 2 * ci, fy ^ fz ^ fx0, fy ^ fz ^ fx1, single ? 1 + col : 3);
-            }
-            if (pc >= 0 && !single) {
-#pragma unroll
-                for (int t = 0; t < 60; ++t) u[t] = gsec[(2 * ci) * 60 + t];
-            }
-        }
-        __syncthreads();
-        fft2::inverse<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
-        float2* base = z.w + (long long)r * 12 * nz * plane + (long long)py * z.Lx + sc0;
-        for (int idx = tid; idx < 12 * nz * (TB / 2); idx += NT) {
-            const int q = idx % (TB / 2), l = (idx / (TB / 2)) % nz, a = idx / ((TB / 2) * nz);
-            *reinterpret_cast<float4*>(base + ((long long)a * nz + l) * plane + 2 * q) =
-                *reinterpret_cast<const float4*>(s + a * GS + l * TB + 2 * q);
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -762,31 +489,6 @@ static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, l
     return VIE_EINVAL;
 }
 
-template <int LZ>
-static int launch_zf_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
-    constexpr size_t smem = ZFCfg<LZ>::smem;
-    // set on every call: the attribute is per device and launches may come from several threads
-    VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long blocks = (long long)z.Ly * (z.Lx / kZTile);
-    const double bytes = 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
-    VIE_KLAUNCH_B("zpass_block_f32", s, bytes,
-                  zfused_kernel<LZ><<<(unsigned)blocks, kZThreads, smem, s>>>(z, h->tw32 + LZ));
-    VIE_CHECK_LAUNCH();
-    return VIE_OK;
-}
-
-static int launch_zf(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
-    switch (h->L[2]) {
-        case 8: return launch_zf_L<8>(h, z, s);
-        case 16: return launch_zf_L<16>(h, z, s);
-        case 32: return launch_zf_L<32>(h, z, s);
-        case 64: return launch_zf_L<64>(h, z, s);
-        case 128: return launch_zf_L<128>(h, z, s);
-    }
-    set_error("z pass: unsupported length");
-    return VIE_EINVAL;
-}
-
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
     size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     size_t comps = (size_t)nrhs * 12 * h->nz;
@@ -834,7 +536,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
             z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
-            VIE_TRY(launch_zf(h, z, s));
+            VIE_TRY(zpass_f32_fused(h, z, s));
         } else {
             ZArgs z{};
             z.w = W2;

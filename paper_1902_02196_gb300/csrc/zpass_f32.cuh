@@ -1,0 +1,16 @@
+// FP32 z pass with the fused 12 x 12 block product (zpass_f32.cu).
+#pragma once
+
+#include "common.cuh"
+
+struct ZFArgs {
+    float2* w;                    // spectrum [R*12][Nz][Ly][Lx], in place
+    const float2* green_t;        // [Oy][Ox][Oz][60]
+    const unsigned char* colkx;   // [Lx] kx of each stored column
+    int R, nz, Lx, Ly, Ox, Oy, Oz;
+    int ay, by;                   // split of Ly: row py holds ky = py / by + ay * (py % by)
+    unsigned mx, my, mz;
+};
+
+// Launches the z pass on the spectrum of xy_fwd_kernel (Lz in 8..128).
+int zpass_f32_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s);
