@@ -159,10 +159,11 @@ __host__ __device__ constexpr int freq_at(int L, int p) { return p / (L / split_
 // not read; nin <= L/2, so the upper half of every pass-1 input is zero at compile time),
 // transposed order out.  Line n starts at s + off(n); elements at stride ES.
 // tw[m] = exp(-2 pi i m / L).  Called by all NT threads; ends with a barrier.
-template <int L, int NT, class Off, typename C>
-__device__ __forceinline__ void forward(C* s, int NL, Off off, int ES, const C* tw, int nin) {
+// forward_g: the same, run by NT threads with index tid, sync() as the barrier between passes.
+template <int L, int NT, class Off, typename C, class Sync>
+__device__ __forceinline__ void forward_g(C* s, int NL, Off off, int ES, const C* tw, int nin, int tid, Sync sync) {
     constexpr int A = Split<L>::A, B = Split<L>::B;
-    for (int t = threadIdx.x; t < NL * B; t += NT) {
+    for (int t = tid; t < NL * B; t += NT) {
         const int n = t % NL, b = t / NL;
         C* ln = s + off(n);
         C v[A];
@@ -177,8 +178,8 @@ __device__ __forceinline__ void forward(C* s, int NL, Off off, int ES, const C* 
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) ln[(b + B * k1) * ES] = v[k1];
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < NL * A; t += NT) {
+    sync();
+    for (int t = tid; t < NL * A; t += NT) {
         const int n = t % NL, k1 = t / NL;
         C* ln = s + off(n) + B * k1 * ES;
         C v[B];
@@ -188,15 +189,20 @@ __device__ __forceinline__ void forward(C* s, int NL, Off off, int ES, const C* 
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) ln[k2 * ES] = v[k2];
     }
-    __syncthreads();
+    sync();
+}
+template <int L, int NT, class Off, typename C>
+__device__ __forceinline__ void forward(C* s, int NL, Off off, int ES, const C* tw, int nin) {
+    forward_g<L, NT>(s, NL, off, ES, tw, nin, (int)threadIdx.x, [] { __syncthreads(); });
 }
 
 // Inverse (unnormalised) transform of NL lines, transposed order in, natural order out;
 // only outputs l < nout (<= L/2) are written.  Called by all NT threads; ends with a barrier.
-template <int L, int NT, class Off, typename C>
-__device__ __forceinline__ void inverse(C* s, int NL, Off off, int ES, const C* tw, int nout) {
+// inverse_g: the same, run by NT threads with index tid, sync() as the barrier between passes.
+template <int L, int NT, class Off, typename C, class Sync>
+__device__ __forceinline__ void inverse_g(C* s, int NL, Off off, int ES, const C* tw, int nout, int tid, Sync sync) {
     constexpr int A = Split<L>::A, B = Split<L>::B;
-    for (int t = threadIdx.x; t < NL * A; t += NT) {
+    for (int t = tid; t < NL * A; t += NT) {
         const int n = t % NL, k1 = t / NL;
         C* ln = s + off(n) + B * k1 * ES;
         C v[B];
@@ -208,8 +214,8 @@ __device__ __forceinline__ void inverse(C* s, int NL, Off off, int ES, const C* 
 #pragma unroll
         for (int b = 0; b < B; ++b) ln[b * ES] = v[b];
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < NL * B; t += NT) {
+    sync();
+    for (int t = tid; t < NL * B; t += NT) {
         const int n = t % NL, b = t / NL;
         C* ln = s + off(n);
         C v[A];
@@ -222,7 +228,11 @@ __device__ __forceinline__ void inverse(C* s, int NL, Off off, int ES, const C* 
             if (l < nout) ln[l * ES] = v[a];
         }
     }
-    __syncthreads();
+    sync();
+}
+template <int L, int NT, class Off, typename C>
+__device__ __forceinline__ void inverse(C* s, int NL, Off off, int ES, const C* tw, int nout) {
+    inverse_g<L, NT>(s, NL, off, ES, tw, nout, (int)threadIdx.x, [] { __syncthreads(); });
 }
 
 }  // namespace fft2
