@@ -96,6 +96,7 @@ void release(vie_handle* h) {
         cudaFree(h->green32);
         cudaFree(h->green32t);
         cudaFree(h->colmap);
+        cudaFree(h->colkx32);
         cudaFree(h->tw64);
         cudaFree(h->tw32);
         cudaFree(h->toeplitz);
@@ -261,6 +262,8 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
         h->green32 = share->green32;
         h->green32t = share->green32t;
         h->colmap = share->colmap;
+        h->colkx32 = share->colkx32;
+        h->colpos32 = share->colpos32;
         h->tw64 = share->tw64;
         h->tw32 = share->tw32;
         h->toeplitz = share->toeplitz;

@@ -114,6 +114,11 @@ struct vie_handle {
     // stored column order of that path's spectrum: [Lx] kx per stored column, then [Lx]
     // positions of those kx in the x transform's output order (square L <= 128 only, else null)
     unsigned char* colmap;
+    // stored column order of every matvec spectrum, any Lx: colkx32[sc] = kx of stored column sc
+    // (mirror pairs (kx, Lx - kx) side by side, columns 0 and Lx/2 last; the order of colmap
+    // when that exists), colpos32[kx] = its stored column
+    int* colkx32;
+    int* colpos32;
     // twiddle tables exp(-2 pi i m / L) for L = 2^k, k = 1..11, concatenated at offset L
     double2* tw64;
     float2* tw32;

@@ -114,6 +114,8 @@ __device__ __forceinline__ void fft_smem(C* s, const C* tw, int dir) {
 // stored (cropping).  When il == 1 the TB lines are consecutive inner indices
 // whose elements are contiguous, otherwise they are adjacent along the inner
 // axis (ib == 1) so that loads of one l coalesce across lines.
+// pin / pout (optional, NULL = identity): element l of a line is read from position pin[l]
+// / written to position pout[l] (the stored column order of the matvec spectrum).
 struct LineArgs {
     const void* in;
     void* out;
@@ -122,6 +124,8 @@ struct LineArgs {
     int na, nb;
     int n_in, n_out;
     int dir;
+    const int* pin;
+    const int* pout;
 };
 
 // Optional epilogue of the last inverse pass of the matvec: crop + material and Gram terms.
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(LineCfg<L>::NT) line_fft_kernel(LineArgs a, co
         }
         int b = b0 + tb;
         C v = zero;
-        if (l < a.n_in && b < a.nb) v = in[ai * a.ia + l * a.il + (long long)b * a.ib];
+        if (l < a.n_in && b < a.nb) v = in[ai * a.ia + (a.pin ? a.pin[l] : l) * a.il + (long long)b * a.ib];
         s[l * TBP + tb] = v;
     }
     __syncthreads();
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(LineCfg<L>::NT) line_fft_kernel(LineArgs a, co
         int b = b0 + tb;
         if (l >= a.n_out || b >= a.nb) continue;
         C v = s[l * TBP + tb];
-        long long o = ai * a.oa + l * a.ol + (long long)b * a.ob;
+        long long o = ai * a.oa + (a.pout ? a.pout[l] : l) * a.ol + (long long)b * a.ob;
         if (EPI) {
             // line b = ((r * 12 + alpha) * nz + z) * ny + y, element l = x
             int alpha = (b / (epi.ny * epi.nz)) % 12;

@@ -1,4 +1,4 @@
-// Two-pass FFT of lines held in shared memory (FP32 or FP64), L = A * B with A, B in {2, 4, 8, 16}.
+// Two-pass FFT of lines held in shared memory (FP32 or FP64), L = A * B with A, B in {2, 4, 8, 16, 32}.
 //
 // With l = b + B a (input index) and k = k1 + A k2 (output index), the DFT factors as
 //   X[k1 + A k2] = sum_b wB^(b k2) [ w^(b k1) sum_a wA^(a k1) x[b + B a] ],   w = exp(-2 pi i / L),
@@ -27,6 +27,10 @@ namespace fft2 {
 constexpr double kC1 = 0.92387953251128674;  // cos(pi/8)
 constexpr double kS1 = 0.38268343236508978;  // sin(pi/8)
 constexpr double kC2 = 0.70710678118654752;  // cos(pi/4)
+constexpr double kC16 = 0.98078528040323044913;  // cos(pi/16)
+constexpr double kS16 = 0.19509032201612826785;  // sin(pi/16)
+constexpr double kC316 = 0.83146961230254523708;  // cos(3 pi/16)
+constexpr double kS316 = 0.55557023301960222474;  // sin(3 pi/16)
 
 template <typename C>
 __device__ __forceinline__ C rot(C a, double c, double s) {  // a * (c + i s), in the precision of C
@@ -93,9 +97,54 @@ struct DFT<16, C> {
     }
 };
 
-// a * w^n, w = exp(dir 2 pi i / N), N in {4, 8, 16}, n < N/2 a compile-time constant after unrolling
+// a * exp(dir i pi k / 16), k in 0..15 a compile-time constant after unrolling
+template <typename C>
+__device__ __forceinline__ C twist32(C a, int k, int dir) {
+    const double d = (double)dir;
+    switch (k) {
+        case 0: return a;
+        case 1: return rot(a, kC16, d * kS16);
+        case 2: return rot(a, kC1, d * kS1);
+        case 3: return rot(a, kC316, d * kS316);
+        case 4: return rot(a, kC2, d * kC2);
+        case 5: return rot(a, kS316, d * kC316);
+        case 6: return rot(a, kS1, d * kC1);
+        case 7: return rot(a, kS16, d * kC16);
+        case 8: return cmul_i(a, dir);
+        case 9: return rot(a, -kS16, d * kC16);
+        case 10: return rot(a, -kS1, d * kC1);
+        case 11: return rot(a, -kS316, d * kC316);
+        case 12: return rot(a, -kC2, d * kC2);
+        case 13: return rot(a, -kC316, d * kS316);
+        case 14: return rot(a, -kC1, d * kS1);
+        default: return rot(a, -kC16, d * kS16);
+    }
+}
+
+template <typename C>
+struct DFT<32, C> {
+    static __device__ __forceinline__ void run(C* v, int dir) {
+        C e[16], o[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        DFT<16, C>::run(e, dir);
+        DFT<16, C>::run(o, dir);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const C t = twist32(o[k], k, dir);
+            v[k] = cadd(e[k], t);
+            v[k + 16] = csub(e[k], t);
+        }
+    }
+};
+
+// a * w^n, w = exp(dir 2 pi i / N), N in {4, 8, 16, 32}, n < N/2 a compile-time constant after unrolling
 template <int N, typename C>
 __device__ __forceinline__ C twist(C a, int n, int dir) {
+    if constexpr (N == 32) return twist32(a, n, dir);
     const double d = (double)dir;
     switch (n * (16 / N)) {  // the same angle in sixteenths of a turn
         case 0: return a;
@@ -143,11 +192,11 @@ __device__ __forceinline__ void dft_half_out(C* v, int dir) {
     for (int k = 0; k < N / 2; ++k) v[k] = cadd(e[k], twist<N>(o[k], k, dir));
 }
 
-// factorisation L = A * B used for each length (8 <= L <= 256)
-__host__ __device__ constexpr int split_a(int L) { return L <= 16 ? 4 : (L <= 64 ? 8 : 16); }
+// factorisation L = A * B used for each length (8 <= L <= 512)
+__host__ __device__ constexpr int split_a(int L) { return L <= 16 ? 4 : (L <= 64 ? 8 : (L <= 256 ? 16 : 32)); }
 template <int L>
 struct Split {
-    static_assert(L >= 8 && L <= 256 && (L & (L - 1)) == 0, "two-pass FFT lengths are 8..256");
+    static_assert(L >= 8 && L <= 512 && (L & (L - 1)) == 0, "two-pass FFT lengths are 8..512");
     static constexpr int A = split_a(L), B = L / A;
 };
 

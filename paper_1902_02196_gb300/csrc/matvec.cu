@@ -59,7 +59,7 @@ struct ZArgs {
     unsigned mx, my, mz;  // reflection flip masks per axis
     // spectrum of the xy kernels: row py holds ky = py / by + ay * (py % by) and stored column sc
     // holds kx = colkx[sc]; by = 0 and colkx = NULL for natural order
-    const unsigned char* colkx;
+    const int* colkx;
     int ay, by;
 };
 
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
             int tb = p % TB;
             int kz = p / TB;
             if (kx0 + tb >= z.Lx) continue;
-            const int kx = z.colkx ? (int)z.colkx[kx0 + tb] : kx0 + tb;
+            const int kx = z.colkx ? z.colkx[kx0 + tb] : kx0 + tb;
             int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
             int kzo = kz <= Lz / 2 ? kz : Lz - kz;
             unsigned mask = fy ^ (kx > z.Lx / 2 ? z.mx : 0u) ^ (kz > Lz / 2 ? z.mz : 0u);
@@ -441,9 +441,9 @@ static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z
 }
 
 // The fused xy kernels need a square xy circulant of 8..128 (the column map is built at
-// setup only for such grids); the FP32 z pass with the block product needs Lz of 8..128.
+// setup only for such grids); the FP32 z pass with the block product needs Lz of 8..512.
 static bool xy_ok(const vie_handle* h) { return h->colmap != nullptr; }
-static bool zfused_ok(const vie_handle* h) { return h->L[2] >= 8 && h->L[2] <= 128; }
+static bool zfused_ok(const vie_handle* h) { return h->L[2] >= 8 && h->L[2] <= 512 && h->L[0] >= 4; }
 
 // in_elems: complex values of the matvec input (and output) vector
 template <int L, typename C>
@@ -524,38 +524,42 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     e.rows = sp.rows;
     e.ns = sp.ns;
     MatvecEpi noepi{};
-    if (xy_ok(h)) {
-        const double in_elems = sp.rows ? (double)R * 12 * sp.ns : (double)comps * ny * nx;
-        VIE_TRY(launch_xy<C>(true, h, x, W2, comps, nx, ny, noepi, sp, in_elems, s));
+    // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
+    // columns follow colkx32: the FP32 fused kernel where it applies, else the line z pass
+    auto zpass = [&](int ay, int by) -> int {
         if (sizeof(T) == 4 && zfused_ok(h)) {
             ZFArgs z{};
             z.w = reinterpret_cast<float2*>(W2);
             z.green_t = h->green32t;
-            z.colkx = h->colmap;
+            z.colkx = h->colkx32;
             z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
-            z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
+            z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
-            VIE_TRY(zpass_f32_fused(h, z, s));
-        } else {
-            ZArgs z{};
-            z.w = W2;
-            z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
-            z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
-            z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
-            z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
-            z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
-            z.colkx = h->colmap;
-            z.ay = fft2::split_a(Ly), z.by = Ly / z.ay;
-            VIE_TRY(launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s));
+            return zpass_f32_fused(h, z, s);
         }
+        ZArgs z{};
+        z.w = W2;
+        z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
+        z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+        z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+        z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
+        z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+        z.colkx = h->colkx32;
+        z.ay = ay, z.by = by;
+        return launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s);
+    };
+    if (xy_ok(h)) {
+        const double in_elems = sp.rows ? (double)R * 12 * sp.ns : (double)comps * ny * nx;
+        VIE_TRY(launch_xy<C>(true, h, x, W2, comps, nx, ny, noepi, sp, in_elems, s));
+        VIE_TRY(zpass(fft2::split_a(Ly), Ly / fft2::split_a(Ly)));
         return launch_xy<C>(false, h, W2, y, comps, nx, ny, e, sp, in_elems, s);
     }
     if (sp.rows) {
         set_error("internal: the line-transform matvec takes full-grid vectors only");
         return VIE_EINVAL;
     }
-    // x-pass: lines along x, contiguous
+    // x-pass: lines along x, contiguous; frequencies stored in the column order of colkx32
     LineArgs a{};
     a.in = x;
     a.out = W1;
@@ -564,6 +568,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.ia = 0, a.il = 1, a.ib = nx;
     a.oa = 0, a.ol = 1, a.ob = Lx;
     a.n_in = nx, a.n_out = Lx, a.dir = -1;
+    a.pout = h->colpos32;
     VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
     // y-pass
     a = LineArgs{};
@@ -575,15 +580,9 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.oa = (long long)Ly * Lx, a.ol = Lx, a.ob = 1;
     a.n_in = ny, a.n_out = Ly, a.dir = -1;
     VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
-    // z-pass with block product
-    ZArgs z{};
-    z.w = W2;
-    z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
-    z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
-    z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
-    z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
-    z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
-    VIE_TRY(launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s));
+    // z-pass with block product (rows in natural ky order: by = Ly, ay = 1 for the fused
+    // kernel's formula, by = 0 for the line z pass)
+    VIE_TRY(sizeof(T) == 4 && zfused_ok(h) ? zpass(1, Ly) : zpass(0, 0));
     // y-inverse
     a = LineArgs{};
     a.in = W2;
@@ -594,7 +593,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.oa = (long long)ny * Lx, a.ol = Lx, a.ob = 1;
     a.n_in = Ly, a.n_out = ny, a.dir = +1;
     VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "ifft_y_f64" : "ifft_y_f32", h, Ly, a, noepi, s)));
-    // x-inverse + crop + material/Gram terms
+    // x-inverse (frequencies read from their stored columns) + crop + material/Gram terms
     a = LineArgs{};
     a.in = W1;
     a.out = y;
@@ -603,6 +602,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.ia = 0, a.il = 1, a.ib = Lx;
     a.oa = 0, a.ol = 1, a.ob = nx;
     a.n_in = Lx, a.n_out = nx, a.dir = +1;
+    a.pin = h->colpos32;
     VIE_TRY((launch_line<T, true>(sizeof(T) == 8 ? "ifft_x_epilogue_f64" : "ifft_x_epilogue_f32", h, Lx, a, e, s)));
     return VIE_OK;
 }
@@ -769,6 +769,11 @@ int twiddle_setup(vie_handle* h) {
     VIE_CUDA(cudaMemcpy(h->tw32, t32.data(), total * sizeof(float2), cudaMemcpyHostToDevice));
     h->colmap = nullptr;
     const int L = h->L[0];
+    std::vector<int> kx32(L), pos32(L);
+    for (int sc = 0; sc < L; ++sc) {  // mirror pairs, then the self-mirrored columns 0 and L/2
+        const int j = sc / 2 + 1;
+        kx32[sc] = sc < L - 2 ? ((sc & 1) ? L - j : j) : (sc == L - 2 ? 0 : L / 2);
+    }
     if (L == h->L[1] && L >= 8 && L <= 128) {
         std::vector<unsigned char> map;
         if (!build_colmap(L, map)) {
@@ -778,7 +783,14 @@ int twiddle_setup(vie_handle* h) {
         VIE_CUDA(cudaMalloc(&h->colmap, map.size()));
         h->bytes_held += map.size();
         VIE_CUDA(cudaMemcpy(h->colmap, map.data(), map.size(), cudaMemcpyHostToDevice));
+        for (int sc = 0; sc < L; ++sc) kx32[sc] = map[sc];
     }
+    for (int sc = 0; sc < L; ++sc) pos32[kx32[sc]] = sc;
+    VIE_CUDA(cudaMalloc(&h->colkx32, sizeof(int) * 2 * L));
+    h->colpos32 = h->colkx32 + L;
+    h->bytes_held += sizeof(int) * 2 * L;
+    VIE_CUDA(cudaMemcpy(h->colkx32, kx32.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
+    VIE_CUDA(cudaMemcpy(h->colpos32, pos32.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
     return VIE_OK;
 }
 

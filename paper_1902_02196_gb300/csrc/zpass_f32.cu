@@ -16,12 +16,16 @@
 // kz = 0 with kz = Lz/2 keeps the second point's values in shared memory; the last
 // tile's self-mirrored columns 0 and Lx/2 reload theirs for each right-hand side.
 // ---------------------------------------------------------------------------
-constexpr int kZThreads = 128;
-constexpr int kZTile = 4;
-
+// Tiles of TB stored columns (TB / 2 mirror pairs): 4 for Lz <= 128, 2 for Lz = 256, 512.
+// One thread per (pair, kz item): NT = max(TB/2 * Lz/2, 128); two CTAs per SM when NT = 128.
 template <int LZ>
 struct ZFCfg {
-    static constexpr int GS = LZ * kZTile + 4;  // component stride: 4 float2 of padding keep half-warps apart
+    static constexpr int TB = LZ <= 128 ? 4 : 2;
+    static constexpr int NPAIR = TB / 2;
+    static constexpr int NT0 = NPAIR * LZ / 2;
+    static constexpr int NT = NT0 < 128 ? 128 : NT0;
+    static constexpr int MINB = NT == 128 ? 2 : 1;
+    static constexpr int GS = LZ * TB + TB;  // component stride: TB float2 of padding keep half-warps apart
     static constexpr int BUF = 12 * GS;
     static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 4 * 60);
 };
@@ -84,9 +88,10 @@ __device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, i
 }
 
 template <int LZ>
-__global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
-    constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = kZThreads, TB = kZTile;
-    constexpr int GS = ZFCfg<LZ>::GS, BUF = ZFCfg<LZ>::BUF;
+__global__ void __launch_bounds__(ZFCfg<LZ>::NT, ZFCfg<LZ>::MINB) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
+    using Cfg = ZFCfg<LZ>;
+    constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = Cfg::NT, TB = Cfg::TB;
+    constexpr int NPAIR = Cfg::NPAIR, GS = Cfg::GS, BUF = Cfg::BUF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sb = reinterpret_cast<float2*>(smem_raw);
     float2* tw = sb + 2 * BUF;
@@ -112,8 +117,8 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused_kernel(ZFArgs z, const fl
     auto line = [](int n) { return (n / TB) * GS + n % TB; };
 
     // block-product item of this thread: column pair ci, kz item j
-    const int ci = tid & 1, j = tid >> 1;
-    const bool single = ct == ntile - 1 && ci == 1;  // columns 0 and Lx/2: own octant columns
+    const int ci = tid % NPAIR, j = tid / NPAIR;
+    const bool single = ct == ntile - 1 && ci == NPAIR - 1;  // columns 0 and Lx/2: own octant columns
     const int kx0 = z.colkx[sc0 + 2 * ci], kx1 = z.colkx[sc0 + 2 * ci + 1];
     const unsigned fx0 = kx0 > z.Lx / 2 ? z.mx : 0u, fx1 = kx1 > z.Lx / 2 ? z.mx : 0u;
     // kz items, in transposed positions p = k2 + B k1 holding kz = k1 + A k2:
@@ -209,10 +214,10 @@ static int launch_zf_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
     constexpr size_t smem = ZFCfg<LZ>::smem;
     // set on every call: the attribute is per device and launches may come from several threads
     VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long blocks = (long long)z.Ly * (z.Lx / kZTile);
+    const long long blocks = (long long)z.Ly * (z.Lx / ZFCfg<LZ>::TB);
     const double bytes = 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
     VIE_KLAUNCH_B("zpass_block_f32", s, bytes,
-                  zfused_kernel<LZ><<<(unsigned)blocks, kZThreads, smem, s>>>(z, h->tw32 + LZ));
+                  zfused_kernel<LZ><<<(unsigned)blocks, ZFCfg<LZ>::NT, smem, s>>>(z, h->tw32 + LZ));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
@@ -224,6 +229,8 @@ int zpass_f32_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
         case 32: return launch_zf_L<32>(h, z, s);
         case 64: return launch_zf_L<64>(h, z, s);
         case 128: return launch_zf_L<128>(h, z, s);
+        case 256: return launch_zf_L<256>(h, z, s);
+        case 512: return launch_zf_L<512>(h, z, s);
     }
     set_error("z pass: unsupported length");
     return VIE_EINVAL;

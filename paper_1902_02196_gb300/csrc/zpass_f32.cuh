@@ -6,11 +6,12 @@
 struct ZFArgs {
     float2* w;                    // spectrum [R*12][Nz][Ly][Lx], in place
     const float2* green_t;        // [Oy][Ox][Oz][60]
-    const unsigned char* colkx;   // [Lx] kx of each stored column
+    const int* colkx;             // [Lx] kx of each stored column
     int R, nz, Lx, Ly, Ox, Oy, Oz;
     int ay, by;                   // split of Ly: row py holds ky = py / by + ay * (py % by)
     unsigned mx, my, mz;
 };
 
-// Launches the z pass on the spectrum of xy_fwd_kernel (Lz in 8..128).
+// Launches the z pass (Lz in 8..512, Lx >= 4) on a spectrum whose row py holds
+// ky = py / by + ay (py % by) and whose stored columns follow colkx (mirror pairs).
 int zpass_f32_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s);

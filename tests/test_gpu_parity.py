@@ -79,9 +79,10 @@ def test_green_toeplitz_parity(vie, shape, delta):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-# (12, 5, 6) has Lx != Ly and (5, 6, 70) has Lz = 256: the FP32 matvec of both takes the
-# line-transform path instead of the three-kernel one
-CASES = [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 10, 6), 3), ((16, 16, 16), 1), ((12, 5, 6), 2), ((5, 6, 70), 1)]
+# (12, 5, 6) has Lx != Ly (line transforms along x and y), (5, 6, 70) has Lz = 256 and
+# (3, 2, 130) Lz = 512 (the FP32 z pass with 2-column tiles)
+CASES = [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 10, 6), 3), ((16, 16, 16), 1), ((12, 5, 6), 2), ((5, 6, 70), 1),
+         ((3, 2, 130), 1)]
 
 
 @pytest.fixture(scope="module")
