@@ -95,6 +95,7 @@ void release(vie_handle* h) {
         cudaFree(h->green64);
         cudaFree(h->green32);
         cudaFree(h->green32t);
+        cudaFree(h->green64t);
         cudaFree(h->colmap);
         cudaFree(h->colkx32);
         cudaFree(h->tw64);
@@ -169,7 +170,7 @@ int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, cons
 
 size_t handle_green_bytes(const vie_handle* h) {
     const size_t ov = (size_t)h->O[0] * h->O[1] * h->O[2];
-    return 60 * ov * (sizeof(double2) + 2 * sizeof(float2)) + 60 * h->nv * sizeof(double2) +
+    return 60 * ov * (2 * sizeof(double2) + 2 * sizeof(float2)) + 60 * h->nv * sizeof(double2) +
            2048 * (sizeof(double2) + sizeof(float2)) + 2 * (size_t)h->L[0];
 }
 
@@ -261,6 +262,7 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
         h->green64 = share->green64;
         h->green32 = share->green32;
         h->green32t = share->green32t;
+        h->green64t = share->green64t;
         h->colmap = share->colmap;
         h->colkx32 = share->colkx32;
         h->colpos32 = share->colpos32;

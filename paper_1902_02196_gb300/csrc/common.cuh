@@ -111,6 +111,8 @@ struct vie_handle {
     float2* green32;
     // FP32 copy in the layout of the z pass of the FP32 three-kernel path: [Oy][Ox][Oz][60]
     float2* green32t;
+    // FP64 copy in the same layout, for the FP64 fused z pass
+    double2* green64t;
     // stored column order of that path's spectrum: [Lx] kx per stored column, then [Lx]
     // positions of those kx in the x transform's output order (square L <= 128 only, else null)
     unsigned char* colmap;

@@ -511,7 +511,8 @@ __global__ void embed_kernel(const double2* __restrict__ T, int nx, int ny, int 
 
 // Octant k_i in [0, L_i/2] of the transformed circulants, scaled, into FP64 and FP32 tables [60][Oz][Oy][Ox].
 __global__ void octant_kernel(const double2* __restrict__ C, int Lx, int Ly, int Lz, int t0, int nt, double scale,
-                              double2* __restrict__ g64, float2* __restrict__ g32, float2* __restrict__ g32t) {
+                              double2* __restrict__ g64, float2* __restrict__ g32, float2* __restrict__ g32t,
+                              double2* __restrict__ g64t) {
     const int Ox = Lx / 2 + 1, Oy = Ly / 2 + 1, Oz = Lz / 2 + 1;
     const long long ovol = (long long)Ox * Oy * Oz;
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -525,7 +526,9 @@ __global__ void octant_kernel(const double2* __restrict__ C, int Lx, int Ly, int
     const long long dst = (long long)(t0 + tl) * ovol + o;
     g64[dst] = v;
     g32[dst] = make_float2((float)v.x, (float)v.y);
-    g32t[(((long long)ky * Ox + kx) * Oz + kz) * 60 + t0 + tl] = make_float2((float)v.x, (float)v.y);
+    const long long tdst = (((long long)ky * Ox + kx) * Oz + kz) * 60 + t0 + tl;
+    g32t[tdst] = make_float2((float)v.x, (float)v.y);
+    g64t[tdst] = v;
 }
 
 int green_setup(vie_handle* h) {
@@ -592,9 +595,10 @@ int green_setup(vie_handle* h) {
     const long long ovol = (long long)h->O[0] * h->O[1] * h->O[2];
     if (cudaMalloc(&h->green64, sizeof(double2) * 60 * ovol) != cudaSuccess ||
         cudaMalloc(&h->green32, sizeof(float2) * 60 * ovol) != cudaSuccess ||
-        cudaMalloc(&h->green32t, sizeof(float2) * 60 * ovol) != cudaSuccess)
+        cudaMalloc(&h->green32t, sizeof(float2) * 60 * ovol) != cudaSuccess ||
+        cudaMalloc(&h->green64t, sizeof(double2) * 60 * ovol) != cudaSuccess)
         return fail((set_error("green alloc"), VIE_ENOMEM));
-    h->bytes_held += (sizeof(double2) + 2 * sizeof(float2)) * 60 * ovol;
+    h->bytes_held += (2 * sizeof(double2) + 2 * sizeof(float2)) * 60 * ovol;
     int chunk = (int)std::max<long long>(1, std::min<long long>(60, (4LL << 30) / (vol * (long long)sizeof(double2))));
     if (cudaMalloc(&C, sizeof(double2) * vol * chunk) != cudaSuccess) return fail((set_error("embed alloc"), VIE_ENOMEM));
     for (int t0 = 0; t0 < 60; t0 += chunk) {
@@ -606,7 +610,8 @@ int green_setup(vie_handle* h) {
         if (rc < 0) return fail(rc);
         long long tho = ovol * nt;
         VIE_KLAUNCH("octant", s, octant_kernel<<<(unsigned)((tho + 255) / 256), 256, 0, s>>>(C, Lx, Ly, Lz, t0, nt, 1.0 / (double)vol,
-                                                                     h->green64, h->green32, h->green32t));
+                                                                     h->green64, h->green32, h->green32t,
+                                                                     h->green64t));
         if (cudaGetLastError() != cudaSuccess) return fail((set_error("octant launch"), VIE_EDEVICE));
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail((set_error("green setup sync"), VIE_EDEVICE));

@@ -22,6 +22,7 @@
 #include "fft.cuh"
 #include "fft2.cuh"
 #include "zpass_f32.cuh"
+#include "zpass_f64.cuh"
 
 // y[12] = B(k) x[12] at one frequency point; xv/acc in registers, Green values streamed once.
 template <typename C>
@@ -525,7 +526,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     e.ns = sp.ns;
     MatvecEpi noepi{};
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
-    // columns follow colkx32: the FP32 fused kernel where it applies, else the line z pass
+    // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
         if (sizeof(T) == 4 && zfused_ok(h)) {
             ZFArgs z{};
@@ -537,6 +538,17 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
             return zpass_f32_fused(h, z, s);
+        }
+        if (sizeof(T) == 8 && zfused_ok(h)) {
+            ZDArgs z{};
+            z.w = reinterpret_cast<double2*>(W2);
+            z.green_t = h->green64t;
+            z.colkx = h->colkx32;
+            z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+            z.ay = ay, z.by = by;
+            z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            return zpass_f64_fused(h, z, s);
         }
         ZArgs z{};
         z.w = W2;
@@ -581,8 +593,8 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.n_in = ny, a.n_out = Ly, a.dir = -1;
     VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
     // z-pass with block product (rows in natural ky order: by = Ly, ay = 1 for the fused
-    // kernel's formula, by = 0 for the line z pass)
-    VIE_TRY(sizeof(T) == 4 && zfused_ok(h) ? zpass(1, Ly) : zpass(0, 0));
+    // kernels' formula, by = 0 for the line z pass)
+    VIE_TRY(zfused_ok(h) ? zpass(1, Ly) : zpass(0, 0));
     // y-inverse
     a = LineArgs{};
     a.in = W2;

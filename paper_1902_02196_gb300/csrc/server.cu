@@ -85,14 +85,15 @@ size_t work_bytes(const vie_grid& g, int R, int restart, int mode) {
     return basis + vecs + fft + mats + ((size_t)64 << 20);
 }
 
-// device bytes of a cache entry: Green tensors (FP64, FP32, FP32 transposed), Toeplitz
+// device bytes of a cache entry: Green tensors (FP64, FP32 and both transposed), Toeplitz
 // tensors, twiddles, column map, and the template handle's own material maps
 size_t green_bytes(const vie_grid& g) {
     size_t O = 1;
     const int n[3] = {g.nx, g.ny, g.nz};
     for (int i = 0; i < 3; ++i) O *= (size_t)next_pow2(2 * n[i] - 1) / 2 + 1;
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
-    return 60 * O * (16 + 8 + 8) + 60 * nv * 16 + 2048 * 24 + 1024 + nv * (4 * 16 + 3 * 8) + ((size_t)16 << 20);
+    return 60 * O * (16 + 16 + 8 + 8) + 60 * nv * 16 + 2048 * 24 + 8 * 4096 + nv * (4 * 16 + 3 * 8) +
+           ((size_t)16 << 20);
 }
 
 }  // namespace

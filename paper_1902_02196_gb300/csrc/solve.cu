@@ -361,23 +361,26 @@ __global__ void cycle_init_kernel(GState s, int R, const double* __restrict__ rn
 }
 
 // after the first projection pass: H[:, j], coefficients, rescale 1/|w|
+// (one block per right-hand side, a thread per entry i <= j)
 __global__ void coef1_kernel(GState s, int R, int j) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.x;
     if (r >= R || !s.active[r]) return;
     const int m = s.m;
     const double2* D = s.D + (long long)r * (m + 2);
     const double* n = s.nrm + (long long)r * (m + 1);
     double2* H = s.H + (long long)r * (m + 1) * m;
     const double nj = n[j];
-    for (int i = 0; i <= j; ++i) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 d = D[i];
         H[i * m + j] = make_double2(d.x / (n[i] * nj), d.y / (n[i] * nj));
         s.coef[(long long)r * (m + 1) + i] = make_double2(d.x / (n[i] * n[i]), d.y / (n[i] * n[i]));
     }
-    const double e = D[j + 1].x;
-    const double sc = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
-    s.scale[r] = sc;
-    s.sigma[r] = sc;
+    if (threadIdx.x == 0) {
+        const double e = D[j + 1].x;
+        const double sc = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
+        s.scale[r] = sc;
+        s.sigma[r] = sc;
+    }
 }
 
 // second pass where the rescaled new vector has squared length below 1/2
@@ -391,21 +394,23 @@ __global__ void reorth_kernel(GState s, int R) {
 }
 
 // after the second projection pass: correction of H[:, j], coefficients, cumulative rescale
+// (one block per right-hand side, a thread per entry i <= j)
 __global__ void coef2_kernel(GState s, int R, int j) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.x;
     if (r >= R || !s.reflag[r]) return;
     const int m = s.m;
     const double2* D = s.D + (long long)r * (m + 2);
     const double* n = s.nrm + (long long)r * (m + 1);
     double2* H = s.H + (long long)r * (m + 1) * m;
     const double f = n[j] * s.sigma[r];
-    for (int i = 0; i <= j; ++i) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 d = D[i];
         H[i * m + j].x += d.x / (n[i] * f);
         H[i * m + j].y += d.y / (n[i] * f);
         s.coef[(long long)r * (m + 1) + i] = make_double2(d.x / (n[i] * n[i]), d.y / (n[i] * n[i]));
     }
-    s.sigma[r] *= s.scale[r];
+    __syncthreads();  // every thread has read sigma
+    if (threadIdx.x == 0) s.sigma[r] *= s.scale[r];
 }
 
 // Givens step j for every active right-hand side
@@ -666,11 +671,11 @@ int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* 
         VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st));
         ++*mv_count;
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
-        VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
+        VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<R, 128, 0, st>>>(S.gs, R, j));
         VIE_TRY(S.update<VC>(U, ustride, w, j + 1, S.gs.active));
         VIE_KLAUNCH("arnoldi_reorth", st, reorth_kernel<<<gr, 128, 0, st>>>(S.gs, R));
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.reflag));
-        VIE_KLAUNCH("arnoldi_coef", st, coef2_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
+        VIE_KLAUNCH("arnoldi_coef", st, coef2_kernel<<<R, 128, 0, st>>>(S.gs, R, j));
         VIE_TRY(S.update<VC>(U, ustride, w, j + 1, S.gs.reflag));
         VIE_KLAUNCH("givens", st, givens_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
         VIE_CHECK_LAUNCH();

@@ -1,0 +1,16 @@
+// FP64 z pass with the fused 12 x 12 block product (zpass_f64.cu).
+#pragma once
+
+#include "common.cuh"
+
+struct ZDArgs {
+    double2* w;                // spectrum [R*12][Nz][Ly][Lx], in place
+    const double2* green_t;    // [Oy][Ox][Oz][60]
+    const int* colkx;          // [Lx] kx of each stored column (mirror pairs)
+    int R, nz, Lx, Ly, Ox, Oy, Oz;
+    int ay, by;                // row py holds ky = py / by + ay * (py % by)
+    unsigned mx, my, mz;
+};
+
+// Launches the FP64 z pass (Lz in 8..512, Lx >= 4).
+int zpass_f64_fused(const vie_handle* h, const ZDArgs& z, cudaStream_t s);
