@@ -12,7 +12,8 @@
 // The z spectrum stays in transposed order between the forward and inverse transforms.
 // A thread of the block product owns one (column pair, kz mirror pair) item for the
 // whole launch: the 60 Green values of its octant point stay in registers and serve
-// the four frequency points (+-kx, +-kz) of every right-hand side.  The item that pairs
+// the four frequency points (+-kx, +-kz) of every right-hand side, one column at a time
+// with packed FP32 pair FMAs.  The item that pairs
 // kz = 0 with kz = Lz/2 keeps the second point's values in shared memory; the last
 // tile's self-mirrored columns 0 and Lx/2 reload theirs for each right-hand side.
 // ---------------------------------------------------------------------------
@@ -47,44 +48,34 @@ __device__ __forceinline__ float2 xflip(float2 v, unsigned sbit) {
 }
 __device__ __forceinline__ unsigned sign_bit(unsigned mask, int a) { return (mask << (31 - a)) & 0x80000000u; }
 
-// y = B x at the two mirror columns c, c + 1 of one z position (float4 accesses); m0, m1
-// are the components whose sign flips at each column's reflected frequency point; wmask
-// selects the columns written back (3: both; 1 or 2: one, for columns with their own
-// Green values).  u: the 60 Green values (registers).
-__device__ __forceinline__ void pair_point(const float2* u, float2* s, int gs, int off, unsigned m0, unsigned m1,
-                                           int wmask) {
-    float2 x0[12], x1[12];
+// y = B x at one column of one z position with packed FP32 pairs (__ffma2_rn, two FMAs per
+// instruction): for each input b, acc1[a] += (x_b.re, x_b.re) u and acc2[a] += (x_b.im, x_b.im) u,
+// so that (B x)_a = (acc1.re - acc2.im, acc1.im + acc2.re); the Green values stay in their
+// natural (re, im) pairs.  m: components whose sign flips at this reflected frequency point.
+__device__ __forceinline__ void col_point2(const float2* u, float2* s, int gs, int off, unsigned m) {
+    float2 xr[12], xi[12], a1[12], a2[12];
 #pragma unroll
     for (int b = 0; b < 12; ++b) {
-        const float4 v = *reinterpret_cast<const float4*>(s + b * gs + off);
-        x0[b] = xflip(make_float2(v.x, v.y), sign_bit(m0, b));
-        x1[b] = xflip(make_float2(v.z, v.w), sign_bit(m1, b));
+        const float2 v = xflip(s[b * gs + off], sign_bit(m, b));
+        xr[b] = make_float2(v.x, v.x);
+        xi[b] = make_float2(v.y, v.y);
     }
 #pragma unroll
-    for (int H = 0; H < 2; ++H) {
-        float2 a0[6], a1[6];
+    for (int a = 0; a < 12; ++a) a1[a] = a2[a] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) a0[a] = a1[a] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 144; ++i) {
-            const int a = kBlockB.e[i].a, b = kBlockB.e[i].b, t = kBlockB.e[i].t;
-            if (a / 6 != H) continue;
-            const float2 ut = kBlockB.e[i].s > 0 ? u[t] : cneg(u[t]);
-            cfma(a0[a - 6 * H], ut, x0[b]);
-            cfma(a1[a - 6 * H], ut, x1[b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            const float2 r0 = xflip(a0[a], sign_bit(m0, a + 6 * H)), r1 = xflip(a1[a], sign_bit(m1, a + 6 * H));
-            float2* d = s + (a + 6 * H) * gs + off;
-            if (wmask == 3)
-                *reinterpret_cast<float4*>(d) = make_float4(r0.x, r0.y, r1.x, r1.y);
-            else if (wmask == 1)
-                d[0] = r0;
-            else
-                d[1] = r1;
+    for (int i = 0; i < 144; ++i) {
+        const int a = kBlockB.e[i].a, b = kBlockB.e[i].b, t = kBlockB.e[i].t;
+        if (kBlockB.e[i].s > 0) {
+            a1[a] = __ffma2_rn(xr[b], u[t], a1[a]);
+            a2[a] = __ffma2_rn(xi[b], u[t], a2[a]);
+        } else {
+            a1[a] = __ffma2_rn(make_float2(-xr[b].x, -xr[b].y), u[t], a1[a]);
+            a2[a] = __ffma2_rn(make_float2(-xi[b].x, -xi[b].y), u[t], a2[a]);
         }
     }
+#pragma unroll
+    for (int a = 0; a < 12; ++a)
+        s[a * gs + off] = xflip(make_float2(a1[a].x - a2[a].y, a1[a].y + a2[a].x), sign_bit(m, a));
 }
 
 template <int LZ>
@@ -190,7 +181,8 @@ __global__ void __launch_bounds__(ZFCfg<LZ>::NT, ZFCfg<LZ>::MINB) zfused_kernel(
                     for (int t = 0; t < 60; ++t) u[t] = gsec[(2 * ci + 1) * 60 + t];
                 }
                 const unsigned fz = kz > LZ / 2 ? z.mz : 0u;
-                pair_point(u, s, GS, pp * TB + 2 * ci, fy ^ fz ^ fx0, fy ^ fz ^ fx1, single ? 1 + col : 3);
+                if (!single || col == 0) col_point2(u, s, GS, pp * TB + 2 * ci, fy ^ fz ^ fx0);
+                if (!single || col == 1) col_point2(u, s, GS, pp * TB + 2 * ci + 1, fy ^ fz ^ fx1);
             }
             if (pc >= 0 && !single) {
 #pragma unroll
