@@ -213,8 +213,10 @@ struct Support {
 // y = op(x) for vectors on a support.  tmp: scratch of 2 nrhs 12 nx ny nz complex values
 // of the precision, used only when the matvec has to run on the full grid (scatter,
 // full matvec, gather).
+// shift (op PA only, optional): device [nrhs] values, y = op(x) - shift[r] x per right-hand side
+// (the shifted operator of the solver's Arnoldi steps).
 int matvec_support(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, const Support& sp,
-                   void* tmp, cudaStream_t s);
+                   void* tmp, cudaStream_t s, const double2* shift = nullptr);
 // full-grid vector <-> vector on a support (values outside the support dropped / set to zero)
 int support_gather(const vie_handle* h, int nrhs, const void* full, void* part, int precision, const Support& sp,
                    cudaStream_t s);

@@ -138,6 +138,7 @@ struct MatvecEpi {
     double g1, g234;   // Gram entries
     const int4* rows;  // support rows (x0, x1, offset) per (z, y) or NULL for the full grid
     long long ns;      // support size (voxels)
+    const double2* shift;  // op PA only, optional: y -= shift[r] x per right-hand side r
 };
 
 template <int L>
@@ -211,6 +212,10 @@ __global__ void __launch_bounds__(LineCfg<L>::NT) line_fft_kernel(LineArgs a, co
                 C c2 = reinterpret_cast<const C*>(epi.c2)[vox];
                 C t = cmul(c2, v);
                 T ig = T(1) / gl;
+                if (epi.shift) {
+                    const double2 sh = epi.shift[b / (12 * epi.ny * epi.nz)];
+                    c1 = csub(c1, mk((T)sh.x, (T)sh.y));
+                }
                 v = csub(cmul(c1, xv), mk(ig * t.x, ig * t.y));
             }
         }

@@ -328,6 +328,11 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     const R ig = (R)1 / gl;
     const C* c1 = reinterpret_cast<const C*>(epi.c1);
     const C* c2 = reinterpret_cast<const C*>(epi.c2);
+    C sh = mk((R)0, (R)0);  // shift of op PA for this plane's right-hand side
+    if (epi.shift) {
+        const double2 d = epi.shift[p / (12 * (long long)nz)];
+        sh = mk((R)d.x, (R)d.y);
+    }
 #pragma unroll 4
     for (int idx = tid; idx < ny * nx; idx += NT) {
         const int yy = idx / nx, xx = idx % nx;
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         } else if (epi.op == VIE_OP_PA) {
             const C xv = pre ? ck[idx] : xin[o];
             const C t = cmul(c2[zoff + idx], v);
-            v = csub(cmul(c1[zoff + idx], xv), mk(ig * t.x, ig * t.y));
+            v = csub(cmul(csub(c1[zoff + idx], sh), xv), mk(ig * t.x, ig * t.y));
         }
         y[o] = v;
     }
@@ -502,7 +507,7 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
 // sp: support of x and y (only the FP32 three-kernel path takes vectors on a support)
 template <typename T>
 static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws,
-                       const Support& sp = Support{}) {
+                       const Support& sp = Support{}, const double2* shift = nullptr) {
     using C = typename CT<T>::C;
     const int nx = h->nx, ny = h->ny, nz = h->nz, Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
     const long long comps = (long long)R * 12 * nz;
@@ -524,6 +529,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     }
     e.rows = sp.rows;
     e.ns = sp.ns;
+    e.shift = op == VIE_OP_PA ? shift : nullptr;
     MatvecEpi noepi{};
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
@@ -682,19 +688,43 @@ int support_scatter(const vie_handle* h, int R, const void* part, void* full, in
                                  : support_copy<float2>(h, R, part, full, sp, false, s);
 }
 
+// y -= shift[r] x for vectors of n complex values per right-hand side
+template <typename C>
+__global__ void shift_sub_kernel(C* __restrict__ y, const C* __restrict__ x, const double2* __restrict__ shift,
+                                 long long n) {
+    const int r = blockIdx.y;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    using R = decltype(C{}.x);
+    const long long o = (long long)r * n + e;
+    y[o] = csub(y[o], cmul(mk((R)shift[r].x, (R)shift[r].y), x[o]));
+}
+
 int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, int op, const Support& sp, void* tmp,
-                   cudaStream_t s) {
-    if (!sp.rows) return matvec_device(h, R, x, y, precision, op, s);
+                   cudaStream_t s, const double2* shift) {
+    if (op != VIE_OP_PA) shift = nullptr;
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, precision)));
-    if (xy_ok(h))
-        return precision == VIE_FP64 ? matvec_impl<double>(h, R, x, y, op, s, h->fft_ws.ptr, sp)
-                                     : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp);
+    if (xy_ok(h) || !sp.rows)
+        return precision == VIE_FP64 ? matvec_impl<double>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift)
+                                     : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift);
     const size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     void* tx = tmp;
     void* ty = static_cast<char*>(tmp) + c * (size_t)R * 12 * h->nv;
     VIE_TRY(support_scatter(h, R, x, tx, precision, sp, s));
     VIE_TRY(matvec_device(h, R, tx, ty, precision, op, s));
-    return support_gather(h, R, ty, y, precision, sp, s);
+    VIE_TRY(support_gather(h, R, ty, y, precision, sp, s));
+    if (shift) {
+        const long long n = 12LL * sp.ns;
+        const dim3 g((unsigned)((n + 255) / 256), R);
+        if (precision == VIE_FP64)
+            VIE_KLAUNCH("matvec_shift", s,
+                        shift_sub_kernel<double2><<<g, 256, 0, s>>>((double2*)y, (const double2*)x, shift, n));
+        else
+            VIE_KLAUNCH("matvec_shift", s,
+                        shift_sub_kernel<float2><<<g, 256, 0, s>>>((float2*)y, (const float2*)x, shift, n));
+        VIE_CHECK_LAUNCH();
+    }
+    return VIE_OK;
 }
 
 // Full forward 3-D FFT of [batch][Lz][Ly][Lx] complex double volumes, in place.

@@ -343,6 +343,7 @@ struct GState {
     int* reflag;     // [R] second Gram-Schmidt pass needed
     int* k;          // [R] Arnoldi steps of the current cycle
     int* nactive;    // [1]
+    double2* shift;  // [R] shift of the Arnoldi matvec: w = (P^-1 A - shift) u_j
 };
 
 // start of a cycle: beta = ||r||, g = (beta, 0...), u_0 = r / beta (n_0 = 1), active = beta > target
@@ -375,11 +376,21 @@ __global__ void coef1_kernel(GState s, int R, int j) {
         H[i * m + j] = make_double2(d.x / (n[i] * nj), d.y / (n[i] * nj));
         s.coef[(long long)r * (m + 1) + i] = make_double2(d.x / (n[i] * n[i]), d.y / (n[i] * n[i]));
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const double e = D[j + 1].x;
         const double sc = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
         s.scale[r] = sc;
         s.sigma[r] = sc;
+        // the matvec applied P^-1 A - shift: restore the diagonal entry, and shift the next
+        // step by it (the Krylov space and H are those of P^-1 A; the shift only removes
+        // the part of the new vector along u_j before the projections, which keeps the
+        // Gram-Schmidt passes from cancelling most of it)
+        double2 hjj = H[j * m + j];
+        hjj.x += s.shift[r].x;
+        hjj.y += s.shift[r].y;
+        H[j * m + j] = hjj;
+        if (isfinite(hjj.x) && isfinite(hjj.y)) s.shift[r] = hjj;
     }
 }
 
@@ -668,7 +679,7 @@ int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* 
         if (*host_i == 0) break;
         VC* uj = U + j * ustride;
         VC* w = U + (j + 1) * ustride;
-        VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st));
+        VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift));
         ++*mv_count;
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
         VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<R, 128, 0, st>>>(S.gs, R, j));
@@ -770,6 +781,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const size_t oDone = take(sizeof(int) * R);
     const size_t oRel = take(sizeof(double) * R);
     const size_t oK1 = take(sizeof(int) * R);
+    const size_t oShift = take(sizeof(double2) * R);
     VIE_TRY(ws_reserve(h, h->solve_ws, off));
     char* base = static_cast<char*>(h->solve_ws.ptr);
     Solver S;
@@ -801,6 +813,8 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     S.gs.reflag = reinterpret_cast<int*>(base + oRe);
     S.gs.k = reinterpret_cast<int*>(base + oK);
     S.gs.nactive = reinterpret_cast<int*>(base + oNact);
+    S.gs.shift = reinterpret_cast<double2*>(base + oShift);
+    VIE_CUDA(cudaMemsetAsync(S.gs.shift, 0, sizeof(double2) * R, st));  // the first step is unshifted
     double2* r64 = reinterpret_cast<double2*>(base + oR);
     double2* bt = reinterpret_cast<double2*>(base + oBt);
     double2* t64 = reinterpret_cast<double2*>(base + oT);
