@@ -20,6 +20,7 @@
 // rotations, the solution and every residual are FP64.  The plain mode is FP64
 // throughout.  Every reduction uses a fixed partition of each right-hand side's
 // vector, so one right-hand side's result does not depend on the others in a batch.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -303,6 +304,20 @@ __global__ void scale_from64_kernel(const double2* __restrict__ src, DC* __restr
     const double2 v = src[o];
     const double f = s[r];
     dst[o] = from_d<DC>(make_double2(v.x * f, v.y * f));
+}
+
+// out = a - b with b in FP32 (the FP32 matvec of a refinement correction)
+__global__ void sub32_kernel(const double2* __restrict__ a, const float2* __restrict__ b, double2* __restrict__ out,
+                             long long total) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    out[e] = make_double2(a[e].x - (double)b[e].x, a[e].y - (double)b[e].y);
+}
+
+__global__ void to32_kernel(const double2* __restrict__ a, float2* __restrict__ out, long long total) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    out[e] = make_float2((float)a[e].x, (float)a[e].y);
 }
 
 __global__ void sub_kernel(const double2* __restrict__ a, const double2* __restrict__ b, double2* __restrict__ out,
@@ -782,6 +797,10 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const size_t oRel = take(sizeof(double) * R);
     const size_t oK1 = take(sizeof(int) * R);
     const size_t oShift = take(sizeof(double2) * R);
+    const size_t oRs0 = take(sizeof(double2) * (size_t)R * n);  // residual at the start of the last sweep
+    const size_t oXs0 = take(sizeof(double2) * (size_t)R * n);  // solution at the start of the last sweep
+    const size_t oDn = take(sizeof(double) * R);
+    const size_t oXn = take(sizeof(double) * R);
     VIE_TRY(ws_reserve(h, h->solve_ws, off));
     char* base = static_cast<char*>(h->solve_ws.ptr);
     Solver S;
@@ -854,13 +873,51 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const double eta_min = mixed ? 2e-5 : 0.0;
     bool x_is_zero = !(flags & 1);
     bool all = false;
+    double2* rs0 = reinterpret_cast<double2*>(base + oRs0);
+    double2* xs0 = reinterpret_cast<double2*>(base + oXs0);
+    double* dn2 = reinterpret_cast<double*>(base + oDn);
+    double* xn2 = reinterpret_cast<double*>(base + oXn);
+    bool have_r0 = false;
+    // Refinement residual.  The first one (after the first sweep) is b - A x with the FP64
+    // matvec.  Later ones update the previous sweep's residual, r - A d with d the sweep's
+    // correction, when |d| <= min(1e-3, 1e5 tol) |x| for every right-hand side: then A d in
+    // FP32 carries an error of order 1e-7 |A| |d|, far below the FP64 rounding of r at the
+    // tolerance, and the FP64 matvec is replaced by an FP32 one.
     auto residual = [&]() -> int {
+        bool done_update = false;
         if (x_is_zero) {
             VIE_CUDA(cudaMemcpyAsync(r64, bt, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
-        } else {
+            done_update = true;
+        } else if (mixed && have_r0) {
+            VIE_KLAUNCH("refine_correction", st, sub_kernel<<<gt, 256, 0, st>>>(xs, xs0, t64, total));
+            VIE_TRY(S.norm2_64(t64, dn2));
+            VIE_TRY(S.norm2_64(xs, xn2));
+            std::vector<double> hd(R), hx(R);
+            VIE_CUDA(cudaMemcpyAsync(hd.data(), dn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            VIE_CUDA(cudaMemcpyAsync(hx.data(), xn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            VIE_CUDA(cudaStreamSynchronize(st));
+            const double ratio = std::min(1e-3, 1e5 * tol);
+            bool small = true;
+            for (int r = 0; r < R; ++r) small = small && hd[r] <= ratio * ratio * hx[r];
+            if (small) {
+                float2* d32 = reinterpret_cast<float2*>(base + oU);
+                float2* ad32 = d32 + total;
+                VIE_KLAUNCH("refine_correction", st, to32_kernel<<<gt, 256, 0, st>>>(t64, d32, total));
+                VIE_TRY(matvec_support(h, R, d32, ad32, VIE_FP32, VIE_OP_PA, sp, S.mv_tmp, st));
+                ++mv32;
+                VIE_KLAUNCH("residual_sub", st, sub32_kernel<<<gt, 256, 0, st>>>(rs0, ad32, r64, total));
+                done_update = true;
+            }
+        }
+        if (!done_update) {
             VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st));
             ++mv64;
             VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
+        }
+        if (mixed) {
+            VIE_CUDA(cudaMemcpyAsync(rs0, r64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
+            VIE_CUDA(cudaMemcpyAsync(xs0, xs, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
+            have_r0 = !x_is_zero;
         }
         VIE_TRY(S.norm2_64(r64, rn2));
         VIE_KLAUNCH("residual_check", st,
