@@ -170,11 +170,14 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *             over all refinement sweeps in mixed mode
  *   mode    : VIE_SOLVE_FP64 (plain FP64: every restart recomputes the residual with
  *             the FP64 matvec) or VIE_SOLVE_FP32_REFINE (FP32 GMRES with FP64 iterative
- *             refinement: each sweep recomputes the residual with the FP64 matvec, then
- *             runs FP32 cycles on the correction until every right-hand side is below
+ *             refinement: each sweep takes the residual in FP64, then runs FP32 cycles
+ *             on the correction until every right-hand side is below
  *             max(2e-5 ||r||, tol ||P^-1 b|| / 2), restarting from the residual carried
  *             by the Krylov basis; Hessenberg matrix, rotations and the solution in
- *             FP64, Krylov vectors in FP32)
+ *             FP64, Krylov vectors in FP32.  The first sweep's residual is b - A x with
+ *             the FP64 matvec; a later one is the previous residual minus A d, d the
+ *             sweep's correction, with A d from the FP32 matvec when |d| <=
+ *             min(1e-3, 1e5 tol) |x| for every right-hand side, else the FP64 matvec)
  *   flags   : bit 0 = use x as initial guess; bit 1 = also compute true_resid
  *             (one more FP64 matvec), else true_resid = -1
  * Where chi, b and the guess all vanish (air), the rows of P^-1 A are the identity and
