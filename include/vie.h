@@ -185,6 +185,9 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  * other voxels (the whole grid when that span covers it), so air costs no iterations'
  * memory traffic.  x is zero outside that span on exit.
  *   info    : vie_solve_info[nrhs] host array or NULL
+ * The handle keeps the point x1 of the solve's last FP64 residual matvec and the FP64
+ * convolution (N - G) x1 on the full grid (2 x 16 bytes per unknown of device memory) for
+ * vie_fields; a new solve on the handle replaces them.  In FP64 mode x1 is the returned x.
  * Synchronous.  Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
  */
 int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int mode,
@@ -199,7 +202,12 @@ int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int r
  *   e_coeff  : [nrhs][12][nz][ny][nx] C128 output or NULL
  *   p_abs    : double[nrhs][nz][ny][nx] output or NULL
  *   P_abs    : double[nrhs] host output or NULL
- * Synchronous when P_abs is requested.
+ * The field map needs (N - G) x.  When the handle holds the point x1 of a vie_solve (same
+ * nrhs) and |x - x1| <= 1e-3 |x| for every right-hand side, that product is the solver's
+ * FP64 (N - G) x1 plus the FP32 product of d = x - x1: the FP32 term adds a relative error
+ * of at most about 1e-6 |d| / |x| <= 1e-9 (none when x = x1, as after an FP64 solve).
+ * Otherwise one FP64 matvec.  p_abs and P_abs depend on x alone.
+ * Synchronous.
  */
 int vie_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, void* e_coeff, double* p_abs,
                double* P_abs, void* stream);

@@ -106,6 +106,8 @@ void release(vie_handle* h) {
     cudaFree(h->stage_ws.ptr);
     cudaFree(h->solve_ws.ptr);
     cudaFree(h->support_ws.ptr);
+    cudaFree(h->post_ws.ptr);
+    cudaFree(h->fcache_ws.ptr);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

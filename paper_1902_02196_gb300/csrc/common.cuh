@@ -129,6 +129,13 @@ struct vie_handle {
     Workspace stage_ws;  // host-buffer staging
     Workspace solve_ws;  // solver vectors
     Workspace support_ws;  // support rows of the current solve
+    Workspace post_ws;     // vie_fields scratch
+    // The point of the last FP64 residual matvec of vie_solve, for vie_fields: the solution
+    // x1 and the convolution (N - G) x1, both full grid [fcache_R][12][nz][ny][nx] FP64
+    // (x1 first, then the product); valid for fcache_R right-hand sides when fcache_valid.
+    Workspace fcache_ws;
+    int fcache_R;
+    int fcache_valid;
     double2* toeplitz;   // [60][nz][ny][nx] Toeplitz tensors of N - G for offsets d >= 0
     size_t bytes_held;
     // set when green64/32/32t, toeplitz, the twiddle tables and colmap belong to another
@@ -215,8 +222,14 @@ struct Support {
 // full matvec, gather).
 // shift (op PA only, optional): device [nrhs] values, y = op(x) - shift[r] x per right-hand side
 // (the shifted operator of the solver's Arnoldi steps).
+// conv (optional): full-grid [nrhs][12][nz][ny][nx] output of the convolution (N - G) x at
+// every voxel, support or not (the operator's value before its voxel-wise terms).
+// rmap, nact (optional, device list of nact < nrhs right-hand sides): compute y only for the
+// listed right-hand sides, leaving the others' y untouched (used on the fused xy path; the
+// other paths compute all of them).
 int matvec_support(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, const Support& sp,
-                   void* tmp, cudaStream_t s, const double2* shift = nullptr);
+                   void* tmp, cudaStream_t s, const double2* shift = nullptr, void* conv = nullptr,
+                   const int* rmap = nullptr, int nact = 0);
 // full-grid vector <-> vector on a support (values outside the support dropped / set to zero)
 int support_gather(const vie_handle* h, int nrhs, const void* full, void* part, int precision, const Support& sp,
                    cudaStream_t s);

@@ -139,6 +139,8 @@ struct MatvecEpi {
     const int4* rows;  // support rows (x0, x1, offset) per (z, y) or NULL for the full grid
     long long ns;      // support size (voxels)
     const double2* shift;  // op PA only, optional: y -= shift[r] x per right-hand side r
+    void* conv;            // optional: full-grid (N - G) x at every voxel, before the voxel-wise terms
+    const int* rmap;       // optional (fused xy path): spectrum right-hand side k holds right-hand side rmap[k]
 };
 
 template <int L>
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(LineCfg<L>::NT) line_fft_kernel(LineArgs a, co
         if (l >= a.n_out || b >= a.nb) continue;
         C v = s[l * TBP + tb];
         long long o = ai * a.oa + (a.pout ? a.pout[l] : l) * a.ol + (long long)b * a.ob;
+        if (EPI && epi.conv) reinterpret_cast<C*>(epi.conv)[o] = v;  // full-grid output: o is the voxel index
         if (EPI) {
             // line b = ((r * 12 + alpha) * nz + z) * ny + y, element l = x
             int alpha = (b / (epi.ny * epi.nz)) % 12;

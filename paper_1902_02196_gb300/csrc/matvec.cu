@@ -159,7 +159,8 @@ struct XYCfg {
 template <int L, typename C>
 __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     xy_fwd_kernel(const C* __restrict__ x, C* __restrict__ w, int nx, int ny, int nz, const int4* __restrict__ rows,
-                  long long ns, const unsigned char* __restrict__ cpos, const C* __restrict__ twg) {
+                  long long ns, const unsigned char* __restrict__ cpos, const C* __restrict__ twg,
+                  const int* __restrict__ rmap) {
     using Cfg = XYCfg<L, C>;
     constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
     constexpr int EPV = Cfg::EPV;
@@ -174,12 +175,13 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         tw[m] = twg[m];
         pos[m] = cpos[m];
     }
-    const long long p = blockIdx.x;
+    const long long p = blockIdx.x;  // spectrum plane; the input plane is pin (rmap: active right-hand sides)
+    const long long pin = rmap ? (long long)rmap[p / (12LL * nz)] * 12 * nz + p % (12LL * nz) : p;
     if (rows) {
         const int z = (int)(p % nz);
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = rows[(long long)z * ny + yy];
         __syncthreads();
-        const C* src = x + (p / nz) * ns;
+        const C* src = x + (pin / nz) * ns;
         for (int idx = tid; idx < ny * nx; idx += NT) {
             const int yy = idx / nx, xx = idx % nx;
             const int4 q = rw[yy];
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
             cp_async_elem(xr + yy * RS + xx, in ? src + q.z + (xx - q.x) : src, in);
         }
     } else {
-        const C* src = x + p * (long long)ny * nx;
+        const C* src = x + pin * (long long)ny * nx;
         for (int idx = tid; idx < ny * nx; idx += NT) cp_async_elem(xr + (idx / nx) * RS + idx % nx, src + idx, true);
     }
     cp_async_commit();
@@ -234,8 +236,9 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     }
 }
 
-// Inverse: W2 plane -> y plane [Ny][Nx] with the material / Gram / preconditioner epilogue.
-template <int L, typename C>
+// Inverse: W2 plane -> y plane [Ny][Nx] with the material / Gram / preconditioner epilogue;
+// CONV: also the plane's (N - G) x at every voxel to epi.conv (full grid).
+template <int L, typename C, bool CONV>
 __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     xy_inv_kernel(const C* __restrict__ w, C* __restrict__ y, MatvecEpi epi, const unsigned char* __restrict__ cpos,
                   const C* __restrict__ twg) {
@@ -255,7 +258,8 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         pos[m] = cpos[m];
     }
     const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
-    const long long p = blockIdx.x;  // plane (r * 12 + alpha) * nz + z
+    const long long p = blockIdx.x;  // spectrum plane (r * 12 + alpha) * nz + z; output plane po
+    const long long po = epi.rmap ? (long long)epi.rmap[p / (12LL * nz)] * 12 * nz + p % (12LL * nz) : p;
     if (epi.rows)
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = epi.rows[(p % nz) * ny + yy];
     const C* src = w + p * (long long)L * L;
@@ -298,8 +302,8 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         }
         __syncthreads();
     }
-    const long long base = p * (long long)ny * nx;
-    const long long cbase = (p / nz) * epi.ns;  // component block on the support
+    const long long base = po * (long long)ny * nx;
+    const long long cbase = (po / nz) * epi.ns;  // component block on the support
     const C* xin = reinterpret_cast<const C*>(epi.x);
     // the epilogue's x values of this plane arrive in the free chunk buffer during the x transform
     const bool pre = epi.op != VIE_OP_NSCAT && L * CW >= ny * nx;
@@ -330,19 +334,21 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     const C* c2 = reinterpret_cast<const C*>(epi.c2);
     C sh = mk((R)0, (R)0);  // shift of op PA for this plane's right-hand side
     if (epi.shift) {
-        const double2 d = epi.shift[p / (12 * (long long)nz)];
+        const double2 d = epi.shift[po / (12 * (long long)nz)];
         sh = mk((R)d.x, (R)d.y);
     }
+    C* conv = CONV ? reinterpret_cast<C*>(epi.conv) : nullptr;
 #pragma unroll 4
     for (int idx = tid; idx < ny * nx; idx += NT) {
         const int yy = idx / nx, xx = idx % nx;
         long long o = base + idx;
+        C v = xr[yy * RS + xx];
+        if (CONV) conv[base + idx] = v;  // every voxel of the plane, full-grid layout
         if (epi.rows) {
             const int4 q = rw[yy];
             if (xx < q.x || xx >= q.y) continue;
             o = cbase + q.z + (xx - q.x);
         }
-        C v = xr[yy * RS + xx];
         if (epi.op == VIE_OP_A) {
             const C xv = pre ? ck[idx] : xin[o];
             v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[zoff + idx], v));
@@ -459,7 +465,14 @@ static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out,
     constexpr bool f32 = sizeof(C) == 8;
     // set on every call: the attribute is per device and launches may come from several threads
     VIE_CUDA(cudaFuncSetAttribute(xy_fwd_kernel<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (sizeof(C) == 16)
+        VIE_CUDA(cudaFuncSetAttribute(xy_inv_kernel<L, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    if (e.conv && sizeof(C) != 16) {
+        set_error("internal: the convolution side output is FP64 only");
+        return VIE_EINVAL;
+    }
     if (planes > 0x7fffffffLL) {
         set_error("xy transform grid too large");
         return VIE_EINVAL;
@@ -470,13 +483,24 @@ static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out,
     if (fwd)
         VIE_KLAUNCH_B(f32 ? "fft_xy_f32" : "fft_xy_f64", s, c * (in_elems + planes * plane_full),
                       xy_fwd_kernel<L, C><<<(unsigned)planes, kXYThreads, smem, s>>>(
-                          (const C*)in, (C*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, tw));
-    else
-        VIE_KLAUNCH_B(f32 ? "ifft_xy_epilogue_f32" : "ifft_xy_epilogue_f64", s,
-                      c * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
-                           (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0)),
-                      xy_inv_kernel<L, C><<<(unsigned)planes, kXYThreads, smem, s>>>((const C*)in, (C*)out, e, cpos,
-                                                                                    tw));
+                          (const C*)in, (C*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, tw, e.rmap));
+    else {
+        const double bytes = c * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
+                                  (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0) +
+                                  (e.conv ? (double)planes * nx * ny : 0.0));
+        if constexpr (sizeof(C) == 16) {
+            if (e.conv) {
+                VIE_KLAUNCH_B("ifft_xy_epilogue_f64", s, bytes,
+                              xy_inv_kernel<L, C, true><<<(unsigned)planes, kXYThreads, smem, s>>>(
+                                  (const C*)in, (C*)out, e, cpos, tw));
+                VIE_CHECK_LAUNCH();
+                return VIE_OK;
+            }
+        }
+        VIE_KLAUNCH_B(f32 ? "ifft_xy_epilogue_f32" : "ifft_xy_epilogue_f64", s, bytes,
+                      xy_inv_kernel<L, C, false><<<(unsigned)planes, kXYThreads, smem, s>>>((const C*)in, (C*)out, e,
+                                                                                           cpos, tw));
+    }
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
@@ -507,10 +531,14 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
 // sp: support of x and y (only the FP32 three-kernel path takes vectors on a support)
 template <typename T>
 static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws,
-                       const Support& sp = Support{}, const double2* shift = nullptr) {
+                       const Support& sp = Support{}, const double2* shift = nullptr, void* conv = nullptr,
+                       const int* rmap = nullptr, int nact = 0) {
     using C = typename CT<T>::C;
     const int nx = h->nx, ny = h->ny, nz = h->nz, Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
-    const long long comps = (long long)R * 12 * nz;
+    // rmap (fused xy path only): transform only the nact right-hand sides it lists
+    if (!xy_ok(h) || nact <= 0 || nact >= R) rmap = nullptr;
+    const int Rs = rmap ? nact : R;  // right-hand sides in the spectrum
+    const long long comps = (long long)Rs * 12 * nz;
     C* W1 = reinterpret_cast<C*>(ws);
     C* W2 = W1 + comps * ny * Lx;
     MatvecEpi e{};
@@ -530,7 +558,11 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     e.rows = sp.rows;
     e.ns = sp.ns;
     e.shift = op == VIE_OP_PA ? shift : nullptr;
+    e.conv = conv;
+    e.rmap = rmap;
     MatvecEpi noepi{};
+    MatvecEpi fwdmap{};  // the forward kernel reads only rmap
+    fwdmap.rmap = rmap;
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
@@ -539,7 +571,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.w = reinterpret_cast<float2*>(W2);
             z.green_t = h->green32t;
             z.colkx = h->colkx32;
-            z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
             z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
@@ -550,7 +582,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.w = reinterpret_cast<double2*>(W2);
             z.green_t = h->green64t;
             z.colkx = h->colkx32;
-            z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
             z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
@@ -559,7 +591,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         ZArgs z{};
         z.w = W2;
         z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
-        z.R = R, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+        z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
         z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
         z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
         z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
@@ -568,8 +600,8 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         return launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s);
     };
     if (xy_ok(h)) {
-        const double in_elems = sp.rows ? (double)R * 12 * sp.ns : (double)comps * ny * nx;
-        VIE_TRY(launch_xy<C>(true, h, x, W2, comps, nx, ny, noepi, sp, in_elems, s));
+        const double in_elems = sp.rows ? (double)Rs * 12 * sp.ns : (double)comps * ny * nx;
+        VIE_TRY(launch_xy<C>(true, h, x, W2, comps, nx, ny, fwdmap, sp, in_elems, s));
         VIE_TRY(zpass(fft2::split_a(Ly), Ly / fft2::split_a(Ly)));
         return launch_xy<C>(false, h, W2, y, comps, nx, ny, e, sp, in_elems, s);
     }
@@ -625,10 +657,15 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     return VIE_OK;
 }
 
-int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s) {
+static int matvec_full(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s,
+                       void* conv) {
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, nrhs, precision)));
-    if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr);
-    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr);
+    if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv);
+    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv);
+}
+
+int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s) {
+    return matvec_full(h, nrhs, x, y, precision, op, s, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -701,17 +738,18 @@ __global__ void shift_sub_kernel(C* __restrict__ y, const C* __restrict__ x, con
 }
 
 int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, int op, const Support& sp, void* tmp,
-                   cudaStream_t s, const double2* shift) {
+                   cudaStream_t s, const double2* shift, void* conv, const int* rmap, int nact) {
     if (op != VIE_OP_PA) shift = nullptr;
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, precision)));
     if (xy_ok(h) || !sp.rows)
-        return precision == VIE_FP64 ? matvec_impl<double>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift)
-                                     : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift);
+        return precision == VIE_FP64
+                   ? matvec_impl<double>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift, conv, rmap, nact)
+                   : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift, conv, rmap, nact);
     const size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     void* tx = tmp;
     void* ty = static_cast<char*>(tmp) + c * (size_t)R * 12 * h->nv;
     VIE_TRY(support_scatter(h, R, x, tx, precision, sp, s));
-    VIE_TRY(matvec_device(h, R, tx, ty, precision, op, s));
+    VIE_TRY(matvec_full(h, R, tx, ty, precision, op, s, conv));
     VIE_TRY(support_gather(h, R, ty, y, precision, sp, s));
     if (shift) {
         const long long n = 12LL * sp.ns;

@@ -1,5 +1,6 @@
 // Material coefficients, tested incident fields / right-hand sides (Eq. 27-31) and
 // post-processing: fields and absorbed power (Section IV-C, Eq. 44).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -178,9 +179,11 @@ __global__ void dipole_kernel(GridD g, double k0, double2 ice, int R, const doub
 }
 
 // e = (e_inc + Nx / c_e) / G ; p_abs(m) = 1/2 Re{sum_a |x_a|^2 G_a / (c_e chi)} / dV ; partial sums of p_abs dV
+// nx_ + corr = (N - G) x; corr (FP32, optional) is the correction term of the cached product
 __global__ void fields_kernel(long long nv, int R, const double2* __restrict__ x, const double2* __restrict__ einc,
-                              const double2* __restrict__ nx_, const double2* __restrict__ chi, double2 ice, double g1,
-                              double g234, double dV, double2* e, double* pabs, double* partial) {
+                              const double2* __restrict__ nx_, const float2* __restrict__ corr,
+                              const double2* __restrict__ chi, double2 ice, double g1, double g234, double dV,
+                              double2* e, double* pabs, double* partial) {
     __shared__ double sh[256];
     const int rr = blockIdx.y;
     long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,7 +196,13 @@ __global__ void fields_kernel(long long nv, int R, const double2* __restrict__ x
             const double2 xv = x[o];
             q += G * (xv.x * xv.x + xv.y * xv.y);
             if (e) {
-                double2 t = cmuld(nx_[o], ice);
+                double2 nv_ = nx_[o];
+                if (corr) {
+                    const float2 c = corr[o];
+                    nv_.x += (double)c.x;
+                    nv_.y += (double)c.y;
+                }
+                double2 t = cmuld(nv_, ice);
                 e[o] = make_double2((einc[o].x + t.x) / G, (einc[o].y + t.y) / G);
             }
         }
@@ -212,6 +221,37 @@ __global__ void fields_kernel(long long nv, int R, const double2* __restrict__ x
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[(long long)rr * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// d = x - x1 in FP32, and per right-hand side (blockIdx.y) the block sums of |d|^2 and |x|^2:
+// partial[rr][block], partial[R + rr][block]; n values per right-hand side, grid-stride loop
+__global__ void fields_diff_kernel(long long n, const double2* __restrict__ x, const double2* __restrict__ x1,
+                                   float2* __restrict__ d, double* __restrict__ partial) {
+    __shared__ double sd[256], sx[256];
+    const int rr = blockIdx.y;
+    double ad = 0.0, ax = 0.0;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const long long o = (long long)rr * n + i;
+        const double2 xv = x[o], yv = x1[o];
+        const double ex = xv.x - yv.x, ey = xv.y - yv.y;
+        d[o] = make_float2((float)ex, (float)ey);
+        ad += ex * ex + ey * ey;
+        ax += xv.x * xv.x + xv.y * xv.y;
+    }
+    sd[threadIdx.x] = ad;
+    sx[threadIdx.x] = ax;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sx[threadIdx.x] += sx[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[(long long)rr * gridDim.x + blockIdx.x] = sd[0];
+        partial[(long long)(gridDim.y + rr) * gridDim.x + blockIdx.x] = sx[0];
+    }
 }
 
 __global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk, double* out) {
@@ -288,38 +328,71 @@ int rhs_dipoles_device(vie_handle* h, int R, const double* pos, const double* mo
     return VIE_OK;
 }
 
+// Fields from the product (N - G) x.  When x is within 1e-3 (per right-hand side, in norm)
+// of x1, the point of the last FP64 residual matvec of vie_solve on this handle, the
+// product is the cached FP64 one at x1 plus the FP32 product of d = x - x1: the FP32
+// term's error, at most about 1e-6 |N - G| |d|, stays below 1e-9 of the product's scale.
+// Otherwise (or with no cached point) one FP64 matvec.
 int fields_device(vie_handle* h, int R, const double2* x, const double2* e_inc, double2* e_out, double* p_abs,
                   double* P_abs_host, cudaStream_t s) {
     const long long nv = (long long)h->nv;
     const long long total = nv * 12 * R;
     const int nblk = (int)((nv + 255) / 256);
-    double2* nx = nullptr;
-    double* part = nullptr;
-    double* tot = nullptr;
-    VIE_CUDA(cudaMalloc(&nx, sizeof(double2) * total));
-    if (cudaMalloc(&part, sizeof(double) * (size_t)nblk * R + sizeof(double) * R) != cudaSuccess) {
-        cudaFree(nx);
-        set_error("fields alloc");
-        return VIE_ENOMEM;
-    }
-    tot = part + (size_t)nblk * R;
-    int rc = VIE_OK;
-    if (e_out) rc = matvec_device(h, R, x, nx, VIE_FP64, VIE_OP_NSCAT, s);
-    if (rc == VIE_OK) {
-        const double dV = h->dx * h->dy * h->dz;
-        const double2 ice = make_double2(0.0, -1.0 / (h->omega * VIE_EPS0));
-        dim3 grid(nblk, R);
-        VIE_KLAUNCH("fields", s, fields_kernel<<<grid, 256, 0, s>>>(nv, R, x, e_inc, nx, h->chi64, ice, dV, dV / 12.0, dV, e_out, p_abs, part));
-        VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<R, 256, 0, s>>>(part, nblk, tot));
-        if (cudaGetLastError() != cudaSuccess) rc = VIE_EDEVICE;
-        if (rc == VIE_OK && P_abs_host) {
-            if (cudaMemcpyAsync(P_abs_host, tot, sizeof(double) * R, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                rc = VIE_EDEVICE;
+    const int ndb = (int)std::min<long long>((12 * nv + 255) / 256, 1024);
+    auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t oPart = a256(sizeof(double2) * (size_t)total);  // product (FP64), or d and its product (FP32)
+    const size_t oDiff = oPart + a256(sizeof(double) * ((size_t)nblk * R + R));
+    const size_t bytes = oDiff + a256(sizeof(double) * (2 * (size_t)R * ndb + 2 * R));
+    VIE_TRY(ws_reserve(h, h->post_ws, bytes));
+    char* base = static_cast<char*>(h->post_ws.ptr);
+    double* part = reinterpret_cast<double*>(base + oPart);
+    double* tot = part + (size_t)nblk * R;
+    double* dpart = reinterpret_cast<double*>(base + oDiff);
+    double* dtot = dpart + 2 * (size_t)R * ndb;
+    const double2* conv = nullptr;
+    const float2* corr = nullptr;
+    if (e_out && h->fcache_valid && h->fcache_R == R) {
+        const double2* x1 = static_cast<const double2*>(h->fcache_ws.ptr);
+        float2* d32 = reinterpret_cast<float2*>(base);
+        float2* c32 = d32 + total;
+        VIE_KLAUNCH("fields_diff", s, fields_diff_kernel<<<dim3(ndb, R), 256, 0, s>>>(12 * nv, x, x1, d32, dpart));
+        VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<2 * R, 256, 0, s>>>(dpart, ndb, dtot));
+        VIE_CHECK_LAUNCH();
+        std::vector<double> hn(2 * (size_t)R);
+        VIE_CUDA(cudaMemcpyAsync(hn.data(), dtot, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaStreamSynchronize(s));
+        bool near = true, zero = true;
+        for (int r = 0; r < R; ++r) {
+            near = near && hn[r] <= 1e-6 * hn[R + r];
+            zero = zero && hn[r] == 0.0;
         }
-        if (cudaStreamSynchronize(s) != cudaSuccess) rc = VIE_EDEVICE;
+        if (near) {
+            conv = x1 + total;
+            if (!zero) {
+                VIE_TRY(matvec_device(h, R, d32, c32, VIE_FP32, VIE_OP_NSCAT, s));
+                corr = c32;
+            }
+        }
     }
-    cudaFree(nx);
-    cudaFree(part);
+    if (e_out && !conv) {
+        double2* nx = reinterpret_cast<double2*>(base);
+        VIE_TRY(matvec_device(h, R, x, nx, VIE_FP64, VIE_OP_NSCAT, s));
+        conv = nx;
+    }
+    int rc = VIE_OK;
+    const double dV = h->dx * h->dy * h->dz;
+    const double2 ice = make_double2(0.0, -1.0 / (h->omega * VIE_EPS0));
+    dim3 grid(nblk, R);
+    VIE_KLAUNCH("fields", s,
+                fields_kernel<<<grid, 256, 0, s>>>(nv, R, x, e_inc, conv, corr, h->chi64, ice, dV, dV / 12.0, dV,
+                                                   e_out, p_abs, part));
+    VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<R, 256, 0, s>>>(part, nblk, tot));
+    if (cudaGetLastError() != cudaSuccess) rc = VIE_EDEVICE;
+    if (rc == VIE_OK && P_abs_host) {
+        if (cudaMemcpyAsync(P_abs_host, tot, sizeof(double) * R, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = VIE_EDEVICE;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = VIE_EDEVICE;
     if (rc != VIE_OK) set_error("fields kernels failed");
     return rc;
 }

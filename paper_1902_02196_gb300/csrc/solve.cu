@@ -357,7 +357,7 @@ struct GState {
     int* active;     // [R]
     int* reflag;     // [R] second Gram-Schmidt pass needed
     int* k;          // [R] Arnoldi steps of the current cycle
-    int* nactive;    // [1]
+    int* nactive;    // [1 + R]: the number of active right-hand sides, then their indices
     double2* shift;  // [R] shift of the Arnoldi matvec: w = (P^-1 A - shift) u_j
 };
 
@@ -486,10 +486,12 @@ __global__ void givens_kernel(GState s, int R, int j) {
     if (res <= s.target[r] || hnext == 0.0 || !isfinite(res)) s.active[r] = 0;
 }
 
+// out[0] = number of active right-hand sides, out[1..] = their indices in increasing order
 __global__ void count_active_kernel(const int* __restrict__ active, int R, int* out) {
     int c = 0;
-    for (int r = 0; r < R; ++r) c += active[r];
-    *out = c;
+    for (int r = 0; r < R; ++r)
+        if (active[r]) out[1 + c++] = r;
+    out[0] = c;
 }
 
 // back substitution H(0:k,0:k) y = g(0:k), then the update coefficients y_i / n_i
@@ -694,7 +696,9 @@ int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* 
         if (*host_i == 0) break;
         VC* uj = U + j * ustride;
         VC* w = U + (j + 1) * ustride;
-        VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift));
+        // only the active right-hand sides (the others' w is never read)
+        VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift, nullptr,
+                               S.gs.nactive + 1, *host_i));
         ++*mv_count;
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
         VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<R, 128, 0, st>>>(S.gs, R, j));
@@ -790,7 +794,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const size_t oAct = take(sizeof(int) * R);
     const size_t oRe = take(sizeof(int) * R);
     const size_t oK = take(sizeof(int) * R);
-    const size_t oNact = take(sizeof(int));
+    const size_t oNact = take(sizeof(int) * (R + 1));
     const size_t oBn = take(sizeof(double) * R);
     const size_t oRn = take(sizeof(double) * R);
     const size_t oDone = take(sizeof(int) * R);
@@ -867,6 +871,9 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     else
         VIE_CUDA(cudaMemsetAsync(xs, 0, sizeof(double2) * total, st));
 
+    h->fcache_valid = 0;
+    VIE_TRY(ws_reserve(h, h->fcache_ws, 2 * sizeof(double2) * (size_t)R * nfull));
+
     std::vector<int> it_rhs(R, 0), hdone(R, 0);
     std::vector<double> hrel(R, 0.0), htrue(R, -1.0);
     int mv64 = 0, mv32 = 0, sweeps = 0;
@@ -910,9 +917,15 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             }
         }
         if (!done_update) {
-            VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st));
+            // the matvec also leaves (N - G) x on the full grid, kept with x for vie_fields
+            double2* cx = static_cast<double2*>(h->fcache_ws.ptr);
+            VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr,
+                                   cx + (size_t)R * nfull));
             ++mv64;
             VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
+            VIE_TRY(support_scatter(h, R, xs, cx, VIE_FP64, sp, st));
+            h->fcache_R = R;
+            h->fcache_valid = 1;
         }
         if (mixed) {
             VIE_CUDA(cudaMemcpyAsync(rs0, r64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
@@ -960,9 +973,15 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     if (!all) VIE_TRY(residual());  // residual of the last iterate when the cycle cap was hit
     VIE_TRY(support_scatter(h, R, xs, x, VIE_FP64, sp, st));
     if (flags & 2) {
-        // unpreconditioned residual ||b - A x|| / ||b|| on the full grid
-        VIE_TRY(matvec_device(h, R, x, full0, VIE_FP64, VIE_OP_A, st));
+        // unpreconditioned residual ||b - A x|| / ||b|| on the full grid; its convolution at
+        // the final x replaces the cached one for vie_fields
+        double2* cx = static_cast<double2*>(h->fcache_ws.ptr);
+        VIE_TRY(matvec_support(h, R, x, full0, VIE_FP64, VIE_OP_A, Support{}, S.mv_tmp, st, nullptr,
+                               cx + (size_t)R * nfull));
         ++mv64;
+        VIE_CUDA(cudaMemcpyAsync(cx, x, sizeof(double2) * (size_t)R * nfull, cudaMemcpyDeviceToDevice, st));
+        h->fcache_R = R;
+        h->fcache_valid = 1;
         VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gtf, 256, 0, st>>>(b, full0, full1, total_full));
         VIE_TRY(S.norm2_64(full1, rn2, nfull));
         VIE_TRY(S.norm2_64(b, bn2, nfull));
