@@ -302,6 +302,16 @@ def fp32_clock_mhz():
     return 2070.0
 
 
+def scaled_traffic(kernel, grid, L, bytes_per_launch):
+    """The recorded ncu traffic (taken on launches of all NRHS right-hand sides) scaled to a launch
+    with the given algorithmic bytes, i.e. to the right-hand sides the timed launches transformed."""
+    t = measured_traffic(kernel)
+    full, _ = kernel_model(kernel, grid, L, NRHS)
+    if t is None or not full:
+        return t
+    return t * bytes_per_launch / full
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -402,12 +412,12 @@ def run_ours(args, ws, rank, local):
         fp64_peak = 1250.0  # GFLOP/s, nominal GB300 FP64 rate
         achieved = flops_pl / avg_s / 1e9 if flops_pl else None
         roofline = dict(bound="alu", kernel=dname, achieved=achieved, peak=fp64_peak, unit="GFLOP/s",
-                        frac=achieved / fp64_peak if achieved else None, traffic=measured_traffic(dname),
+                        frac=achieved / fp64_peak if achieved else None, traffic=scaled_traffic(dname, grid, L, dbytes / dl),
                         peak_kind="nominal FP64", launches=dl, avg_ms=1000 * avg_s)
     else:
         achieved = dbytes / (dms / 1000.0) / 1e9
         roofline = dict(bound="hbm", kernel=dname, achieved=achieved, peak=hbm_peak, unit="GB/s",
-                        frac=achieved / hbm_peak, traffic=measured_traffic(dname), peak_kind=peak_kind,
+                        frac=achieved / hbm_peak, traffic=scaled_traffic(dname, grid, L, dbytes / dl), peak_kind=peak_kind,
                         launches=dl, avg_ms=1000 * avg_s, alg_bytes_per_launch=dbytes / dl)
         # right-hand sides a launch actually transformed (the solver skips converged ones), from the
         # library's per-launch algorithmic bytes, which are affine in that count; flops are linear in it
@@ -421,7 +431,7 @@ def run_ours(args, ws, rank, local):
             if flops_pl / alu_peak > (dbytes / dl) / hbm_peak:  # the ALU time floor is the larger one
                 alu = flops_pl / avg_s / 1e9
                 roofline = dict(bound="alu", kernel=dname, achieved=alu, peak=alu_peak, unit="GFLOP/s",
-                                frac=alu / alu_peak, traffic=measured_traffic(dname),
+                                frac=alu / alu_peak, traffic=scaled_traffic(dname, grid, L, dbytes / dl),
                                 peak_kind=f"FP32 FMA: {sms} SMs x 128 lanes x 2 x max SM clock",
                                 launches=dl, avg_ms=1000 * avg_s, alg_flops_per_launch=flops_pl,
                                 rhs_per_launch=(dbytes / dl - b0) / (b1 - b0),
