@@ -179,15 +179,17 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *             sweep's correction, with A d from the FP32 matvec when |d| <=
  *             min(1e-3, 1e5 tol) |x| for every right-hand side, else the FP64 matvec)
  *   flags   : bit 0 = use x as initial guess; bit 1 = also compute true_resid
- *             (one more FP64 matvec), else true_resid = -1
+ *             (one more FP64 matvec), else true_resid = -1; bit 2 = keep no point for
+ *             vie_fields (below)
  * Where chi, b and the guess all vanish (air), the rows of P^-1 A are the identity and
  * the solution is zero; the solver's vectors cover only each grid row's span of the
  * other voxels (the whole grid when that span covers it), so air costs no iterations'
  * memory traffic.  x is zero outside that span on exit.
  *   info    : vie_solve_info[nrhs] host array or NULL
- * The handle keeps the point x1 of the solve's last FP64 residual matvec and the FP64
- * convolution (N - G) x1 on the full grid (2 x 16 bytes per unknown of device memory) for
- * vie_fields; a new solve on the handle replaces them.  In FP64 mode x1 is the returned x.
+ * Unless flags bit 2 is set, the handle keeps the point x1 of the solve's last FP64
+ * residual matvec and the FP64 convolution (N - G) x1 on the full grid (2 x 16 bytes per
+ * unknown of device memory) for vie_fields; a new solve on the handle drops them.  In FP64
+ * mode x1 is the returned x.
  * Synchronous.  Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
  */
 int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int mode,

@@ -215,11 +215,12 @@ def vie_rhs_dipoles(h, pos, mom, e_inc=None, b=None, stream=None):
 
 
 def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFINE, guess=False, true_resid=False,
-              stream=None):
-    """Returns (rc, [info dict per right-hand side]); rc is VIE_OK or VIE_NOT_CONVERGED."""
+              keep_point=True, stream=None):
+    """Returns (rc, [info dict per right-hand side]); rc is VIE_OK or VIE_NOT_CONVERGED.
+    keep_point=False: the handle keeps no residual point for vie_fields (flags bit 2)."""
     n = _nrhs(b, h.nv)
     info = (vie_solve_info * n)()
-    flags = (1 if guess else 0) | (2 if true_resid else 0)
+    flags = (1 if guess else 0) | (2 if true_resid else 0) | (0 if keep_point else 4)
     rc = _check(_lib().vie_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
                                  flags, info, _stream(stream)), "vie_solve")
     return rc, [i.as_dict() for i in info]

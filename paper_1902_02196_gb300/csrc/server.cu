@@ -73,15 +73,14 @@ int next_pow2(int v) {
 }
 
 // device bytes of one request's working set (material maps, b, e_inc, x, p_abs, solver and
-// FFT workspaces, the solver's kept residual point and the fields scratch), an upper bound:
-// the solver's vectors are sized for the full grid
+// FFT workspaces), an upper bound: the solver's vectors are sized for the full grid
 size_t work_bytes(const vie_grid& g, int R, int restart, int mode) {
     const size_t nv = (size_t)g.nx * g.ny * g.nz;
     const size_t n = (size_t)R * 12 * nv;
     const size_t Lx = next_pow2(2 * g.nx - 1), Ly = next_pow2(2 * g.ny - 1);
     const size_t basis = (mode == VIE_SOLVE_FP64 ? 16 : 8) * (size_t)(restart + 1) * n;
-    // b, e_inc, x; solver r, bt, t, x; scratch; kept point x1 and its product; fields scratch
-    const size_t vecs = 16 * n * (3 + 4 + 2 + 2 + 1) + 8 * (size_t)R * nv;
+    // b, e_inc, x; solver r, bt, t, x; scratch (the solve keeps no point for vie_fields: flags 4)
+    const size_t vecs = 16 * n * (3 + 4 + 2) + 8 * (size_t)R * nv;
     const size_t fft = 16 * (size_t)R * 12 * g.nz * (g.ny * Lx + Ly * Lx);
     const size_t mats = nv * (4 * 16 + 3 * 8);
     return basis + vecs + fft + mats + ((size_t)64 << 20);
@@ -221,7 +220,8 @@ int run_request(vie_server* s, Req& r, bool builder, vie_solve_info* info) {
     g.bufs.push_back(pa);
     void* st = h->stream;
     SRV_TRY(vie_rhs_dipoles(h, r.nrhs, r.pos.data(), r.mom.data(), e, b, st));
-    const int rc = vie_solve(h, r.nrhs, b, x, r.tol, r.restart, r.maxit, r.mode, 0, info, st);
+    // flags 4: the request's vie_fields takes no field map, so the solve keeps no point for it
+    const int rc = vie_solve(h, r.nrhs, b, x, r.tol, r.restart, r.maxit, r.mode, 4, info, st);
     if (rc < 0) return rc;
     std::vector<double> P(r.nrhs);
     SRV_TRY(vie_fields(h, r.nrhs, x, e, nullptr, (double*)pa, P.data(), st));

@@ -747,6 +747,8 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         set_error("restart above 128 is not supported");
         return VIE_EINVAL;
     }
+    h->fcache_valid = 0;  // a new solve replaces the point kept for vie_fields
+    const bool keep = !(flags & 4);
     // vectors live on the support of the solve: [R][12][ns]
     Support sp;
     VIE_TRY(build_support(h, R, b, (flags & 1) ? x : nullptr, &sp, st));
@@ -871,8 +873,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     else
         VIE_CUDA(cudaMemsetAsync(xs, 0, sizeof(double2) * total, st));
 
-    h->fcache_valid = 0;
-    VIE_TRY(ws_reserve(h, h->fcache_ws, 2 * sizeof(double2) * (size_t)R * nfull));
+    if (keep) VIE_TRY(ws_reserve(h, h->fcache_ws, 2 * sizeof(double2) * (size_t)R * nfull));
 
     std::vector<int> it_rhs(R, 0), hdone(R, 0);
     std::vector<double> hrel(R, 0.0), htrue(R, -1.0);
@@ -918,14 +919,16 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         }
         if (!done_update) {
             // the matvec also leaves (N - G) x on the full grid, kept with x for vie_fields
-            double2* cx = static_cast<double2*>(h->fcache_ws.ptr);
+            double2* cx = keep ? static_cast<double2*>(h->fcache_ws.ptr) : nullptr;
             VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr,
-                                   cx + (size_t)R * nfull));
+                                   keep ? cx + (size_t)R * nfull : nullptr));
             ++mv64;
             VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
-            VIE_TRY(support_scatter(h, R, xs, cx, VIE_FP64, sp, st));
-            h->fcache_R = R;
-            h->fcache_valid = 1;
+            if (keep) {
+                VIE_TRY(support_scatter(h, R, xs, cx, VIE_FP64, sp, st));
+                h->fcache_R = R;
+                h->fcache_valid = 1;
+            }
         }
         if (mixed) {
             VIE_CUDA(cudaMemcpyAsync(rs0, r64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
@@ -975,13 +978,15 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     if (flags & 2) {
         // unpreconditioned residual ||b - A x|| / ||b|| on the full grid; its convolution at
         // the final x replaces the cached one for vie_fields
-        double2* cx = static_cast<double2*>(h->fcache_ws.ptr);
+        double2* cx = keep ? static_cast<double2*>(h->fcache_ws.ptr) : nullptr;
         VIE_TRY(matvec_support(h, R, x, full0, VIE_FP64, VIE_OP_A, Support{}, S.mv_tmp, st, nullptr,
-                               cx + (size_t)R * nfull));
+                               keep ? cx + (size_t)R * nfull : nullptr));
         ++mv64;
-        VIE_CUDA(cudaMemcpyAsync(cx, x, sizeof(double2) * (size_t)R * nfull, cudaMemcpyDeviceToDevice, st));
-        h->fcache_R = R;
-        h->fcache_valid = 1;
+        if (keep) {
+            VIE_CUDA(cudaMemcpyAsync(cx, x, sizeof(double2) * (size_t)R * nfull, cudaMemcpyDeviceToDevice, st));
+            h->fcache_R = R;
+            h->fcache_valid = 1;
+        }
         VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gtf, 256, 0, st>>>(b, full0, full1, total_full));
         VIE_TRY(S.norm2_64(full1, rn2, nfull));
         VIE_TRY(S.norm2_64(b, bn2, nfull));

@@ -260,7 +260,18 @@ def test_fields_reuse_the_solver_product(vie, shape):
     assert st.get("fields_diff") == 1 and f64_matvec_launches(st) > 0, st
     assert torch.equal(ef, ef2)
 
+    # a solve that keeps no point (flags bit 2): the FP64 matvec, the same bits as the reference
+    x4 = torch.zeros_like(b)
+    rc, _ = vie.vie_solve(h, b, x4, tol=1e-7, restart=30, maxit=40, mode=vie.VIE_SOLVE_FP32_REFINE,
+                          keep_point=False)
+    assert rc == vie.VIE_OK and rel(x4.cpu().numpy(), x.cpu().numpy()) <= 1e-6  # both meet tol 1e-7
+    ef, _, _, st = fields_launches(vie, h, x4, e, R, g.shape)
+    ef2, _, _, _ = fields_launches(vie, h2, x4, e, R, g.shape)
+    assert "fields_diff" not in st and f64_matvec_launches(st) > 0, st
+    assert torch.equal(ef, ef2)
+
     # another number of right-hand sides: the FP64 matvec
+    rc, _ = vie.vie_solve(h, b, x, tol=1e-7, restart=30, maxit=40, mode=vie.VIE_SOLVE_FP32_REFINE)
     xs, es = x[:2].contiguous(), e[:2].contiguous()
     ef, _, _, st = fields_launches(vie, h, xs, es, 2, g.shape)
     ef2, _, _, _ = fields_launches(vie, h2, xs, es, 2, g.shape)
