@@ -295,6 +295,23 @@ def measured_traffic(kernel):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(x, device=None):
+    """Largest value of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world_size, max_seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world_size / max_seconds
+
+
 def fp32_clock_mhz():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -363,6 +380,43 @@ def run_ours(args, ws, rank, local):
         P = vie.vie_fields(h, x, e_inc, e_coeff, p_abs, stream=stream)
         return rc, info, P
 
+    def run_e2e():
+        """The same step through the C ABI with pinned host buffers, copies inside the timed region."""
+        bh = b.cpu().pin_memory()
+        eh = e_inc.cpu().pin_memory()
+        xh = torch.empty(shape, dtype=torch.complex128).pin_memory()
+        ph = torch.empty((NRHS,) + g.shape, dtype=torch.float64).pin_memory()
+        ech = torch.empty(shape, dtype=torch.complex128).pin_memory()
+        split = [0.0, 0.0]
+
+        def step_host():
+            # both calls return after their device-to-host copies (host buffers synchronize the stream)
+            t0 = time.perf_counter()
+            vie.vie_solve(h, bh, xh, tol=TOL, restart=RESTART, maxit=MAXIT, mode=vie.VIE_SOLVE_FP32_REFINE,
+                          stream=stream)
+            t1 = time.perf_counter()
+            P = vie.vie_fields(h, xh, eh, ech, ph, stream=stream)
+            split[0] += t1 - t0
+            split[1] += time.perf_counter() - t1
+            return P
+
+        step_host()
+        ke = max(1, min(3, args.steps))
+        barrier()
+        torch.cuda.synchronize()
+        split[:] = [0.0, 0.0]
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            step_host()
+        torch.cuda.synchronize()
+        te = max_over_ranks((time.perf_counter() - t0) / ke, dev)
+        vb = NRHS * 12 * g.nv * 16
+        return dict(value=job_throughput(NRHS, ws, te), unit="solves/s", h2d_bytes_per_step=3 * vb,
+                    d2h_bytes_per_step=2 * vb + NRHS * g.nv * 8 + NRHS * 8,
+                    solve_ms=1e3 * split[0] / ke, fields_ms=1e3 * split[1] / ke,
+                    note="C ABI with pinned host buffers: b in, x out; x and e_inc in, field map, p_abs and "
+                         "P_abs out; slowest rank")
+
     for _ in range(max(3, args.warmup)):
         rc, info, P = step()
     barrier()
@@ -389,13 +443,11 @@ def run_ours(args, ws, rank, local):
     vie.vie_stats_reset(False)
     step_ms = [a.elapsed_time(bb) for a, bb in evs]
     total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = NRHS * args.steps * ws / (total_ms / 1000.0)
+    total_ms = max_over_ranks(total_ms, dev)
+    value = job_throughput(NRHS * args.steps, ws, total_ms / 1000.0)
     rcs = [r for r, _, _ in infos]
     last_info = infos[-1][1]
+    e2e = None if args.no_e2e else run_e2e()  # every rank, like the timed steps
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -499,40 +551,8 @@ def run_ours(args, ws, rank, local):
                            iterations=info64[0]["iterations"], max_resid=max(i["resid"] for i in info64))
         out["speedup_vs_fp64"] = value / (NRHS * ws / t64)
 
-    if not args.no_e2e:
-        bh = b.cpu().pin_memory()
-        eh = e_inc.cpu().pin_memory()
-        xh = torch.empty(shape, dtype=torch.complex128).pin_memory()
-        ph = torch.empty((NRHS,) + g.shape, dtype=torch.float64).pin_memory()
-        ech = torch.empty(shape, dtype=torch.complex128).pin_memory()
-
-        split = [0.0, 0.0]
-
-        def step_host():
-            # both calls return after their device-to-host copies (host buffers synchronize the stream)
-            t0 = time.perf_counter()
-            vie.vie_solve(h, bh, xh, tol=TOL, restart=RESTART, maxit=MAXIT, mode=vie.VIE_SOLVE_FP32_REFINE,
-                          stream=stream)
-            t1 = time.perf_counter()
-            P = vie.vie_fields(h, xh, eh, ech, ph, stream=stream)
-            split[0] += t1 - t0
-            split[1] += time.perf_counter() - t1
-            return P
-
-        step_host()
-        ke = max(1, min(3, args.steps))
-        torch.cuda.synchronize()
-        split[:] = [0.0, 0.0]
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            step_host()
-        torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / ke
-        vb = NRHS * 12 * g.nv * 16
-        out["e2e"] = dict(value=NRHS * ws / te, unit="solves/s", h2d_bytes_per_step=3 * vb,
-                          d2h_bytes_per_step=2 * vb + NRHS * g.nv * 8 + NRHS * 8,
-                          solve_ms=1e3 * split[0] / ke, fields_ms=1e3 * split[1] / ke,
-                          note="C ABI with pinned host buffers: b in, x out; x and e_inc in, field map, p_abs and P_abs out")
+    if e2e is not None:
+        out["e2e"] = e2e
     if not args.no_cpu and ws == 1:
         try:
             out["cpu_baseline"] = cpu_baseline_block()
