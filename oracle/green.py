@@ -1,4 +1,4 @@
-"""Galerkin entries of the N operator for PWL functions on voxels (oracle; test infrastructure only).
+"""Galerkin entries of the N and K operators for PWL functions on voxels (oracle; test infrastructure only).
 
 What is computed (Section III-B/C, Eq. 25, Eq. 32-34, Eq. 42-43):
 
@@ -418,6 +418,57 @@ def q_entries(delta, k0, D, mom=None):
                             v += ca * cb * pair_integral(fa, fb, D, mom)
                     Q[comp(p, l), comp(q, lp)] = dV * dV / (delta[p] * delta[q]) * v
     return Q
+
+
+# ---------------------------------------------------------------------------
+# K operator (Eq. 8: K u = curl S u), for the magnetic field h = h_inc + K j (tot_fields)
+# ---------------------------------------------------------------------------
+
+LEVI_CIVITA = np.zeros((3, 3, 3))
+for _i, _j, _k in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+    LEVI_CIVITA[_i, _j, _k] = 1.0
+    LEVI_CIVITA[_i, _k, _j] = -1.0
+
+
+def k_entries(delta, k0, D, mom=None):
+    """All 144 Galerkin entries K^{alpha beta}(d) = < f_m^{pl}, K f_n^{ql'} > (Eq. 25) for offsets
+    D (n, 3) = (dx, dy, dz) in voxels; complex array (12, 12, n).
+
+    (K u)_p = (curl S u)_p = sum_{j,q} eps_{pjq} d_j S u_q, so with d_j acting on g(r - r'),
+
+        K^{(p,l),(q,l')}(d) = sum_j eps_{pjq} int int N^l_m(r) d_j g(r - r') N^{l'}_n(r') dr dr'
+                            = - sum_j eps_{pjq} int int (D_j N^l_m)(r) g(r - r') N^{l'}_n(r') dr dr',
+
+    integrating by parts in r over the testing function's support: D_j N^l is its distributional
+    derivative (the volume part and the point masses of its jumps on the faces s_j = +-1/2),
+    i.e. divergence_pieces(j, l) / Delta_j.  The kernel d_j g is only weakly singular; after this
+    step every term is g times polynomials, evaluated by the same cell moments as N.
+    """
+    D = np.asarray(D, dtype=np.int64).reshape(-1, 3)
+    delta = np.asarray(delta, dtype=float)
+    if mom is None:
+        mom = prepare_moments(delta, k0, D)
+    dV = float(np.prod(delta))
+    # P[j][l][l'] = int int (D_j N^l) g N^{l'} (physical units)
+    P = np.zeros((3, 4, 4, len(D)), dtype=complex)
+    for j in range(3):
+        for l in range(1, 5):
+            for lp in range(1, 5):
+                v = np.zeros(len(D), dtype=complex)
+                for c, fa in divergence_pieces(j, l):
+                    v += c * pair_integral(fa, basis_factors(lp), D, mom)
+                P[j, l - 1, lp - 1] = dV * dV / delta[j] * v
+    T = np.zeros((NCOMP, NCOMP, len(D)), dtype=complex)
+    for p in range(3):
+        for q in range(3):
+            for j in range(3):
+                e = LEVI_CIVITA[p, j, q]
+                if e == 0.0:
+                    continue
+                for l in range(1, 5):
+                    for lp in range(1, 5):
+                        T[comp(p, l), comp(q, lp)] -= e * P[j, l - 1, lp - 1]
+    return T
 
 
 def all_offsets(nx, ny, nz):
