@@ -485,3 +485,10 @@ def toeplitz_tensors(grid, k0):
     D = all_offsets(grid.nx, grid.ny, grid.nz)
     T = n_entries((grid.dx, grid.dy, grid.dz), k0, D)
     return T.reshape(NCOMP, NCOMP, 2 * grid.nz - 1, 2 * grid.ny - 1, 2 * grid.nx - 1)
+
+
+def k_toeplitz_tensors(grid, k0):
+    """Toeplitz defining tensors of K for every offset, laid out as toeplitz_tensors."""
+    D = all_offsets(grid.nx, grid.ny, grid.nz)
+    T = k_entries((grid.dx, grid.dy, grid.dz), k0, D)
+    return T.reshape(NCOMP, NCOMP, 2 * grid.nz - 1, 2 * grid.ny - 1, 2 * grid.nx - 1)

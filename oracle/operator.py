@@ -18,7 +18,7 @@ import dataclasses
 import numpy as np
 
 from . import C0, EPS0
-from .green import NCOMP, gram, toeplitz_tensors
+from .green import NCOMP, gram, k_toeplitz_tensors, toeplitz_tensors
 
 
 def k0_of(freq):
@@ -108,6 +108,13 @@ class NOperator:
         Y = _block_apply(self.Chat, X)
         y = np.fft.ifftn(Y, axes=(-3, -2, -1))
         return y[..., :nz, :ny, :nx]
+
+
+class KOperator(NOperator):
+    """K x (K u = curl S u, Eq. 8) by the same circulant embedding + FFT, from the K tensors."""
+
+    def __init__(self, grid, k0, T=None):
+        super().__init__(grid, k0, k_toeplitz_tensors(grid, k0) if T is None else T)
 
 
 def _block_apply(Chat, X):

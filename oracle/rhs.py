@@ -82,6 +82,17 @@ def dipole_field(r, r0, moment, k0, ce):
     return E / ce
 
 
+def dipole_hfield(r, r0, moment, k0):
+    """Incident H field (..., 3) at points r of a Hertzian dipole p = moment (A m) at r0:
+    h = K (p delta_r0) = curl (g p) = grad g x p (Eq. 8), grad g = g (-1/R - i k0) R^."""
+    R = r - np.asarray(r0, dtype=float)
+    Rn = np.sqrt((R**2).sum(-1))
+    Rh = R / Rn[..., None]
+    g = np.exp(-1j * k0 * Rn) / (4.0 * np.pi * Rn)
+    grad = (g * (-1.0 / Rn - 1j * k0))[..., None] * Rh
+    return np.cross(grad, np.broadcast_to(np.asarray(moment, dtype=float), grad.shape))
+
+
 def tested_field_quadrature(grid, field, n=6):
     """Tested field of an arbitrary callable field(r (..., 3)) -> (..., 3) with n^3 Gauss points per voxel."""
     x, w = gauss01(n)
@@ -110,6 +121,14 @@ def dipoles_tested(grid, k0, ce, positions, moments, n=6):
     out = []
     for r0, mom in zip(positions, moments):
         out.append(tested_field_quadrature(grid, lambda r: dipole_field(r, r0, mom, k0, ce), n))
+    return np.array(out)
+
+
+def dipoles_tested_h(grid, k0, positions, moments, n=6):
+    """Tested incident magnetic fields of R dipoles: (R, 12, Nz, Ny, Nx)."""
+    out = []
+    for r0, mom in zip(positions, moments):
+        out.append(tested_field_quadrature(grid, lambda r: dipole_hfield(r, r0, mom, k0), n))
     return np.array(out)
 
 

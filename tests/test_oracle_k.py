@@ -1,4 +1,4 @@
-"""Pins of the oracle's Galerkin entries of the K operator (K u = curl S u, Eq. 8; Eq. 25).
+"""Pins of the oracle's K operator (K u = curl S u, Eq. 8; Eq. 25) and magnetic post-processing.
 
 Each checks the reduced evaluation against an independent route: plain 6-D Gauss of the
 unreduced kernel eps_{pjq} d_j g on separated voxels, the integration by parts done on the
@@ -12,8 +12,13 @@ import os
 import numpy as np
 import pytest
 
+from oracle import EPS0, MU0
 from oracle import green as G
+from oracle import operator as O
+from oracle import post as OP
+from oracle import rhs as RHS
 from oracle.quadrature import gauss01
+from synth import Grid, random_coefficients, random_tissue
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
 DELTA = np.array([0.004, 0.005, 0.0045])
@@ -151,3 +156,89 @@ def test_quadrature_self_convergence(monkeypatch):
     monkeypatch.setattr(G.Moments, "DUFFY_S", G.Moments.DUFFY_S + 4)
     T1 = G.k_entries(DELTA, 12.0, NEAR)
     assert np.max(np.abs(T0 - T1)) < 1e-13 * np.max(np.abs(T0))
+
+
+# ---------------------------------------------------------------------------
+# Magnetic field of a dipole, the K operator on a grid, and the magnetic post-processing
+# ---------------------------------------------------------------------------
+
+F = 298e6
+KF = O.k0_of(F)
+R0 = np.array([0.01, -0.02, 0.03])
+PM = np.array([0.2, -0.5, 1.0])
+PTS = np.array([[0.05, 0.04, -0.02], [0.1, 0.0, 0.0], [0.013, -0.017, 0.09]])
+
+
+def _g(x):
+    d = np.linalg.norm(x - R0)
+    return np.exp(-1j * KF * d) / (4 * np.pi * d)
+
+
+def _richardson(fd, h):
+    return (4.0 * fd(h) - fd(2 * h)) / 3.0  # O(h^4) from two central differences
+
+
+def test_dipole_hfield_matches_finite_differences():
+    """h = grad g x p vs central differences of g (no closed-form derivative)."""
+    H = RHS.dipole_hfield(PTS, R0, PM, KF)
+    for i, ri in enumerate(PTS):
+        grad = _richardson(lambda h: np.array([(_g(ri + e * h) - _g(ri - e * h)) / (2 * h) for e in np.eye(3)]), 1e-4)
+        ref = np.cross(grad, PM)
+        assert np.linalg.norm(H[i] - ref) < 1e-8 * np.linalg.norm(ref)
+
+
+def test_dipole_fields_obey_faraday():
+    """curl e_inc = -i omega mu0 h_inc (time factor exp(i omega t)): the electric field of the
+    dipole (pinned separately) and its magnetic field agree in sign and scale."""
+    ce = 1j * 2 * np.pi * F * EPS0
+    for ri in PTS:
+        def curl(h):
+            J = np.zeros((3, 3), dtype=complex)  # J[a, b] = d E_a / d x_b
+            for b in range(3):
+                e = np.eye(3)[b] * h
+                J[:, b] = (RHS.dipole_field((ri + e)[None], R0, PM, KF, ce)[0]
+                           - RHS.dipole_field((ri - e)[None], R0, PM, KF, ce)[0]) / (2 * h)
+            return np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+        lhs = _richardson(curl, 1e-4)
+        rhs = -1j * 2 * np.pi * F * MU0 * RHS.dipole_hfield(ri[None], R0, PM, KF)[0]
+        assert np.linalg.norm(lhs - rhs) < 1e-7 * np.linalg.norm(rhs)
+
+
+def test_k_operator_fft_equals_dense_product():
+    """K x by circulant embedding + FFT equals the dense Galerkin matrix of K applied to x."""
+    g = Grid(3, 2, 4, 0.004, 0.005, 0.0045)
+    T = G.k_toeplitz_tensors(g, KF)
+    x = random_coefficients(g, 2, seed=3)
+    Kop = O.KOperator(g, KF, T)
+    y = Kop.apply(x)
+    M = O.dense_N(g, T)  # entry (m alpha, n beta) = T^{alpha beta}(m - n), any operator
+    ref = (M @ x.reshape(2, -1).T).T.reshape(x.shape)
+    assert np.max(np.abs(y - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_magnetic_energy_is_the_integral_of_the_pwl_field():
+    """W_m from the Gram-weighted coefficients equals 1/4 mu0 int |sum_l h_l N^l|^2 over the tissue
+    voxels by direct quadrature of the PWL field; b1+ is mu0 (h_x + i h_y) of the voxel averages."""
+    g = Grid(3, 3, 2, 0.004, 0.005, 0.0045)
+    eps, sig = random_tissue(g, seed=8, air_fraction=0.4)
+    prob = O.Problem(g, F, eps, sig)
+    h = random_coefficients(g, 1, seed=9)[0]
+    w, W = OP.magnetic_energy(prob, h)
+    x, wq = gauss01(4)
+    s = x - 0.5
+    ref = 0.0
+    for iz in range(g.nz):
+        for iy in range(g.ny):
+            for ix in range(g.nx):
+                if prob.chi[iz, iy, ix] == 0:
+                    continue
+                for a, wa in zip(s, wq):
+                    for b, wb in zip(s, wq):
+                        for c, wc in zip(s, wq):
+                            phi = np.array([1.0, a, b, c])
+                            v = np.array([h[4 * p:4 * p + 4, iz, iy, ix] @ phi for p in range(3)])
+                            ref += wa * wb * wc * prob.dV * 0.25 * MU0 * np.sum(np.abs(v) ** 2)
+    assert abs(W - ref) < 1e-12 * ref
+    assert np.all(w[prob.chi == 0] == 0)
+    b1 = OP.b1_plus(h)
+    assert np.allclose(b1, MU0 * (h[0] + 1j * h[4]), rtol=0, atol=0)
