@@ -224,6 +224,21 @@ int vie_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, void* 
  */
 int vie_green_toeplitz(vie_handle* h, void* out);
 
+/*
+ * vie_green_toeplitz_k -- the 30 unique Toeplitz tensors of the K operator, K u = curl S u
+ * (Eq. 8; Galerkin entries of Eq. 25), for offsets d in [0,nx)x[0,ny)x[0,nz):
+ * out[t][dz][dy][dx] C128 with t = 10 j + ll, j the axis of the derivative (x, y, z) and ll
+ * the ordered scalar pair l <= l' as for vie_green_toeplitz (Section III-C: the
+ * anti-symmetric kernel has 3 unique dyadic components, 3 x 10 = 30 tensors):
+ *   P_t(d) = int int (d_j N^l)(r) g(r - r') N^l'(r') dr dr'   (d_j N^l with its face jumps),
+ *   K^{(p,l),(q,l')}(d) = -eps_pjq P_t(d)   (eps the Levi-Civita symbol).
+ * Computed on the device at each call (the handle keeps the cell moments of vie_setup for
+ * no longer than setup, so they are computed again).  out: host or device memory of
+ * 30 nx ny nz complex values.  Entries for negative offsets follow from the reflection
+ * parities of N times -1.  Synchronous.  Errors: VIE_EINVAL (NULL), VIE_ENOMEM, VIE_EDEVICE.
+ */
+int vie_green_toeplitz_k(vie_handle* h, void* out);
+
 /* Sizes used by the handle: FFT lengths per axis and bytes of device memory held. */
 int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes);
 

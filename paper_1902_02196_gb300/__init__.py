@@ -24,7 +24,7 @@ VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
 
 EXPORTS = (
     "vie_setup", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
-    "vie_fields", "vie_green_toeplitz", "vie_info", "vie_strerror", "vie_last_error",
+    "vie_fields", "vie_green_toeplitz", "vie_green_toeplitz_k", "vie_info", "vie_strerror", "vie_last_error",
     "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc",
     "vie_server_create", "vie_server_destroy", "vie_submit", "vie_poll", "vie_server_stats",
 )
@@ -97,6 +97,7 @@ def _lib():
     lib.vie_solve.argtypes = [P, I, P, P, D, I, I, I, I, ctypes.POINTER(vie_solve_info), P]
     lib.vie_fields.argtypes = [P, I, P, P, P, P, ctypes.POINTER(D), P]
     lib.vie_green_toeplitz.argtypes = [P, P]
+    lib.vie_green_toeplitz_k.argtypes = [P, P]
     lib.vie_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(S)]
     lib.vie_strerror.argtypes = [I]
     lib.vie_strerror.restype = ctypes.c_char_p
@@ -237,6 +238,11 @@ def vie_fields(h, x, e_inc, e_coeff=None, p_abs=None, stream=None):
 
 def vie_green_toeplitz(h, out):
     return _check(_lib().vie_green_toeplitz(h.ptr, _ptr(out)), "vie_green_toeplitz")
+
+
+def vie_green_toeplitz_k(h, out):
+    """The 30 Toeplitz tensors of the K operator, [30][nz][ny][nx] complex128 (host or device)."""
+    return _check(_lib().vie_green_toeplitz_k(h.ptr, _ptr(out)), "vie_green_toeplitz_k")
 
 
 def vie_info(h):

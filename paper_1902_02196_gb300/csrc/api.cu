@@ -399,4 +399,16 @@ int vie_green_toeplitz(vie_handle* h, void* out) {
     return VIE_OK;
 }
 
+int vie_green_toeplitz_k(vie_handle* h, void* out) {
+    g_last_error.clear();
+    REQUIRE(h && out, "NULL argument");
+    const size_t bytes = 30 * h->nv * sizeof(double2);
+    Stager sg{h, h->stream};
+    sg.add(out, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(green_k_toeplitz(h, static_cast<double2*>(d[0]), h->stream));
+    return sg.finish(d);
+}
+
 }  // extern "C"

@@ -467,6 +467,31 @@ __global__ void assemble_kernel(GreenArgs A) {
     A.out[(long long)t * nd + di] = val;
 }
 
+// K operator (K u = curl S u): P_t(d) = (dV^2 / Delta_j) int int (D_j N^la) g N^lb for
+// t = 10 j + ll(la, lb), la <= lb, d in [0, N)^3; thread per (d, t).  D_j N^la is the
+// distributional derivative (volume part and face masses), the testing-side integration by
+// parts that turns the weakly singular d_j g into g.  K^{(p,la),(q,lb)}(d) = -eps_pjq P_t(d).
+__global__ void assemble_k_kernel(GreenArgs A) {
+    const long long nd = (long long)A.g.nx * A.g.ny * A.g.nz;
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nd * 30) return;
+    const int t = (int)(gid % 30);
+    const long long di = gid / 30;
+    const int dd[3] = {(int)(di % A.g.nx), (int)((di / A.g.nx) % A.g.ny), (int)(di / ((long long)A.g.nx * A.g.ny))};
+    const int j = t / 10, ll = t % 10;
+    const int LA[10] = {1, 1, 1, 1, 2, 2, 2, 3, 3, 4}, LB[10] = {1, 2, 3, 4, 2, 3, 4, 3, 4, 4};
+    Density ra = divergence_density(j, LA[ll]), rb = basis_density(LB[ll]);
+    double2 acc = make_double2(0, 0);
+    for (int i = 0; i < ra.n; ++i) {
+        const double2 v = pair_integral(A, ra.f[i], rb.f[0], dd);
+        acc.x = fma(ra.coef[i], v.x, acc.x);
+        acc.y = fma(ra.coef[i], v.y, acc.y);
+    }
+    const double dV = A.g.d[0] * A.g.d[1] * A.g.d[2];
+    const double f = dV * dV / A.g.d[j];
+    A.out[(long long)t * nd + di] = make_double2(f * acc.x, f * acc.y);
+}
+
 // Circulant embedding of tensors [t0, t0 + nt) into [nt][Lz][Ly][Lx].
 __global__ void embed_kernel(const double2* __restrict__ T, int nx, int ny, int nz, int Lx, int Ly, int Lz, int t0,
                              int nt, double2* __restrict__ C) {
@@ -622,4 +647,47 @@ int green_setup(vie_handle* h) {
     h->toeplitz = T;
     h->bytes_held += sizeof(double2) * 60 * nd;
     return VIE_OK;
+}
+
+// The 30 Toeplitz tensors of the K operator into out [30][nz][ny][nx] (device), from the same
+// cell moments as green_setup (computed again here; the handle keeps none of them).
+int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s) {
+    GreenGeo g;
+    g.nx = h->nx, g.ny = h->ny, g.nz = h->nz;
+    g.d[0] = h->dx, g.d[1] = h->dy, g.d[2] = h->dz;
+    g.k0 = h->k0;
+    const long long n3 = (long long)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
+    size_t n2[3];
+    const int n[3] = {h->nx, h->ny, h->nz};
+    for (int ax = 0; ax < 3; ++ax) {
+        int j = ax == 0 ? 1 : 0, k = ax == 2 ? 1 : 2;
+        n2[ax] = (size_t)(n[ax] + 2) * (n[j] + 1) * (n[k] + 1);
+    }
+    const long long nd = (long long)h->nx * h->ny * h->nz;
+    double2 *mu3 = nullptr, *mu2[3] = {nullptr, nullptr, nullptr};
+    auto done = [&](int code) {
+        cudaFree(mu3);
+        for (int ax = 0; ax < 3; ++ax) cudaFree(mu2[ax]);
+        return code;
+    };
+    if (cudaMalloc(&mu3, sizeof(double2) * 64 * n3) != cudaSuccess) return done((set_error("moments alloc"), VIE_ENOMEM));
+    for (int ax = 0; ax < 3; ++ax)
+        if (cudaMalloc(&mu2[ax], sizeof(double2) * 16 * n2[ax]) != cudaSuccess)
+            return done((set_error("face moments alloc"), VIE_ENOMEM));
+    const long long th = n3 * 4;
+    VIE_KLAUNCH("moments3", s, moments3_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(g, mu3));
+    for (int ax = 0; ax < 3; ++ax) {
+        const long long th2 = (long long)n2[ax] * 4;
+        VIE_KLAUNCH("moments2", s, moments2_kernel<<<(unsigned)((th2 + 127) / 128), 128, 0, s>>>(g, ax, mu2[ax]));
+    }
+    GreenArgs A;
+    A.g = g;
+    A.mu3 = mu3;
+    for (int ax = 0; ax < 3; ++ax) A.mu2[ax] = mu2[ax];
+    A.out = out;
+    const long long tha = nd * 30;
+    VIE_KLAUNCH("assemble_k", s, assemble_k_kernel<<<(unsigned)((tha + 127) / 128), 128, 0, s>>>(A));
+    if (cudaGetLastError() != cudaSuccess) return done((set_error("K tensor kernels launch"), VIE_EDEVICE));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return done((set_error("K tensor sync"), VIE_EDEVICE));
+    return done(VIE_OK);
 }

@@ -79,6 +79,28 @@ def test_green_toeplitz_parity(vie, shape, delta):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("shape,delta", [((5, 4, 6), (0.004, 0.005, 0.0045)), ((8, 8, 8), (0.003, 0.003, 0.003))])
+def test_green_toeplitz_k_parity(vie, shape, delta):
+    """The 30 Toeplitz tensors of the K operator computed on the GPU vs the oracle's K entries at
+    every d >= 0: P_{10 j + ll}(d) = -eps_pjq K^{(p,la),(q,lb)}(d) for (p, j, q) a permutation."""
+    g = Grid(*shape, *delta)
+    freq = 298e6
+    h = setup(vie, g, freq, np.ones(g.shape), np.zeros(g.shape))
+    out = np.zeros((30,) + g.shape, dtype=np.complex128)
+    vie.vie_green_toeplitz_k(h, out)
+    h.close()
+    dz, dy, dx = np.meshgrid(np.arange(g.nz), np.arange(g.ny), np.arange(g.nx), indexing="ij")
+    D = np.stack([dx.ravel(), dy.ravel(), dz.ravel()], 1)
+    T = OG.k_entries(delta, O.k0_of(freq), D)
+    ref = np.zeros((30, D.shape[0]), dtype=complex)
+    for j in range(3):
+        p, q = (j + 1) % 3, (j + 2) % 3  # eps_{p j q} = -1 for this cyclic choice
+        for lli, (la, lb) in enumerate(LL):
+            ref[10 * j + lli] = T[4 * p + la - 1, 4 * q + lb - 1]  # -eps_pjq K = +K
+    got = out.reshape(30, -1)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 # (12, 5, 6) has Lx != Ly (line transforms along x and y), (5, 6, 70) has Lz = 256 and
 # (3, 2, 130) Lz = 512 (the FP32 z pass with 2-column tiles)
 # FFT lengths (Lx, Ly, Lz): (8, 8, 8), (16, 16, 32), (32, 32, 16), (32, 32, 32), (32, 16, 16), (16, 16, 256),
