@@ -7,6 +7,9 @@
 
 #include "common.cuh"
 
+// green.cu: the 30 Toeplitz tensors of the K operator into device memory
+int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);
+
 namespace {
 thread_local std::string g_last_error;
 

@@ -205,7 +205,6 @@ int solve_device_bytes(double out[3], bool reset);
 // Entry points between translation units
 // ---------------------------------------------------------------------------
 int green_setup(vie_handle* h);                 // green.cu
-int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);  // green.cu: K operator tensors
 int twiddle_setup(vie_handle* h);               // matvec.cu
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);
