@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "kblock.h"
 
 // ---------------------------------------------------------------------------
 // Gauss-Legendre rules on [0, 1], computed on the host by Newton iteration on
@@ -466,6 +467,8 @@ __global__ void assemble_kernel(GreenArgs A) {
     val.y -= fq * qs.y;
     A.out[(long long)t * nd + di] = val;
 }
+
+static_assert(kblock::table_complete(), "K block table: 30 tensors, 96 non-zero entries");
 
 // K operator (K u = curl S u): P_t(d) = (dV^2 / Delta_j) int int (D_j N^la) g N^lb for
 // t = 10 j + ll(la, lb), la <= lb, d in [0, N)^3; thread per (d, t).  D_j N^la is the
