@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libvie.so")
 
 VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_EDEVICE, VIE_ETIMEOUT, VIE_NOT_CONVERGED = 0, -1, -2, -3, -4, 1
 VIE_FP64, VIE_FP32 = 0, 1
-VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT = 0, 1, 2
+VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT, VIE_OP_K = 0, 1, 2, 3
 VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
 
 EXPORTS = (

@@ -9,6 +9,9 @@
 
 // green.cu: the 30 Toeplitz tensors of the K operator into device memory
 int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);
+// kmatvec.cu: y = K x (FP64) and the release of a handle's K spectrum
+int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s);
+void kmatvec_release(const vie_handle* h);
 
 namespace {
 thread_local std::string g_last_error;
@@ -87,6 +90,7 @@ struct Stager {
 
 void release(vie_handle* h) {
     if (!h) return;
+    kmatvec_release(h);
     cudaFree(h->eps64);
     cudaFree(h->chi64);
     cudaFree(h->tau64);
@@ -304,7 +308,8 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
     REQUIRE(h && x && y, "NULL argument");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     REQUIRE(precision == VIE_FP64 || precision == VIE_FP32, "unknown precision");
-    REQUIRE(op == VIE_OP_A || op == VIE_OP_PA || op == VIE_OP_NSCAT, "unknown operator");
+    REQUIRE(op == VIE_OP_A || op == VIE_OP_PA || op == VIE_OP_NSCAT || op == VIE_OP_K, "unknown operator");
+    REQUIRE(op != VIE_OP_K || precision == VIE_FP64, "the K operator is FP64 only");
     REQUIRE(x != y, "x and y must not overlap");
     const size_t bytes = (size_t)nrhs * 12 * h->nv * (precision == VIE_FP64 ? sizeof(double2) : sizeof(float2));
     cudaStream_t st = pick(h, stream);
@@ -313,7 +318,10 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
     sg.add(y, bytes, true);
     std::vector<void*> d;
     VIE_TRY(sg.bind(d));
-    VIE_TRY(matvec_device(h, nrhs, d[0], d[1], precision, op, st));
+    if (op == VIE_OP_K)
+        VIE_TRY(kmatvec_device(h, nrhs, static_cast<const double2*>(d[0]), static_cast<double2*>(d[1]), st));
+    else
+        VIE_TRY(matvec_device(h, nrhs, d[0], d[1], precision, op, st));
     return sg.finish(d);
 }
 

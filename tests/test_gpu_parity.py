@@ -101,6 +101,23 @@ def test_green_toeplitz_k_parity(vie, shape, delta):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("shape,nrhs", [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 5, 6), 2)])
+def test_k_matvec_parity(vie, shape, nrhs):
+    """y = K x (VIE_OP_K, FP64) vs the oracle's K operator (its own K tensors, circulant + FFT)."""
+    g = Grid(*shape, 0.004, 0.005, 0.0045)
+    eps, sig = random_tissue(g, seed=sum(shape) + 1)
+    freq = 298e6
+    h = setup(vie, g, freq, eps, sig)
+    x = random_coefficients(g, nrhs, seed=21 + nrhs)
+    y = gpu_matvec(vie, h, x, vie.VIE_FP64, vie.VIE_OP_K)
+    with pytest.raises(vie.VieError) as e:
+        gpu_matvec(vie, h, x, vie.VIE_FP32, vie.VIE_OP_K)
+    assert e.value.code == vie.VIE_EINVAL
+    h.close()
+    ref = O.KOperator(g, O.k0_of(freq)).apply(x)
+    assert rel(y, ref) <= 1e-12
+
+
 # (12, 5, 6) has Lx != Ly (line transforms along x and y), (5, 6, 70) has Lz = 256 and
 # (3, 2, 130) Lz = 512 (the FP32 z pass with 2-column tiles)
 # FFT lengths (Lx, Ly, Lz): (8, 8, 8), (16, 16, 32), (32, 32, 16), (32, 32, 32), (32, 16, 16), (16, 16, 256),
