@@ -242,6 +242,32 @@ int vie_green_toeplitz(vie_handle* h, void* out);
  */
 int vie_green_toeplitz_k(vie_handle* h, void* out);
 
+/*
+ * vie_rhs_dipoles_h -- tested incident magnetic fields of nrhs Hertzian dipoles, one per
+ * right-hand side: h_inc = curl (g p) = grad g x p (Eq. 8, g of Eq. 10, p = I l), tested
+ * with the 6x6x6 Gauss-Legendre rule per voxel of vie_rhs_dipoles.
+ *   pos, mom : double[nrhs][3] (m, A m), host memory
+ *   h_inc    : [nrhs][12][nz][ny][nx] C128 output (host or device)
+ * Synchronous.
+ */
+int vie_rhs_dipoles_h(vie_handle* h, int nrhs, const double* pos, const double* mom, void* h_inc, void* stream);
+
+/*
+ * vie_hfields -- magnetic post-processing (Eq. tot_fields: h_tot = h_inc + K j): tested field
+ * h~ = h_inc + K x (K in FP64 as vie_matvec VIE_OP_K), PWL coefficients h = G^-1 h~, the
+ * transmit field b1+ = mu0 (h_x + i h_y) of the voxel-average (l = 1) coefficients
+ * (Section V-D), and the magnetic energy W_m = 1/4 int mu0 |h|^2 over the scatterer
+ * (chi != 0; Section V-D, exact for the PWL field since the four functions of a voxel are
+ * orthogonal).
+ *   x, h_inc : [nrhs][12][nz][ny][nx] C128 (x: current coefficients of vie_solve)
+ *   h_coeff  : [nrhs][12][nz][ny][nx] C128 output or NULL
+ *   b1_plus  : [nrhs][nz][ny][nx] C128 output (T per unit source) or NULL
+ *   W_m      : double[nrhs] host output (J) or NULL
+ * Synchronous.
+ */
+int vie_hfields(vie_handle* h, int nrhs, const void* x, const void* h_inc, void* h_coeff, void* b1_plus, double* W_m,
+                void* stream);
+
 /* Sizes used by the handle: FFT lengths per axis and bytes of device memory held. */
 int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes);
 

@@ -24,7 +24,7 @@ VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
 
 EXPORTS = (
     "vie_setup", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
-    "vie_fields", "vie_green_toeplitz", "vie_green_toeplitz_k", "vie_info", "vie_strerror", "vie_last_error",
+    "vie_fields", "vie_green_toeplitz", "vie_green_toeplitz_k", "vie_rhs_dipoles_h", "vie_hfields", "vie_info", "vie_strerror", "vie_last_error",
     "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc",
     "vie_server_create", "vie_server_destroy", "vie_submit", "vie_poll", "vie_server_stats",
 )
@@ -98,6 +98,8 @@ def _lib():
     lib.vie_fields.argtypes = [P, I, P, P, P, P, ctypes.POINTER(D), P]
     lib.vie_green_toeplitz.argtypes = [P, P]
     lib.vie_green_toeplitz_k.argtypes = [P, P]
+    lib.vie_rhs_dipoles_h.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D), P, P]
+    lib.vie_hfields.argtypes = [P, I, P, P, P, P, ctypes.POINTER(D), P]
     lib.vie_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(S)]
     lib.vie_strerror.argtypes = [I]
     lib.vie_strerror.restype = ctypes.c_char_p
@@ -234,6 +236,26 @@ def vie_fields(h, x, e_inc, e_coeff=None, p_abs=None, stream=None):
     _check(_lib().vie_fields(h.ptr, n, _ptr(x), _ptr(e_inc), _ptr(e_coeff), _ptr(p_abs), P, _stream(stream)),
            "vie_fields")
     return list(P)
+
+
+def vie_rhs_dipoles_h(h, pos, mom, h_inc, stream=None):
+    """Tested incident magnetic fields of the dipoles into h_inc [R][12][nz][ny][nx] complex128."""
+    import numpy as np
+
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    mom = np.ascontiguousarray(mom, dtype=np.float64).reshape(-1, 3)
+    Dp = ctypes.POINTER(ctypes.c_double)
+    return _check(_lib().vie_rhs_dipoles_h(h.ptr, pos.shape[0], pos.ctypes.data_as(Dp), mom.ctypes.data_as(Dp),
+                                           _ptr(h_inc), _stream(stream)), "vie_rhs_dipoles_h")
+
+
+def vie_hfields(h, x, h_inc, h_coeff=None, b1_plus=None, stream=None):
+    """Magnetic field coefficients, b1+ and the magnetic energy; returns W_m (J) per right-hand side."""
+    n = _nrhs(x, h.nv)
+    W = (ctypes.c_double * n)()
+    _check(_lib().vie_hfields(h.ptr, n, _ptr(x), _ptr(h_inc), _ptr(h_coeff), _ptr(b1_plus), W, _stream(stream)),
+           "vie_hfields")
+    return list(W)
 
 
 def vie_green_toeplitz(h, out):

@@ -12,6 +12,10 @@ int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);
 // kmatvec.cu: y = K x (FP64) and the release of a handle's K spectrum
 int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s);
 void kmatvec_release(const vie_handle* h);
+// rhs_post.cu: tested incident magnetic field of dipoles; magnetic field, b1+ and W_m from x
+int rhs_dipoles_h_device(vie_handle* h, int R, const double* pos, const double* mom, double2* hinc, cudaStream_t s);
+int hfields_device(vie_handle* h, int R, const double2* x, const double2* hinc, double2* hout, double2* b1p,
+                   double* Wm_host, cudaStream_t s);
 
 namespace {
 thread_local std::string g_last_error;
@@ -408,6 +412,40 @@ int vie_green_toeplitz(vie_handle* h, void* out) {
     VIE_CUDA(cudaStreamSynchronize(h->stream));
     VIE_CUDA(cudaMemcpy(out, h->toeplitz, bytes, cudaMemcpyDefault));
     return VIE_OK;
+}
+
+int vie_rhs_dipoles_h(vie_handle* h, int nrhs, const double* pos, const double* mom, void* h_inc, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && pos && mom && h_inc, "NULL argument");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    for (int i = 0; i < 3 * nrhs; ++i) REQUIRE(std::isfinite(pos[i]) && std::isfinite(mom[i]), "non-finite source");
+    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(h_inc, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(rhs_dipoles_h_device(h, nrhs, pos, mom, static_cast<double2*>(d[0]), st));
+    return sg.finish(d);
+}
+
+int vie_hfields(vie_handle* h, int nrhs, const void* x, const void* h_inc, void* h_coeff, void* b1_plus, double* W_m,
+                void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && x && h_inc, "NULL argument");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(x, bytes, false);
+    sg.add(h_inc, bytes, false);
+    sg.add(h_coeff, bytes, true);
+    sg.add(b1_plus, (size_t)nrhs * h->nv * sizeof(double2), true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(hfields_device(h, nrhs, static_cast<const double2*>(d[0]), static_cast<const double2*>(d[1]),
+                           static_cast<double2*>(d[2]), static_cast<double2*>(d[3]), W_m, st));
+    return sg.finish(d);
 }
 
 int vie_green_toeplitz_k(vie_handle* h, void* out) {

@@ -268,6 +268,86 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk
     if (threadIdx.x == 0) out[rr] = sh[0];
 }
 
+// Tested incident magnetic field of R dipoles: h = curl (g p) = grad g x p (Eq. 8),
+// grad g = g (-1/R - i k0) R^, with the same 6 x 6 x 6 Gauss rule per voxel as dipole_kernel.
+__global__ void dipole_h_kernel(GridD g, double k0, int R, const double* __restrict__ pos,
+                                const double* __restrict__ mom, double2* __restrict__ hout) {
+    const long long nv = (long long)g.nx * g.ny * g.nz;
+    long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nv * R) return;
+    const long long m = gid % nv;
+    const int rr = (int)(gid / nv);
+    double rc[3];
+    centre(g, m, rc);
+    const double d[3] = {g.dx, g.dy, g.dz};
+    const double p[3] = {mom[3 * rr], mom[3 * rr + 1], mom[3 * rr + 2]};
+    double2 acc[12];
+    for (int i = 0; i < 12; ++i) acc[i] = make_double2(0, 0);
+    const double dV = g.dx * g.dy * g.dz;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j)
+            for (int k = 0; k < 6; ++k) {
+                const double s[3] = {c_g6x[i] - 0.5, c_g6x[j] - 0.5, c_g6x[k] - 0.5};
+                const double w = c_g6w[i] * c_g6w[j] * c_g6w[k] * dV;
+                double R3[3], Rn2 = 0;
+                for (int q = 0; q < 3; ++q) {
+                    R3[q] = rc[q] + d[q] * s[q] - pos[3 * rr + q];
+                    Rn2 += R3[q] * R3[q];
+                }
+                const double Rn = sqrt(Rn2);
+                double sn, cs;
+                sincos(k0 * Rn, &sn, &cs);
+                const double2 gg = make_double2(cs / (4.0 * VIE_PI * Rn), -sn / (4.0 * VIE_PI * Rn));
+                const double2 f = cmuld(gg, make_double2(-1.0 / Rn, -k0));  // dg/dR
+                double2 gr[3];
+                for (int q = 0; q < 3; ++q) gr[q] = make_double2(f.x * R3[q] / Rn, f.y * R3[q] / Rn);
+                for (int q = 0; q < 3; ++q) {
+                    const int q1 = (q + 1) % 3, q2 = (q + 2) % 3;  // (grad g x p)_q
+                    const double2 Hq = make_double2(gr[q1].x * p[q2] - gr[q2].x * p[q1],
+                                                    gr[q1].y * p[q2] - gr[q2].y * p[q1]);
+                    acc[4 * q].x += w * Hq.x;
+                    acc[4 * q].y += w * Hq.y;
+                    for (int l = 1; l < 4; ++l) {
+                        acc[4 * q + l].x += w * s[l - 1] * Hq.x;
+                        acc[4 * q + l].y += w * s[l - 1] * Hq.y;
+                    }
+                }
+            }
+    for (int a = 0; a < 12; ++a) hout[((long long)rr * 12 + a) * nv + m] = acc[a];
+}
+
+// h = (h_inc + K x) / G; b1+ = mu0 (h_(x,1) + i h_(y,1)); per-block sums of the magnetic energy
+// 1/4 mu0 sum_a G_a |h_a|^2 over the scatterer's voxels (chi != 0)
+__global__ void hfields_kernel(long long nv, const double2* __restrict__ hinc, const double2* __restrict__ kx,
+                               const double2* __restrict__ chi, double g1, double g234, double mu0, double2* hout,
+                               double2* b1p, double* partial) {
+    __shared__ double sh[256];
+    const int rr = blockIdx.y;
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double wm = 0.0;
+    if (m < nv) {
+        double2 h[12];
+        double q = 0.0;
+        for (int a = 0; a < 12; ++a) {
+            const long long o = ((long long)rr * 12 + a) * nv + m;
+            const double G = (a % 4 == 0) ? g1 : g234;
+            h[a] = make_double2((hinc[o].x + kx[o].x) / G, (hinc[o].y + kx[o].y) / G);
+            q += G * (h[a].x * h[a].x + h[a].y * h[a].y);
+            if (hout) hout[o] = h[a];
+        }
+        if (b1p) b1p[(long long)rr * nv + m] = make_double2(mu0 * (h[0].x - h[4].y), mu0 * (h[0].y + h[4].x));
+        const double2 c = chi[m];
+        if (c.x != 0.0 || c.y != 0.0) wm = 0.25 * mu0 * q;
+    }
+    sh[threadIdx.x] = wm;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(long long)rr * gridDim.x + blockIdx.x] = sh[0];
+}
+
 GridD gridd(const vie_handle* h) { return GridD{h->nx, h->ny, h->nz, h->dx, h->dy, h->dz}; }
 
 int ensure_rule6() {
@@ -394,5 +474,60 @@ int fields_device(vie_handle* h, int R, const double2* x, const double2* e_inc, 
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = VIE_EDEVICE;
     if (rc != VIE_OK) set_error("fields kernels failed");
+    return rc;
+}
+
+int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s);  // kmatvec.cu
+
+int rhs_dipoles_h_device(vie_handle* h, int R, const double* pos, const double* mom, double2* hinc, cudaStream_t s) {
+    VIE_TRY(ensure_rule6());
+    const long long nv = (long long)h->nv;
+    double* dbuf = nullptr;
+    VIE_CUDA(cudaMalloc(&dbuf, sizeof(double) * 6 * R));
+    cudaMemcpyAsync(dbuf, pos, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dbuf + 3 * R, mom, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s);
+    const long long th = nv * R;
+    VIE_KLAUNCH("dipole_h", s, dipole_h_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(gridd(h), h->k0, R, dbuf,
+                                                                                       dbuf + 3 * R, hinc));
+    cudaError_t err = cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(dbuf);
+    if (err != cudaSuccess) {
+        set_error(std::string("dipole h kernel: ") + cudaGetErrorString(err));
+        return VIE_EDEVICE;
+    }
+    return VIE_OK;
+}
+
+// magnetic field from the current coefficients (Eq. tot_fields: h = h_inc + K j), b1+ and W_m
+int hfields_device(vie_handle* h, int R, const double2* x, const double2* hinc, double2* hout, double2* b1p,
+                   double* Wm_host, cudaStream_t s) {
+    const long long nv = (long long)h->nv;
+    const int nblk = (int)((nv + 255) / 256);
+    double2* kx = nullptr;
+    double* part = nullptr;
+    if (cudaMalloc(&kx, sizeof(double2) * 12 * R * nv) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(double) * ((size_t)nblk * R + R)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(kx);
+        set_error("magnetic field scratch allocation failed");
+        return VIE_ENOMEM;
+    }
+    double* tot = part + (size_t)nblk * R;
+    int rc = kmatvec_device(h, R, x, kx, s);
+    if (rc == VIE_OK) {
+        const double mu0 = 1.0 / (VIE_EPS0 * VIE_C0 * VIE_C0);
+        const double dV = h->dx * h->dy * h->dz;
+        VIE_KLAUNCH("hfields", s, hfields_kernel<<<dim3(nblk, R), 256, 0, s>>>(nv, hinc, kx, h->chi64, dV, dV / 12.0, mu0,
+                                                                               hout, b1p, part));
+        VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<R, 256, 0, s>>>(part, nblk, tot));
+        if (cudaGetLastError() != cudaSuccess) rc = (set_error("magnetic field kernels"), VIE_EDEVICE);
+    }
+    if (rc == VIE_OK && Wm_host &&
+        cudaMemcpyAsync(Wm_host, tot, sizeof(double) * R, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = (set_error("magnetic energy copy"), VIE_EDEVICE);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == VIE_OK) rc = (set_error("magnetic field sync"), VIE_EDEVICE);
+    cudaFree(kx);
+    cudaFree(part);
     return rc;
 }

@@ -118,6 +118,32 @@ def test_k_matvec_parity(vie, shape, nrhs):
     assert rel(y, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("shape", [(6, 5, 4), (9, 7, 6)])
+def test_magnetic_post_parity(vie, shape):
+    """Tested dipole h_inc, the magnetic field coefficients h = (h_inc + K x) / G, b1+ and W_m vs the
+    oracle's (Eq. tot_fields; Section V-D definitions)."""
+    g = Grid(*shape, 0.006, 0.005, 0.007)
+    eps, sig = random_tissue(g, seed=sum(shape) + 5, air_fraction=0.3)
+    freq = 298e6
+    prob = O.Problem(g, freq, eps, sig)
+    pos, mom = ring_dipoles(2, 0.05)
+    h = setup(vie, g, freq, eps, sig)
+    hinc = np.zeros((2, 12) + g.shape, dtype=complex)
+    vie.vie_rhs_dipoles_h(h, pos, mom, hinc)
+    x = random_coefficients(g, 2, seed=sum(shape))
+    hc = np.zeros((2, 12) + g.shape, dtype=complex)
+    b1 = np.zeros((2,) + g.shape, dtype=complex)
+    W = vie.vie_hfields(h, x, hinc, hc, b1)
+    h.close()
+    hinc_ref = OR.dipoles_tested_h(g, prob.k0, pos, mom)
+    assert rel(hinc, hinc_ref) <= 1e-12
+    hc_ref = OP.magnetic_fields(prob, O.KOperator(g, prob.k0), x, hinc_ref)
+    assert rel(hc, hc_ref) <= 1e-12
+    assert rel(b1, OP.b1_plus(hc_ref)) <= 1e-12
+    _, W_ref = OP.magnetic_energy(prob, hc_ref)
+    assert np.max(np.abs(np.asarray(W) - W_ref) / np.abs(W_ref)) <= 1e-12
+
+
 # (12, 5, 6) has Lx != Ly (line transforms along x and y), (5, 6, 70) has Lz = 256 and
 # (3, 2, 130) Lz = 512 (the FP32 z pass with 2-column tiles)
 # FFT lengths (Lx, Ly, Lz): (8, 8, 8), (16, 16, 32), (32, 32, 16), (32, 32, 32), (32, 16, 16), (16, 16, 256),
