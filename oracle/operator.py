@@ -145,6 +145,25 @@ def apply_Pinv(prob: Problem, v):
     return v / (prob.eps * G)
 
 
+# PWC variant (the paper's comparison solver, Section V-A): one constant function per
+# component and voxel, f = N^1 p-hat, so its Galerkin system is exactly the l = 1 sub-block
+# of the PWL system (Eq. 19-22 with l = l' = 1: N entries, Gram G^1 = DV, P = M_eps G, b).
+PWC_COMPONENTS = (0, 4, 8)
+
+
+def pwc_mask():
+    """(12, 1, 1, 1) mask keeping the l = 1 components: the PWC unknowns inside the PWL layout."""
+    m = np.zeros((NCOMP, 1, 1, 1))
+    m[list(PWC_COMPONENTS)] = 1.0
+    return m
+
+
+def apply_PA_pwc(prob: Problem, Nop: NOperator, x):
+    """P^-1 A of the PWC system on vectors in the PWL layout: the l = 1 sub-block, zero elsewhere."""
+    m = pwc_mask()
+    return m * apply_PA(prob, Nop, m * x)
+
+
 def dense_N(grid, T):
     """Dense Galerkin matrix N (12 N_V x 12 N_V) from the Toeplitz values, entry (m alpha, n beta) = T^{alpha beta}(m - n)."""
     nz, ny, nx = grid.shape

@@ -172,9 +172,12 @@ def test_mie_positivity_and_lossless():
 
 @pytest.mark.slow
 def test_sphere_absorbed_power_vs_mie():
-    """Section V-A: PWL absorbed power of a homogeneous sphere vs the Mie series; a discretisation-error
-    pin (staircase sphere): a few per cent at 12.5 mm voxels and decreasing under refinement."""
-    errs = []
+    """Section V-A: absorbed power of a homogeneous sphere vs the Mie series, PWL and PWC.
+    PWL: a discretisation-error pin (staircase sphere), a few per cent at 12.5 mm voxels and
+    decreasing under refinement.  PWC (the l = 1 sub-block): several times the PWL error, the
+    factor growing under refinement (the paper finds about 12 at 5 mm and finer)."""
+    Pm = mie.absorbed_power(50.0, 0.5, 0.1, 298e6)
+    errs, errs_pwc = [], []
     for n in (16, 20):
         h = 0.2 / n
         g = Grid(n, n, n, h, h, h)
@@ -185,8 +188,17 @@ def test_sphere_absorbed_power_vs_mie():
         x, info = S.gmres(lambda v: O.apply_PA(prob, Nop, v), O.apply_Pinv(prob, b), tol=1e-6, restart=50, maxit=20)
         assert info["converged"]
         _, Pabs = P.absorbed_power(prob, x)
-        errs.append(abs(Pabs - mie.absorbed_power(50.0, 0.5, 0.1, 298e6)) / mie.absorbed_power(50.0, 0.5, 0.1, 298e6))
+        errs.append(abs(Pabs - Pm) / Pm)
+        m = O.pwc_mask()
+        xc, info = S.gmres(lambda v: O.apply_PA_pwc(prob, Nop, v), m * O.apply_Pinv(prob, b), tol=1e-6, restart=50,
+                           maxit=20)
+        assert info["converged"]
+        assert np.all(xc * (1 - m) == 0)  # the iteration stays in the PWC unknowns
+        _, Pabs_c = P.absorbed_power(prob, xc)
+        errs_pwc.append(abs(Pabs_c - Pm) / Pm)
     assert errs[0] < 0.15 and errs[1] < errs[0]
+    ratios = [c / l for c, l in zip(errs_pwc, errs)]
+    assert ratios[0] > 2.5 and ratios[1] > ratios[0]
 
 
 def test_planewave_voxel_integrals_vs_mpmath():
