@@ -14,11 +14,27 @@ Toeplitz defining tensors (Eq. 43) into 2N circulant tensors and using the FFT
 from __future__ import annotations
 
 import dataclasses
+import os
 
 import numpy as np
+import scipy.fft
+
 
 from . import C0, EPS0
 from .green import NCOMP, gram, k_toeplitz_tensors, toeplitz_tensors
+
+
+# The FFT steps go through scipy.fft with one worker thread per core this process may run
+# on; the transform is the plain DFT of Section IV-A either way.
+FFT_WORKERS = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def _fftn(a):
+    return scipy.fft.fftn(a, axes=(-3, -2, -1), workers=FFT_WORKERS)
+
+
+def _ifftn(a):
+    return scipy.fft.ifftn(a, axes=(-3, -2, -1), workers=FFT_WORKERS)
 
 
 def k0_of(freq):
@@ -97,16 +113,16 @@ class NOperator:
         if T is None:
             T = toeplitz_tensors(grid, k0)
         self.T = T
-        self.Chat = np.fft.fftn(circulant(T, self.shape), axes=(-3, -2, -1))
+        self.Chat = _fftn(circulant(T, self.shape))
 
     def apply(self, x):
         """x: (..., 12, Nz, Ny, Nx) complex -> N x of the same shape."""
         nz, ny, nx = self.shape
         pad = np.zeros(x.shape[:-3] + (2 * nz, 2 * ny, 2 * nx), dtype=complex)
         pad[..., :nz, :ny, :nx] = x
-        X = np.fft.fftn(pad, axes=(-3, -2, -1))
+        X = _fftn(pad)
         Y = _block_apply(self.Chat, X)
-        y = np.fft.ifftn(Y, axes=(-3, -2, -1))
+        y = _ifftn(Y)
         return y[..., :nz, :ny, :nx]
 
 
