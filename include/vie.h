@@ -54,7 +54,7 @@ extern "C" {
 #define VIE_OP_A 0      /* y = A x = M_eps G x - M_chi N x                     (Eq. 24) */
 #define VIE_OP_PA 1     /* y = P^-1 A x, P = M_eps G: x/eps - tau G^-1 (N - G) x (Section IV-B, Eq. 17) */
 #define VIE_OP_NSCAT 2  /* y = (N - G) x, the Galerkin "N - I" operator (tested scattered field * c_e) */
-#define VIE_OP_K 3      /* y = K x, K u = curl S u (Eq. 8): the tested scattered magnetic field (Eq. tot_fields); FP64 only */
+#define VIE_OP_K 3      /* y = K x, K u = curl S u (Eq. 8): the tested scattered magnetic field (Eq. 13); FP64 only */
 
 /* Solver modes of vie_solve. */
 #define VIE_SOLVE_FP64 0         /* plain FP64 GMRES */
@@ -94,6 +94,25 @@ typedef struct {
 int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma, int flags,
               vie_handle** out);
 
+/*
+ * vie_setup_green_external -- vie_setup with the Galerkin entries of N supplied by the
+ * caller instead of computed on the GPU: a test hook that checks the matvec apart from the
+ * Green-tensor setup.  Everything else (circulant embedding and FFT of Section IV-A, octant
+ * storage in FP64 and FP32, material maps) is as in vie_setup.
+ *   grid, freq_hz, eps_real, sigma : as for vie_setup
+ *   toeplitz_fp64 : complex128 [144][2nz-1][2ny-1][2nx-1], host or device, read during the
+ *                   call only: entry alpha * 12 + beta holds N^{alpha beta}(d) (Eq. 25, Eq. 42-43,
+ *                   the Gram term G^l of Eq. 33 included at d = 0 on the diagonal) for the voxel
+ *                   offset d = m - n, stored at index d + N - 1 per axis.  Only the 60 entries
+ *                   (alpha, beta) = (4p + l - 1, 4q + l' - 1) with p <= q and l <= l' at offsets
+ *                   d >= 0 are read; the others must follow from them by reciprocity and the
+ *                   reflection parities (Section III-C), as the exact entries do.
+ * The K tensors (VIE_OP_K, vie_green_toeplitz_k) are still computed on the GPU.
+ * Synchronous.  Errors as for vie_setup; VIE_EINVAL for a NULL table.
+ */
+int vie_setup_green_external(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
+                             const void* toeplitz_fp64, vie_handle** out);
+
 /* Release every device buffer of the handle.  NULL is ignored. */
 void vie_destroy(vie_handle* h);
 
@@ -122,13 +141,18 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
  * scratch (the spectrum buffers) is one static device array of 64 MiB
  * compiled into the library, which every GPU that loads the library holds
- * until the process exits.  A call that would need more scratch
- * (roughly nrhs * 12 * nz * L_y * L_x complex values, plus nrhs * 12 * nz *
- * ny * L_x on the FP64 path) returns VIE_EINVAL without doing anything: use
- * fewer right-hand sides per call, or vie_matvec.
- *   h, nrhs, precision, op : as for vie_matvec
- *   x, y                   : device memory only (host buffers would need
- *                            staging memory); VIE_EINVAL otherwise
+ * until the process exits.  A call needs nrhs * 12 * nz * L_y * L_x complex
+ * values of the precision (8 or 16 bytes each) plus 256 bytes, where L_i is
+ * the FFT length of vie_info; grids whose xy circulant is not square or is
+ * longer than 128 take the line-transform path, which needs nrhs * 12 * nz *
+ * ny * L_x more.  A call that needs more than the array returns VIE_EINVAL
+ * without doing anything: use fewer right-hand sides per call, or vie_matvec.
+ *   h, nrhs, precision     : as for vie_matvec
+ *   op                     : VIE_OP_A, VIE_OP_PA or VIE_OP_NSCAT (not VIE_OP_K,
+ *                            whose spectra are held by the handle)
+ *   x, y                   : device memory of the handle's device only (host
+ *                            buffers would need staging memory); VIE_EINVAL
+ *                            otherwise
  *   stream                 : cudaStream_t as void*, NULL = the handle's stream
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
@@ -253,7 +277,7 @@ int vie_green_toeplitz_k(vie_handle* h, void* out);
 int vie_rhs_dipoles_h(vie_handle* h, int nrhs, const double* pos, const double* mom, void* h_inc, void* stream);
 
 /*
- * vie_hfields -- magnetic post-processing (Eq. tot_fields: h_tot = h_inc + K j): tested field
+ * vie_hfields -- magnetic post-processing (Section II total fields: h_tot = h_inc + K j): tested field
  * h~ = h_inc + K x (K in FP64 as vie_matvec VIE_OP_K), PWL coefficients h = G^-1 h~, the
  * transmit field b1+ = mu0 (h_x + i h_y) of the voxel-average (l = 1) coefficients
  * (Section V-D), and the magnetic energy W_m = 1/4 int mu0 |h|^2 over the scatterer
@@ -350,6 +374,20 @@ int vie_submit(vie_server* s, const vie_request* req, unsigned long long* ticket
 int vie_poll(vie_server* s, unsigned long long ticket, int timeout_us, vie_result* out);
 /* Snapshot: queued requests, requests running, device bytes reserved, cached Green keys. */
 int vie_server_stats(vie_server* s, int* queued, int* running, size_t* bytes_in_use, int* cache_entries);
+
+/*
+ * Host-side fault injection for tests of the failure paths (no counterpart in the paper).
+ * Nothing here touches the GPU: an injected failure is returned by the host code at the point
+ * where the real one would be detected, and the handle stays usable.
+ *   VIE_INJECT_OOM  : the next `count` growths of a handle's device workspace (matvec spectra,
+ *                     solver vectors, staging, post-processing scratch) fail with VIE_ENOMEM
+ *                     before allocating
+ *   VIE_INJECT_NONE : clear every pending injection (count ignored)
+ * Process-wide.  VIE_EINVAL for an unknown kind or count < 0.
+ */
+#define VIE_INJECT_NONE 0
+#define VIE_INJECT_OOM 1
+int vie_fault_inject(int kind, int count);
 
 /* Static description of an error code. */
 const char* vie_strerror(int code);

@@ -421,7 +421,7 @@ def q_entries(delta, k0, D, mom=None):
 
 
 # ---------------------------------------------------------------------------
-# K operator (Eq. 8: K u = curl S u), for the magnetic field h = h_inc + K j (tot_fields)
+# K operator (Eq. 8: K u = curl S u), for the magnetic field h = h_inc + K j (Section II total fields)
 # ---------------------------------------------------------------------------
 
 LEVI_CIVITA = np.zeros((3, 3, 3))

@@ -1,7 +1,7 @@
 """Fields, absorbed power and magnetic quantities from the solution (oracle; test infrastructure only).
 
 Section IV-C: the tested total field follows from the discrete analogue of
-e_tot = e_inc + (1/c_e)(N - I) j (Eq. tot_fields),
+e_tot = e_inc + (1/c_e)(N - I) j (Section II, total fields),
 
     e~ = e_inc_tested + (1/c_e) (N x - G x),
 
@@ -10,7 +10,7 @@ Absorbed power (Eq. 44):  P_abs = 1/2 Re{ x^* (c_e M_chi)^-1 G x },  split per
 voxel into the absorbed-power density p_abs(m) = (1/2 Re{...}_m) / DV (W/m^3),
 zero in air (chi = 0).
 
-Magnetic field (Eq. tot_fields, h_tot = h_inc + K j): the tested field is
+Magnetic field (Section II total fields, h_tot = h_inc + K j): the tested field is
 h~ = h_inc_tested + K x and its PWL coefficients h~ / G.  The transmit field
 b1+ = mu0 (h_x + i h_y) (Section V-D) is taken from the voxel-average (l = 1)
 coefficients, and the magnetic energy W_m = 1/4 int mu |h|^2 dV (Section V-D,

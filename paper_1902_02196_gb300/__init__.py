@@ -21,11 +21,12 @@ VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_EDEVICE, VIE_ETIMEOUT, VIE_NOT_CONVERGED = 0
 VIE_FP64, VIE_FP32 = 0, 1
 VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT, VIE_OP_K = 0, 1, 2, 3
 VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
+VIE_INJECT_NONE, VIE_INJECT_OOM = 0, 1
 
 EXPORTS = (
-    "vie_setup", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
+    "vie_setup", "vie_setup_green_external", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
     "vie_fields", "vie_green_toeplitz", "vie_green_toeplitz_k", "vie_rhs_dipoles_h", "vie_hfields", "vie_info", "vie_strerror", "vie_last_error",
-    "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc",
+    "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc", "vie_fault_inject",
     "vie_server_create", "vie_server_destroy", "vie_submit", "vie_poll", "vie_server_stats",
 )
 
@@ -88,6 +89,7 @@ def _lib():
     lib = ctypes.CDLL(LIB_PATH)
     P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     lib.vie_setup.argtypes = [ctypes.POINTER(vie_grid), D, P, P, I, ctypes.POINTER(P)]
+    lib.vie_setup_green_external.argtypes = [ctypes.POINTER(vie_grid), D, P, P, P, ctypes.POINTER(P)]
     lib.vie_destroy.argtypes = [P]
     lib.vie_destroy.restype = None
     lib.vie_matvec.argtypes = [P, I, P, P, I, I, P]
@@ -105,6 +107,7 @@ def _lib():
     lib.vie_strerror.restype = ctypes.c_char_p
     lib.vie_stats_reset.argtypes = [I]
     lib.vie_stats_read.argtypes = [I, P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]
+    lib.vie_fault_inject.argtypes = [I, I]
     lib.vie_last_error.argtypes = []
     lib.vie_last_error.restype = ctypes.c_char_p
     lib.vie_server_create.argtypes = [S, I, ctypes.POINTER(P)]
@@ -182,6 +185,23 @@ def vie_setup(grid, freq_hz, eps_real, sigma, flags=0):
     out = ctypes.c_void_p()
     _check(lib.vie_setup(ctypes.byref(g), float(freq_hz), _ptr(eps_real), _ptr(sigma), int(flags), ctypes.byref(out)),
            "vie_setup")
+    return Handle(out.value, (g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), freq_hz)
+
+
+def vie_setup_green_external(grid, freq_hz, eps_real, sigma, toeplitz):
+    """vie_setup with the caller's Galerkin entries of N: toeplitz is complex128
+    [144][2nz-1][2ny-1][2nx-1] (entry alpha * 12 + beta, offset d at index d + N - 1), host or device."""
+    lib = _lib()
+    g = vie_grid(*[int(v) for v in grid[:3]], *[float(v) for v in grid[3:]])
+    shape = (2 * g.nz - 1, 2 * g.ny - 1, 2 * g.nx - 1)
+    n = 1
+    for d in toeplitz.shape:
+        n *= int(d)
+    if n != 144 * shape[0] * shape[1] * shape[2]:
+        raise ValueError("toeplitz must hold 144 x (2nz-1) x (2ny-1) x (2nx-1) complex values")
+    out = ctypes.c_void_p()
+    _check(lib.vie_setup_green_external(ctypes.byref(g), float(freq_hz), _ptr(eps_real), _ptr(sigma), _ptr(toeplitz),
+                                        ctypes.byref(out)), "vie_setup_green_external")
     return Handle(out.value, (g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), freq_hz)
 
 
@@ -272,6 +292,11 @@ def vie_info(h):
     nb = ctypes.c_size_t()
     _check(_lib().vie_info(h.ptr, L, ctypes.byref(nb)), "vie_info")
     return tuple(L), nb.value
+
+
+def vie_fault_inject(kind, count=1):
+    """Host-side fault injection (VIE_INJECT_OOM: the next `count` workspace growths fail)."""
+    return _check(_lib().vie_fault_inject(int(kind), int(count)), "vie_fault_inject")
 
 
 def vie_strerror(code):

@@ -1,4 +1,5 @@
 // C ABI entry points (include/vie.h): argument checks, host-buffer staging, handle lifetime.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -11,7 +12,7 @@
 int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);
 // kmatvec.cu: y = K x (FP64) and the release of a handle's K spectrum
 int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s);
-void kmatvec_release(const vie_handle* h);
+void kmatvec_release(vie_handle* h);
 // rhs_post.cu: tested incident magnetic field of dipoles; magnetic field, b1+ and W_m from x
 int rhs_dipoles_h_device(vie_handle* h, int R, const double* pos, const double* mom, double2* hinc, cudaStream_t s);
 int hfields_device(vie_handle* h, int R, const double2* x, const double2* hinc, double2* hout, double2* b1p,
@@ -135,8 +136,17 @@ void release(vie_handle* h) {
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+namespace {
+std::atomic<int> g_inject_oom{0};  // workspace allocations still to fail (vie_fault_inject)
+}
+
 int ws_reserve(vie_handle* h, Workspace& w, size_t bytes) {
     if (w.bytes >= bytes) return VIE_OK;
+    for (int n = g_inject_oom.load(); n > 0;)
+        if (g_inject_oom.compare_exchange_weak(n, n - 1)) {
+            set_error("injected allocation failure (vie_fault_inject) of " + std::to_string(bytes) + " bytes");
+            return VIE_ENOMEM;
+        }
     if (w.ptr) {
         VIE_CUDA(cudaFree(w.ptr));
         h->bytes_held -= w.bytes;
@@ -170,6 +180,16 @@ const char* vie_strerror(int code) {
 
 const char* vie_last_error(void) { return g_last_error.c_str(); }
 
+int vie_fault_inject(int kind, int count) {
+    REQUIRE(count >= 0, "count must be >= 0");
+    switch (kind) {
+        case VIE_INJECT_NONE: g_inject_oom = 0; return VIE_OK;
+        case VIE_INJECT_OOM: g_inject_oom = count; return VIE_OK;
+    }
+    set_error("unknown fault kind");
+    return VIE_EINVAL;
+}
+
 int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma, int flags,
               vie_handle** out) {
     g_last_error.clear();
@@ -177,6 +197,15 @@ int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, cons
     *out = nullptr;
     REQUIRE(flags == 0, "flags must be 0");
     return handle_create(grid, freq_hz, eps_real, sigma, nullptr, out);
+}
+
+int vie_setup_green_external(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
+                             const void* toeplitz_fp64, vie_handle** out) {
+    g_last_error.clear();
+    REQUIRE(out, "out is NULL");
+    *out = nullptr;
+    REQUIRE(toeplitz_fp64, "toeplitz_fp64 is NULL");
+    return handle_create(grid, freq_hz, eps_real, sigma, nullptr, out, toeplitz_fp64);
 }
 
 }  // extern "C"
@@ -188,7 +217,7 @@ size_t handle_green_bytes(const vie_handle* h) {
 }
 
 int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
-                  const vie_handle* share, vie_handle** out) {
+                  const vie_handle* share, vie_handle** out, const void* ext) {
     *out = nullptr;
     REQUIRE(grid && eps_real && sigma, "NULL argument");
     REQUIRE(grid->nx >= 1 && grid->ny >= 1 && grid->nz >= 1, "grid sizes must be >= 1");
@@ -286,7 +315,30 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
         return VIE_OK;
     }
     if ((rc = twiddle_setup(h)) < 0) return fail(rc);
-    if ((rc = green_setup(h)) < 0) return fail(rc);
+    if (ext) {
+        const size_t ebytes = sizeof(double2) * 144 * (size_t)(2 * h->nx - 1) * (2 * h->ny - 1) * (2 * h->nz - 1);
+        const void* dext = ext;
+        void* tmp = nullptr;
+        if (!is_device_ptr(ext)) {
+            if (cudaMalloc(&tmp, ebytes) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("staging of the external Toeplitz table failed");
+                return fail(VIE_ENOMEM);
+            }
+            if (cudaMemcpy(tmp, ext, ebytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaFree(tmp);
+                set_error("cannot read the external Toeplitz table");
+                return fail(VIE_EINVAL);
+            }
+            dext = tmp;
+        }
+        rc = green_setup_external(h, static_cast<const double2*>(dext));
+        cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        if (rc < 0) return fail(rc);
+    } else if ((rc = green_setup(h)) < 0) {
+        return fail(rc);
+    }
     *out = h;
     return VIE_OK;
 }

@@ -146,8 +146,11 @@ struct vie_handle {
 // vie_setup with an optional template: when share != NULL the new handle takes the
 // template's Green tensors, twiddles and column map (same grid, voxel and frequency
 // required) and computes only its own material maps.
+// ext (optional, no template): the caller's Toeplitz table [144][2nz-1][2ny-1][2nx-1] complex128
+// (host or device) from which the Green tensors are taken instead of being computed
+// (vie_setup_green_external).
 int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
-                  const vie_handle* share, vie_handle** out);
+                  const vie_handle* share, vie_handle** out, const void* ext = nullptr);
 // device bytes held by a handle's Green tensors, twiddles and column map (shared part)
 size_t handle_green_bytes(const vie_handle* h);
 
@@ -205,6 +208,7 @@ int solve_device_bytes(double out[3], bool reset);
 // Entry points between translation units
 // ---------------------------------------------------------------------------
 int green_setup(vie_handle* h);                 // green.cu
+int green_setup_external(vie_handle* h, const double2* ext);  // green.cu, ext on the device
 int twiddle_setup(vie_handle* h);               // matvec.cu
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);

@@ -559,21 +559,26 @@ __global__ void octant_kernel(const double2* __restrict__ C, int Lx, int Ly, int
     g64t[tdst] = v;
 }
 
-int green_setup(vie_handle* h) {
-    // quadrature tables
-    {
-        double gx[128], gw[128];
-        int off[kNumRules];
-        int pos = 0;
-        for (int r = 0; r < kNumRules; ++r) {
-            off[r] = pos;
-            gauss_legendre01(kOrders[r], gx + pos, gw + pos);
-            pos += kOrders[r];
-        }
-        VIE_CUDA(cudaMemcpyToSymbol(c_gx, gx, sizeof(double) * pos));
-        VIE_CUDA(cudaMemcpyToSymbol(c_gw, gw, sizeof(double) * pos));
-        VIE_CUDA(cudaMemcpyToSymbol(c_goff, off, sizeof(off)));
+// Gauss-Legendre tables of the cell-moment kernels in constant memory (current device)
+static int quad_tables() {
+    double gx[128], gw[128];
+    int off[kNumRules];
+    int pos = 0;
+    for (int r = 0; r < kNumRules; ++r) {
+        off[r] = pos;
+        gauss_legendre01(kOrders[r], gx + pos, gw + pos);
+        pos += kOrders[r];
     }
+    VIE_CUDA(cudaMemcpyToSymbol(c_gx, gx, sizeof(double) * pos));
+    VIE_CUDA(cudaMemcpyToSymbol(c_gw, gw, sizeof(double) * pos));
+    VIE_CUDA(cudaMemcpyToSymbol(c_goff, off, sizeof(off)));
+    return VIE_OK;
+}
+
+int green_embed(vie_handle* h, double2* T);
+
+int green_setup(vie_handle* h) {
+    VIE_TRY(quad_tables());
     cudaStream_t s = h->stream;
     GreenGeo g;
     g.nx = h->nx, g.ny = h->ny, g.nz = h->nz;
@@ -587,13 +592,11 @@ int green_setup(vie_handle* h) {
         n2[ax] = (size_t)(n[ax] + 2) * (n[j] + 1) * (n[k] + 1);
     }
     const long long nd = (long long)h->nx * h->ny * h->nz;
-    double2 *mu3 = nullptr, *mu2[3] = {nullptr, nullptr, nullptr}, *T = nullptr, *C = nullptr;
-    int rc = VIE_OK;
+    double2 *mu3 = nullptr, *mu2[3] = {nullptr, nullptr, nullptr}, *T = nullptr;
     auto fail = [&](int code) {
         cudaFree(mu3);
         for (int ax = 0; ax < 3; ++ax) cudaFree(mu2[ax]);
         cudaFree(T);
-        cudaFree(C);
         return code;
     };
     if (cudaMalloc(&mu3, sizeof(double2) * 64 * n3) != cudaSuccess) return fail((set_error("moments alloc"), VIE_ENOMEM));
@@ -617,7 +620,24 @@ int green_setup(vie_handle* h) {
         VIE_KLAUNCH("assemble", s, assemble_kernel<<<(unsigned)((tha + 127) / 128), 128, 0, s>>>(A));
         if (cudaGetLastError() != cudaSuccess) return fail((set_error("green kernels launch"), VIE_EDEVICE));
     }
-    // keep the Toeplitz tensors for vie_green_toeplitz
+    cudaFree(mu3);
+    for (int ax = 0; ax < 3; ++ax) cudaFree(mu2[ax]);
+    return green_embed(h, T);  // takes T
+}
+
+// Circulant embedding, 3-D FFT and octant storage of the 60 Toeplitz tensors T [60][nz][ny][nx]
+// (device, N - G at offsets d >= 0) in FP64 and FP32 (Section IV-A); the handle keeps T for
+// vie_green_toeplitz (it takes ownership of T, also on failure).
+int green_embed(vie_handle* h, double2* T) {
+    cudaStream_t s = h->stream;
+    const long long nd = (long long)h->nx * h->ny * h->nz;
+    double2* C = nullptr;
+    auto fail = [&](int code) {
+        cudaFree(T);
+        cudaFree(C);
+        return code;
+    };
+    int rc = VIE_OK;
     const int Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
     const long long vol = (long long)Lx * Ly * Lz;
     const long long ovol = (long long)h->O[0] * h->O[1] * h->O[2];
@@ -643,13 +663,57 @@ int green_setup(vie_handle* h) {
         if (cudaGetLastError() != cudaSuccess) return fail((set_error("octant launch"), VIE_EDEVICE));
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail((set_error("green setup sync"), VIE_EDEVICE));
-    cudaFree(mu3);
-    for (int ax = 0; ax < 3; ++ax) cudaFree(mu2[ax]);
     cudaFree(C);
     // The Toeplitz table is kept for inspection (vie_green_toeplitz)
     h->toeplitz = T;
     h->bytes_held += sizeof(double2) * 60 * nd;
     return VIE_OK;
+}
+
+// T[t][d] = the representative entry (alpha, beta) of unique tensor t at offset d >= 0, taken
+// from a caller's full table E[144][2nz-1][2ny-1][2nx-1] (entry alpha * 12 + beta, offset d at
+// index d + N - 1 per axis), minus the Gram term G^l on the diagonal at d = 0 (the device keeps
+// N - G).
+__global__ void external_pick_kernel(const double2* __restrict__ E, int nx, int ny, int nz, double g1, double g234,
+                                     double2* __restrict__ T) {
+    const long long nd = (long long)nx * ny * nz;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 60 * nd) return;
+    const int t = (int)(gid / nd);
+    const long long d = gid % nd;
+    const int dx = (int)(d % nx), dy = (int)((d / nx) % ny), dz = (int)(d / ((long long)nx * ny));
+    const int pq = t / 10, ll = t % 10;
+    const int P[6] = {0, 0, 0, 1, 1, 2}, Q[6] = {0, 1, 2, 1, 2, 2};
+    const int LA[10] = {1, 1, 1, 1, 2, 2, 2, 3, 3, 4}, LB[10] = {1, 2, 3, 4, 2, 3, 4, 3, 4, 4};
+    const int alpha = 4 * P[pq] + LA[ll] - 1, beta = 4 * Q[pq] + LB[ll] - 1;
+    const long long ex = 2LL * nx - 1, ey = 2LL * ny - 1, ez = 2LL * nz - 1;
+    double2 v = E[(long long)(alpha * 12 + beta) * ex * ey * ez + ((dz + nz - 1) * ey + (dy + ny - 1)) * ex + dx + nx - 1];
+    if (d == 0 && alpha == beta) v.x -= LA[ll] == 1 ? g1 : g234;
+    T[gid] = v;
+}
+
+// Green tensors of a handle from a caller's Toeplitz table (vie_setup_green_external): `ext` is
+// device memory [144][2nz-1][2ny-1][2nx-1] complex128.
+int green_setup_external(vie_handle* h, const double2* ext) {
+    VIE_TRY(quad_tables());  // for the K tensors, which the device still computes
+    const long long nd = (long long)h->nx * h->ny * h->nz;
+    double2* T = nullptr;
+    if (cudaMalloc(&T, sizeof(double2) * 60 * nd) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("toeplitz alloc");
+        return VIE_ENOMEM;
+    }
+    const double dV = h->dx * h->dy * h->dz;
+    cudaStream_t s = h->stream;
+    VIE_KLAUNCH("green_external", s,
+                external_pick_kernel<<<(unsigned)((60 * nd + 255) / 256), 256, 0, s>>>(ext, h->nx, h->ny, h->nz, dV,
+                                                                                      dV / 12.0, T));
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaFree(T);
+        set_error("green_external launch");
+        return VIE_EDEVICE;
+    }
+    return green_embed(h, T);
 }
 
 // The 30 Toeplitz tensors of the K operator into out [30][nz][ny][nx] (device), from the same

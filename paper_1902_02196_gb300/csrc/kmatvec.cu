@@ -1,5 +1,6 @@
 // K operator matvec (K u = curl S u, Eq. 8), FP64: y = K x for nrhs vectors by circulant
-// embedding and 3-D FFTs (Section IV-A), the magnetic field's h~ = K x of Eq. tot_fields.
+// embedding and 3-D FFTs (Section IV-A), the tested scattered magnetic field h~ = K x
+// (Eq. 13: h_sca = K j).
 //
 // The 30 Toeplitz tensors P_t (green.cu, assemble_k_kernel) are embedded into full 2N
 // circulants, the entries at negative offsets taken from the reflection parities of the
@@ -8,6 +9,7 @@
 // applies the signed 12 x 12 K block at every frequency point, and transforms back as
 // conj(FFT(conj(.))) with the same forward transform; the 1/(Lx Ly Lz) of the inverse is
 // folded into the block product.  Correctness path: full spectra, no octant storage.
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
@@ -139,38 +141,54 @@ int kspectrum(vie_handle* h, cudaStream_t s, const double2** out) {
         return rc;
     }
     g_kspec[h] = C;
+    h->bytes_held += sizeof(double2) * 30 * (size_t)vol;  // counted until kmatvec_release
     *out = C;
     return VIE_OK;
 }
 
+// right-hand sides per pass of the K matvec: the padded spectra of a pass ([12 Rc][Lz][Ly][Lx]
+// FP64) stay within 4 GiB of scratch, one right-hand side at least
+constexpr size_t kKPassBytes = size_t(4) << 30;
+
 }  // namespace
 
-// y = K x, FP64, x and y device [R][12][nz][ny][nx]
+// y = K x, FP64, x and y device [R][12][nz][ny][nx]; the right-hand sides go through in passes
+// of at most kKPassBytes of padded spectra each
 int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s) {
     const double2* KS = nullptr;
     VIE_TRY(kspectrum(h, s, &KS));
     const int Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
-    const long long vol = (long long)Lx * Ly * Lz, planes = 12LL * R;
-    VIE_TRY(ws_reserve(h, h->post_ws, sizeof(double2) * (size_t)(vol * planes)));
+    const long long vol = (long long)Lx * Ly * Lz, nv = (long long)h->nv;
+    const size_t per_rhs = sizeof(double2) * 12 * (size_t)vol;
+    const int Rc = (int)std::max<size_t>(1, std::min<size_t>((size_t)R, kKPassBytes / per_rhs));
+    VIE_TRY(ws_reserve(h, h->post_ws, per_rhs * (size_t)Rc));
     double2* W = static_cast<double2*>(h->post_ws.ptr);
-    VIE_KLAUNCH("k_pad", s, pad_kernel<<<blocks(vol * planes), 256, 0, s>>>(x, h->nx, h->ny, h->nz, Lx, Ly, Lz, planes, W));
-    VIE_CHECK_LAUNCH();
-    VIE_TRY(fft3d_inplace64(h, W, (int)planes, s));
-    VIE_KLAUNCH("k_block", s, kblock_kernel<<<blocks(vol * R), 256, 0, s>>>(W, KS, vol, R, 1.0 / (double)vol));
-    VIE_CHECK_LAUNCH();
-    VIE_TRY(fft3d_inplace64(h, W, (int)planes, s));
-    VIE_KLAUNCH("k_crop", s,
-                crop_conj_kernel<<<blocks((long long)h->nv * planes), 256, 0, s>>>(W, h->nx, h->ny, h->nz, Lx, Ly, Lz,
-                                                                                     planes, y));
-    VIE_CHECK_LAUNCH();
+    for (int r0 = 0; r0 < R; r0 += Rc) {
+        const int Rp = std::min(Rc, R - r0);
+        const long long planes = 12LL * Rp;
+        const double2* xp = x + (long long)r0 * 12 * nv;
+        double2* yp = y + (long long)r0 * 12 * nv;
+        VIE_KLAUNCH("k_pad", s,
+                    pad_kernel<<<blocks(vol * planes), 256, 0, s>>>(xp, h->nx, h->ny, h->nz, Lx, Ly, Lz, planes, W));
+        VIE_CHECK_LAUNCH();
+        VIE_TRY(fft3d_inplace64(h, W, (int)planes, s));
+        VIE_KLAUNCH("k_block", s, kblock_kernel<<<blocks(vol * Rp), 256, 0, s>>>(W, KS, vol, Rp, 1.0 / (double)vol));
+        VIE_CHECK_LAUNCH();
+        VIE_TRY(fft3d_inplace64(h, W, (int)planes, s));
+        VIE_KLAUNCH("k_crop", s,
+                    crop_conj_kernel<<<blocks(nv * planes), 256, 0, s>>>(W, h->nx, h->ny, h->nz, Lx, Ly, Lz, planes,
+                                                                           yp));
+        VIE_CHECK_LAUNCH();
+    }
     return VIE_OK;
 }
 
 // frees the handle's K spectrum, if any (called when the handle is released)
-void kmatvec_release(const vie_handle* h) {
+void kmatvec_release(vie_handle* h) {
     std::lock_guard<std::mutex> lk(g_kmu);
     auto it = g_kspec.find(h);
     if (it == g_kspec.end()) return;
     cudaFree(it->second);
     g_kspec.erase(it);
+    h->bytes_held -= sizeof(double2) * 30 * (size_t)h->L[0] * h->L[1] * h->L[2];
 }

@@ -519,11 +519,13 @@ static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, l
     return VIE_EINVAL;
 }
 
+// Spectrum scratch of one matvec: W2 [R*12][Nz][Ly][Lx] on the fused xy path, W1
+// [R*12][Nz][Ny][Lx] in front of it on the line-transform path (the only one that uses W1).
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
     size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     size_t comps = (size_t)nrhs * 12 * h->nz;
     size_t w2 = comps * h->L[1] * h->L[0];
-    size_t w1 = comps * h->ny * h->L[0];
+    size_t w1 = xy_ok(h) ? 0 : comps * h->ny * h->L[0];
     return c * (w1 + w2) + 256;
 }
 
@@ -539,8 +541,9 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     if (!xy_ok(h) || nact <= 0 || nact >= R) rmap = nullptr;
     const int Rs = rmap ? nact : R;  // right-hand sides in the spectrum
     const long long comps = (long long)Rs * 12 * nz;
+    // W1 exists on the line-transform path only (matvec_workspace_bytes)
     C* W1 = reinterpret_cast<C*>(ws);
-    C* W2 = W1 + comps * ny * Lx;
+    C* W2 = xy_ok(h) ? W1 : W1 + comps * ny * Lx;
     MatvecEpi e{};
     e.x = x;
     e.op = op;
@@ -909,13 +912,15 @@ int noalloc_scratch(void** out) {
     return VIE_OK;
 }
 
-bool on_device(const void* p) {
+// p is device memory of `device` (or managed memory)
+bool on_device(const void* p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 }  // namespace
 
@@ -930,8 +935,9 @@ extern "C" int vie_matvec_noalloc(vie_handle* h, int nrhs, const void* x, void* 
         set_error("invalid nrhs, precision, operator, or x == y");
         return VIE_EINVAL;
     }
-    if (!on_device(x) || !on_device(y)) {
-        set_error("vie_matvec_noalloc needs device pointers for x and y (host buffers would need staging memory)");
+    if (!on_device(x, h->device) || !on_device(y, h->device)) {
+        set_error("vie_matvec_noalloc needs x and y in device memory of the handle's device (host buffers would "
+                  "need staging memory)");
         return VIE_EINVAL;
     }
     int dev = -1;

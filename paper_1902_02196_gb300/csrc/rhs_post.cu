@@ -499,7 +499,7 @@ int rhs_dipoles_h_device(vie_handle* h, int R, const double* pos, const double* 
     return VIE_OK;
 }
 
-// magnetic field from the current coefficients (Eq. tot_fields: h = h_inc + K j), b1+ and W_m
+// magnetic field from the current coefficients (Section II total fields: h = h_inc + K j), b1+ and W_m
 int hfields_device(vie_handle* h, int R, const double2* x, const double2* hinc, double2* hout, double2* b1p,
                    double* Wm_host, cudaStream_t s) {
     const long long nv = (long long)h->nv;

@@ -872,6 +872,22 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         VIE_TRY(support_gather(h, R, x, xs, VIE_FP64, sp, st));
     else
         VIE_CUDA(cudaMemsetAsync(xs, 0, sizeof(double2) * total, st));
+    {
+        // NaN or Inf in b or in the guess: rejected before any iteration (the squared norms
+        // of P^-1 b and of the guess on the support are then not finite)
+        double* xn0 = reinterpret_cast<double*>(base + oXn);
+        VIE_TRY(S.norm2_64(xs, xn0));
+        std::vector<double> hb(R), hx(R);
+        VIE_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaMemcpyAsync(hx.data(), xn0, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < R; ++r)
+            if (!std::isfinite(hb[r]) || !std::isfinite(hx[r])) {
+                set_error("right-hand side " + std::to_string(r) + (std::isfinite(hb[r]) ? ": the initial guess" : "") +
+                          " holds a NaN or Inf");
+                return VIE_EINVAL;
+            }
+    }
 
     if (keep) VIE_TRY(ws_reserve(h, h->fcache_ws, 2 * sizeof(double2) * (size_t)R * nfull));
 

@@ -121,7 +121,7 @@ def test_k_matvec_parity(vie, shape, nrhs):
 @pytest.mark.parametrize("shape", [(6, 5, 4), (9, 7, 6)])
 def test_magnetic_post_parity(vie, shape):
     """Tested dipole h_inc, the magnetic field coefficients h = (h_inc + K x) / G, b1+ and W_m vs the
-    oracle's (Eq. tot_fields; Section V-D definitions)."""
+    oracle's (Section II total fields; Section V-D definitions)."""
     g = Grid(*shape, 0.006, 0.005, 0.007)
     eps, sig = random_tissue(g, seed=sum(shape) + 5, air_fraction=0.3)
     freq = 298e6

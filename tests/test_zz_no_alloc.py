@@ -75,3 +75,28 @@ def test_noalloc_rejects_oversize_and_host_buffers(vie):
     torch.cuda.synchronize()
     assert rel(y, ref) <= 1e-5
     h.close()
+
+
+def test_noalloc_just_under_the_limit(vie):
+    """The scratch check counts only the spectrum the call's path uses: on the fused xy path
+    (square xy circulant <= 128) that is nrhs * 12 * nz * Ly * Lx values.  16 x 16 x 31 voxels
+    (circulant 32 x 32 x 64), FP32: 22 right-hand sides need 682 * 12 * 32 * 32 * 8 + 256 bytes,
+    just under 64 MiB, and run; 23 do not fit and are refused."""
+    g = Grid(16, 16, 31, 0.004, 0.004, 0.004)
+    eps, sig = random_tissue(g, seed=9)
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), 298e6, eps, sig)
+    need = 22 * 31 * 12 * 32 * 32 * 8 + 256
+    assert need <= 64 << 20 < need + 31 * 12 * 32 * 32 * 8
+    x = torch.from_numpy(random_coefficients(g, 22, seed=12)).to("cuda", torch.complex64)
+    for _ in range(2):
+        out = torch.full_like(x, float("nan"))
+        ref = torch.empty_like(x)
+        vie.vie_matvec_noalloc(h, x, out, vie.VIE_FP32, vie.VIE_OP_PA)
+        vie.vie_matvec(h, x, ref, vie.VIE_FP32, vie.VIE_OP_PA)
+        torch.cuda.synchronize()
+        assert rel(out, ref) <= 1e-5
+    x23 = torch.zeros((23, 12) + g.shape, dtype=torch.complex64, device="cuda")
+    with pytest.raises(vie.VieError) as e:
+        vie.vie_matvec_noalloc(h, x23, torch.zeros_like(x23), vie.VIE_FP32, vie.VIE_OP_PA)
+    assert e.value.code == vie.VIE_EINVAL and "static scratch" in str(e.value)
+    h.close()
