@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--fp64-reps", type=int, default=3, help="plain FP64 solves timed (the median is reported)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serving", type=int, default=0, metavar="N",
@@ -87,67 +88,69 @@ def dist_init(args):
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (subprocess: fresh interpreter, no CUDA)
 # ---------------------------------------------------------------------------
+# Mean GMRES(50) iterations per right-hand side of the head64 batch to a 1e-6 preconditioned
+# residual, measured once with the plain FP64 GPU solve of the same workload (the oracle runs the
+# same GMRES(50) with the same preconditioner and stopping rule; its modified Gram-Schmidt differs
+# from the GPU's classical one only in rounding).
+HEAD64_ITERS_PER_RHS = 230.0
+
 ORACLE_SAMPLE = r"""
-import os, sys, time, json, math
+import os, sys, time, json
 sys.path.insert(0, {root!r})
 import numpy as np
 from synth import workload
-from oracle import operator as O, rhs as R, solver as S
-w = workload("head", n={n})
+from oracle import operator as O
+w = workload("head64")
 g = w["grid"]
 prob = O.Problem(g, w["freq"], w["eps_real"], w["sigma"])
-t0 = time.perf_counter(); Nop = O.NOperator(g, prob.k0); t_setup = time.perf_counter() - t0
-e = R.dipoles_tested(g, prob.k0, prob.ce, w["dip_pos"][:1], w["dip_mom"][:1])[0]
-b = R.rhs(prob, e)
-times = []; iters = []
+# Green setup excluded: the apply's arithmetic and memory traffic do not depend on the tensor
+# values, so a seeded random table of the oracle's Toeplitz shape stands in for the 4.7 GB one
+rng = np.random.Generator(np.random.PCG64(3))
+shape = (12, 12, 2 * g.nz - 1, 2 * g.ny - 1, 2 * g.nx - 1)
+T = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+t0 = time.perf_counter(); Nop = O.NOperator(g, prob.k0, T); t_setup = time.perf_counter() - t0
+del T
+x = rng.standard_normal((1, 12) + g.shape) + 1j * rng.standard_normal((1, 12) + g.shape)
+times = []
 for s in range({reps}):
     t0 = time.perf_counter()
-    x, info = S.gmres(lambda v: O.apply_PA(prob, Nop, v), O.apply_Pinv(prob, b), tol={tol}, restart={restart}, maxit={maxit})
-    times.append(time.perf_counter() - t0); iters.append(info["iters"])
-print(json.dumps(dict(times=times, iters=iters, setup_s=t_setup, nv=g.nv)))
+    y = O.apply_PA(prob, Nop, x)
+    times.append(time.perf_counter() - t0)
+print(json.dumps(dict(times=times, setup_s=t_setup, workers=O.FFT_WORKERS, nv=g.nv)))
 """
 
 
-def oracle_sample(n=16, reps=1):
-    """Oracle GMRES (FP64, NumPy, single thread) for one dipole RHS of the head phantom family at n^3
-    (192 mm box, voxel 192/n mm), Green setup excluded; returns dict(times, iters, setup_s, nv)."""
+def oracle_sample(reps):
+    """The oracle's preconditioned FFT-Toeplitz matvec (P^-1 A x, NumPy + scipy.fft) of one right-hand
+    side on the full 64^3 head64 grid, `reps` times; returns dict(times, setup_s, workers, nv)."""
     env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = ORACLE_SAMPLE.format(root=ROOT, n=n, reps=reps, tol=TOL, restart=RESTART, maxit=MAXIT)
-    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    code = ORACLE_SAMPLE.format(root=ROOT, reps=reps)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if p.returncode != 0:
         raise RuntimeError("oracle sample failed: " + p.stderr[-2000:])
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
-def scale_to_workload(t_sample, n_sample, n_target=64):
-    """Per-solve time scaled from the sample grid to the target grid by the FFT-matvec work ratio
-    (padded size M = (2n)^3 times log2 M), assuming the preconditioned iteration count does not grow
-    with refinement (Section V-C observes nearly h-independent counts with the preconditioner)."""
-    def work(n):
-        M = (2 * n) ** 3
-        return M * math.log2(M)
-
-    return t_sample * work(n_target) / work(n_sample)
+def oracle_solves_per_s(t_matvec_1rhs):
+    """Oracle solves/s derived from its measured full-size matvec: one matvec per GMRES iteration,
+    HEAD64_ITERS_PER_RHS iterations per right-hand side.  Its Gram-Schmidt, restarts and
+    post-processing are left out, so this overstates the oracle's rate."""
+    return 1.0 / (HEAD64_ITERS_PER_RHS * t_matvec_1rhs)
 
 
-def cpu_baseline_block(n=16):
-    s = oracle_sample(n=n, reps=1)
-    t = statistics.median(s["times"])
-    t64 = scale_to_workload(t, n)
-    return dict(
-        value=1.0 / t64,
-        unit="solves/s",
-        cores=1,
-        kind="oracle",
-        sample=(f"oracle FP64 GMRES (NumPy, 1 thread) of 1 dipole RHS on the {n}^3 head-phantom grid "
-                f"(same 192 mm box, {192.0 / n:.0f} mm voxels) to 1e-6: {t:.2f} s, {s['iters'][0]} iterations, "
-                f"Green setup {s['setup_s']:.1f} s excluded; scaled to 64^3 by the matvec work ratio "
-                f"M log2 M (x{t64 / t:.0f})"),
-        sample_seconds=t,
-    )
+def oracle_sample_text(t, s, n):
+    return (f"oracle P^-1 A x matvec (NumPy, scipy.fft with {s['workers']} workers) of one right-hand side on "
+            f"the full 64^3 head64 grid: median {t:.2f} s over {n} timed runs; solves/s = 1 / "
+            f"({HEAD64_ITERS_PER_RHS:.0f} GMRES iterations per right-hand side x that time), Gram-Schmidt left "
+            f"out; Green setup excluded (seeded random table of the Toeplitz shape, {s['setup_s']:.1f} s)")
+
+
+def cpu_baseline_block(reps=5):
+    s = oracle_sample(reps=reps + 1)
+    t = statistics.median(s["times"][1:])
+    return dict(value=oracle_solves_per_s(t), unit="solves/s", cores=s["workers"], kind="oracle",
+                sample=oracle_sample_text(t, s, reps), sample_seconds=sum(s["times"]))
 
 
 # ---------------------------------------------------------------------------
@@ -156,20 +159,18 @@ def cpu_baseline_block(n=16):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    n = 16
-    s = oracle_sample(n=n, reps=args.warmup + args.steps)
+    s = oracle_sample(reps=args.warmup + args.steps)
     times = s["times"][args.warmup:]
-    t = sum(times)
-    per = [scale_to_workload(ti, n) for ti in times]
-    value = len(per) / sum(per)
+    t = statistics.median(times)
+    value = oracle_solves_per_s(t)
     line = dict(
         impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus, steps=args.steps,
-        warmup=args.warmup, ms_per_step=1000.0 * sum(per) / len(per), higher_is_better=True, scaling="weak",
+        warmup=args.warmup, ms_per_step=1000.0 * sum(times) / len(times), higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f64", data="synthetic",
-        config=dict(workload=WORKLOAD, nrhs=1, sample=f"{n}^3"),
-        cpu_baseline=dict(value=value, unit="solves/s", cores=1, kind="oracle",
-                          sample=f"oracle FP64 GMRES, 1 dipole RHS at {n}^3 per step ({t / len(times):.2f} s), "
-                                 f"scaled to 64^3 by M log2 M"),
+        config=dict(workload=WORKLOAD, nrhs=NRHS, tol=TOL, restart=RESTART,
+                    step="one oracle matvec of one right-hand side at 64^3 (bounded sample)"),
+        cpu_baseline=dict(value=value, unit="solves/s", cores=s["workers"], kind="oracle",
+                          sample=oracle_sample_text(t, s, len(times))),
         e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
     )
     print(json.dumps(line), flush=True)
@@ -540,15 +541,20 @@ def run_ours(args, ws, rank, local):
     )
 
     if not args.no_fp64:
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        rc64, info64, _ = step(vie.VIE_SOLVE_FP64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        t64 = f0.elapsed_time(f1) / 1000.0
-        out["fp64"] = dict(value=NRHS / t64, unit="solves/s", seconds=t64, rc=rc64,
-                           iterations=info64[0]["iterations"], max_resid=max(i["resid"] for i in info64))
+        t64s = []
+        for _ in range(max(1, args.fp64_reps)):
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            rc64, info64, _ = step(vie.VIE_SOLVE_FP64)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            t64s.append(f0.elapsed_time(f1) / 1000.0)
+        t64 = statistics.median(t64s)
+        it64 = [i["iterations"] for i in info64]
+        out["fp64"] = dict(value=NRHS / t64, unit="solves/s", seconds=t64, seconds_all=t64s, rc=rc64,
+                           iterations=it64, mean_iterations=sum(it64) / len(it64),
+                           max_resid=max(i["resid"] for i in info64))
         out["speedup_vs_fp64"] = value / (NRHS * ws / t64)
 
     if e2e is not None:
