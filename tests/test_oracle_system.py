@@ -209,3 +209,95 @@ def test_planewave_voxel_integrals_vs_mpmath():
         for k, f in ((0, R._f0), (1, R._f1)):
             ref = complex(mp.quad(lambda s: s ** k * mp.exp(-1j * kap * s), [-0.5, 0.5]))
             assert abs(complex(f(np.array(kap))) - ref) <= 1e-13 * abs(ref)
+
+
+def _mie_direct(m, x, n_terms):
+    """a_n, b_n of Bohren & Huffman (Eq. 4.53) straight from the Riccati-Bessel functions
+    psi_n(z) = z j_n(z), xi_n(z) = z h_n^(1)(z) of scipy.special (no logarithmic derivative,
+    no recurrence of the oracle's)."""
+    from scipy.special import spherical_jn, spherical_yn
+
+    n = np.arange(1, n_terms + 1)
+    mx = m * x
+
+    def psi(z):
+        return z * spherical_jn(n, z)
+
+    def dpsi(z):
+        return spherical_jn(n, z) + z * spherical_jn(n, z, derivative=True)
+
+    def xi(z):
+        return z * (spherical_jn(n, z) + 1j * spherical_yn(n, z))
+
+    def dxi(z):
+        h = spherical_jn(n, z) + 1j * spherical_yn(n, z)
+        dh = spherical_jn(n, z, derivative=True) + 1j * spherical_yn(n, z, derivative=True)
+        return h + z * dh
+
+    a = (m * psi(mx) * dpsi(x) - psi(x) * dpsi(mx)) / (m * psi(mx) * dxi(x) - xi(x) * dpsi(mx))
+    b = (psi(mx) * dpsi(x) - m * psi(x) * dpsi(mx)) / (psi(mx) * dxi(x) - m * xi(x) * dpsi(mx))
+    return a, b
+
+
+@pytest.mark.parametrize("er,s,a,f", [(50.0, 0.5, 0.1, 298e6), (80.0, 2.0, 0.01, 447e6), (5.0, 0.05, 0.064, 447e6),
+                                       (40.0, 0.6, 0.09, 128e6)])
+def test_mie_coefficients_vs_direct_bessel(er, s, a, f):
+    """The oracle's a_n, b_n (downward logarithmic-derivative recurrence) against a direct
+    evaluation with spherical Bessel functions, at the sizes and materials of the workloads
+    (the Mie-check sphere: k0 a = 0.62, |m| k0 a = 4.4)."""
+    eps = er - 1j * s / (2 * np.pi * f * EPS0)
+    m = np.sqrt(np.conj(eps))
+    x = 2 * np.pi * f / 299792458.0 * a
+    ao, bo = mie.mie_coefficients(m, x)
+    ad, bd = _mie_direct(m, x, len(ao))
+    assert np.max(np.abs(ao - ad)) <= 1e-10 * np.max(np.abs(ad))
+    assert np.max(np.abs(bo - bd)) <= 1e-10 * np.max(np.abs(bd))
+    # and the cross-sections the oracle forms from them
+    k0 = 2 * np.pi * f / 299792458.0
+    n = np.arange(1, len(ad) + 1)
+    cext = 2 * np.pi / k0 ** 2 * np.sum((2 * n + 1) * np.real(ad + bd))
+    csca = 2 * np.pi / k0 ** 2 * np.sum((2 * n + 1) * (np.abs(ad) ** 2 + np.abs(bd) ** 2))
+    ce, cs, ca = mie.cross_sections(eps, a, f)
+    assert abs(ce - cext) <= 1e-10 * abs(cext) and abs(cs - csca) <= 1e-10 * abs(csca)
+
+
+def test_mie_published_example():
+    """The sample output of Bohren & Huffman's BHMIE (Appendix A): Q_ext, Q_sca and Q_back of a
+    sphere of radius 0.525 um, m = 1.55, in light of 0.6328 um, printed to six digits."""
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mie_published.json")))
+    x = 2 * np.pi * ref["radius_um"] / ref["wavelength_um"]
+    m = complex(*ref["refractive_index"])
+    f = 298e6  # any frequency: only the size parameter k0 a enters
+    a = x / (2 * np.pi * f / 299792458.0)
+    cext, csca, _ = mie.cross_sections(np.conj(m) ** 2, a, f)
+    area = np.pi * a * a
+    half_ulp = 0.5 * 10.0 ** (1 - ref["digits"])
+    assert abs(cext / area - ref["Q_ext"]) <= half_ulp * 1.01
+    assert abs(csca / area - ref["Q_sca"]) <= half_ulp * 1.01
+    an, bn = mie.mie_coefficients(m, x)
+    n = np.arange(1, len(an) + 1)
+    qback = abs(np.sum((2 * n + 1) * (-1.0) ** n * (an - bn))) ** 2 / x ** 2
+    assert abs(qback - ref["Q_back"]) <= half_ulp * 1.01
+    # the rounded size parameter the table prints gives a visibly different Q_ext: the pin is sharp
+    cext2, _, _ = mie.cross_sections(np.conj(m) ** 2, 5.213 / (2 * np.pi * f / 299792458.0), f)
+    assert abs(cext2 / (np.pi * (5.213 / (2 * np.pi * f / 299792458.0)) ** 2) - ref["Q_ext"]) > 1e-4
+
+
+def test_dense_N_from_absolute_positions():
+    """The dense Galerkin matrix assembled pair by pair from the voxels' absolute centre positions
+    (each pair's entries computed on their own) equals the one indexed from the Toeplitz tensor
+    T[m - n] (translation invariance of the Galerkin entries, Eq. 42-43)."""
+    from oracle import green as OG
+
+    g = Grid(3, 2, 4, 0.004, 0.005, 0.0045)
+    k0 = O.k0_of(298e6)
+    xx, yy, zz = g.centres()
+    pos = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1)
+    delta = np.array([g.dx, g.dy, g.dz])
+    nv = g.nv
+    D = np.rint((pos[:, None, :] - pos[None, :, :]) / delta).astype(np.int64).reshape(-1, 3)
+    E = OG.n_entries(delta, k0, D).reshape(12, 12, nv, nv)
+    M = np.transpose(E, (0, 2, 1, 3)).reshape(12 * nv, 12 * nv)
+    T = OG.toeplitz_tensors(g, k0)
+    ref = O.dense_N(g, T)
+    assert np.max(np.abs(M - ref)) <= 1e-14 * np.max(np.abs(ref))
