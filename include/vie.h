@@ -75,6 +75,10 @@ typedef struct {
     int refinements;     /* outer refinement sweeps (mode VIE_SOLVE_FP32_REFINE) */
     double resid;        /* final ||P^-1 (b - A x)|| / ||P^-1 b||, recomputed in FP64 */
     double true_resid;   /* final ||b - A x|| / ||b|| in FP64 when requested (flags bit 1), else -1 */
+    double err_est;      /* estimated relative error ||x - x*|| / ||x|| of the returned x (x* the exact
+                            solution of A x = b): the last refinement sweep's (mixed) or restart cycle's
+                            (FP64) correction dx, scaled by the residual reduction it left,
+                            ||dx|| / ||x|| * ||r_end|| / ||r_start|| (preconditioned residuals) */
 } vie_solve_info;
 
 /*

@@ -39,7 +39,7 @@ class vie_grid(ctypes.Structure):
 class vie_solve_info(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
                 ("fp32_matvecs", ctypes.c_int), ("refinements", ctypes.c_int), ("resid", ctypes.c_double),
-                ("true_resid", ctypes.c_double)]
+                ("true_resid", ctypes.c_double), ("err_est", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -555,6 +555,18 @@ __global__ void check_kernel(const double* __restrict__ rn2, const double* __res
     target[r] = rr <= tol ? INFINITY : fmax(eta_min * rn, 0.5 * tol * bn);
 }
 
+// Forward-error estimate of the right-hand sides a sweep or cycle worked on (not done before it):
+// err = ||dx|| / ||x|| * ||r_end|| / ||r_start||, dx the step's correction (Section IV-B residuals)
+__global__ void err_est_kernel(const double* __restrict__ dn2, const double* __restrict__ xn2,
+                               const double* __restrict__ rn2, const double* __restrict__ rn2_prev,
+                               const int* __restrict__ done_prev, double* err, int R) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || done_prev[r]) return;
+    const double x = sqrt(fmax(xn2[r], 0.0)), d = sqrt(fmax(dn2[r], 0.0));
+    const double r0 = sqrt(fmax(rn2_prev[r], 0.0)), r1 = sqrt(fmax(rn2[r], 0.0));
+    err[r] = (x > 0.0 && r0 > 0.0) ? d / x * (r1 / r0) : 0.0;
+}
+
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Per (z, y) row: [x0, x1) spanning the voxels where chi, any right-hand side or the
@@ -756,7 +768,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     if (sp.ns == 0) {  // chi = 0 everywhere and b = 0: x = 0
         VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)(R * nfull), st));
         VIE_CUDA(cudaStreamSynchronize(st));
-        for (int r = 0; info && r < R; ++r) info[r] = vie_solve_info{1, 0, 0, 0, 0, 0.0, (flags & 2) ? 0.0 : -1.0};
+        for (int r = 0; info && r < R; ++r) info[r] = vie_solve_info{1, 0, 0, 0, 0, 0.0, (flags & 2) ? 0.0 : -1.0, 0.0};
         return VIE_OK;
     }
     const long long n = 12LL * sp.ns;
@@ -807,6 +819,9 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const size_t oXs0 = take(sizeof(double2) * (size_t)R * n);  // solution at the start of the last sweep
     const size_t oDn = take(sizeof(double) * R);
     const size_t oXn = take(sizeof(double) * R);
+    const size_t oRnp = take(sizeof(double) * R);  // squared residual norms at the start of a step
+    const size_t oDonep = take(sizeof(int) * R);   // converged before that step
+    const size_t oErr = take(sizeof(double) * R);  // forward-error estimates
     VIE_TRY(ws_reserve(h, h->solve_ws, off));
     char* base = static_cast<char*>(h->solve_ws.ptr);
     Solver S;
@@ -902,6 +917,35 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     double* dn2 = reinterpret_cast<double*>(base + oDn);
     double* xn2 = reinterpret_cast<double*>(base + oXn);
     bool have_r0 = false;
+    double* rn2_prev = reinterpret_cast<double*>(base + oRnp);
+    int* done_prev = reinterpret_cast<int*>(base + oDonep);
+    double* err = reinterpret_cast<double*>(base + oErr);
+    VIE_CUDA(cudaMemsetAsync(err, 0, sizeof(double) * R, st));
+    bool step_open = false;  // a sweep (mixed) or cycle (FP64) started from xs0 / rn2_prev / done_prev
+    // start of a refinement sweep or FP64 cycle: keep its starting point (the refinement's residual
+    // update and the error estimate use it)
+    auto open_step = [&]() -> int {
+        if (mixed) {
+            VIE_CUDA(cudaMemcpyAsync(rs0, r64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
+            have_r0 = !x_is_zero;
+        }
+        VIE_CUDA(cudaMemcpyAsync(xs0, xs, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
+        VIE_CUDA(cudaMemcpyAsync(rn2_prev, rn2, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
+        VIE_CUDA(cudaMemcpyAsync(done_prev, done, sizeof(int) * R, cudaMemcpyDeviceToDevice, st));
+        step_open = true;
+        return VIE_OK;
+    };
+    // after the residual of the step's end point: the error estimate of the right-hand sides it moved
+    auto close_step = [&]() -> int {
+        if (!step_open) return VIE_OK;
+        VIE_KLAUNCH("err_est", st, sub_kernel<<<gt, 256, 0, st>>>(xs, xs0, t64, total));
+        VIE_TRY(S.norm2_64(t64, dn2));
+        VIE_TRY(S.norm2_64(xs, xn2));
+        VIE_KLAUNCH("err_est", st, err_est_kernel<<<gr, 128, 0, st>>>(dn2, xn2, rn2, rn2_prev, done_prev, err, R));
+        VIE_CHECK_LAUNCH();
+        step_open = false;
+        return VIE_OK;
+    };
     // Refinement residual.  The first one (after the first sweep) is b - A x with the FP64
     // matvec.  Later ones update the previous sweep's residual, r - A d with d the sweep's
     // correction, when |d| <= min(1e-3, 1e5 tol) |x| for every right-hand side: then A d in
@@ -946,11 +990,6 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
                 h->fcache_valid = 1;
             }
         }
-        if (mixed) {
-            VIE_CUDA(cudaMemcpyAsync(rs0, r64, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
-            VIE_CUDA(cudaMemcpyAsync(xs0, xs, sizeof(double2) * total, cudaMemcpyDeviceToDevice, st));
-            have_r0 = !x_is_zero;
-        }
         VIE_TRY(S.norm2_64(r64, rn2));
         VIE_KLAUNCH("residual_check", st,
                     check_kernel<<<gr, 128, 0, st>>>(rn2, bn2, tol, eta_min, S.gs.target, done, rel, R));
@@ -969,7 +1008,9 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     int cyc = 0;
     while (cyc < maxit) {
         VIE_TRY(residual());
+        VIE_TRY(close_step());
         if (all) break;
+        VIE_TRY(open_step());
         if (mixed) {
             ++sweeps;
             float2* U32 = reinterpret_cast<float2*>(base + oU);
@@ -989,7 +1030,13 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             x_is_zero = false;
         }
     }
-    if (!all) VIE_TRY(residual());  // residual of the last iterate when the cycle cap was hit
+    if (!all) {  // residual of the last iterate when the cycle cap was hit
+        VIE_TRY(residual());
+        VIE_TRY(close_step());
+    }
+    std::vector<double> herr(R, 0.0);
+    VIE_CUDA(cudaMemcpyAsync(herr.data(), err, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaStreamSynchronize(st));
     VIE_TRY(support_scatter(h, R, xs, x, VIE_FP64, sp, st));
     if (flags & 2) {
         // unpreconditioned residual ||b - A x|| / ||b|| on the full grid; its convolution at
@@ -1024,6 +1071,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             info[r].refinements = sweeps;
             info[r].resid = hrel[r];
             info[r].true_resid = htrue[r];
+            info[r].err_est = herr[r];
         }
     }
     return rc;
