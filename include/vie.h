@@ -49,6 +49,10 @@ extern "C" {
 /* Compute precision of a matvec; also the element type of its vectors. */
 #define VIE_FP64 0 /* complex128 vectors, FP64 FFT and block product */
 #define VIE_FP32 1 /* complex64 vectors, FP32 FFT and block product */
+#define VIE_BF16X3 2 /* complex64 vectors, FP32 FFT; block product on the tensor cores from bf16
+                        (hi, lo) splits of both operands, x_lo B_hi + x_hi B_lo + x_hi B_hi with FP32
+                        accumulation (each real product within 3 * 2^-16 relative); FFT lengths
+                        along z of 8..512 */
 
 /* Operator applied by vie_matvec. */
 #define VIE_OP_A 0      /* y = A x = M_eps G x - M_chi N x                     (Eq. 24) */
@@ -59,6 +63,7 @@ extern "C" {
 /* Solver modes of vie_solve. */
 #define VIE_SOLVE_FP64 0         /* plain FP64 GMRES */
 #define VIE_SOLVE_FP32_REFINE 1  /* FP32 inner GMRES inside FP64 iterative refinement */
+#define VIE_SOLVE_BF16X3_REFINE 2 /* as VIE_SOLVE_FP32_REFINE with the VIE_BF16X3 matvec in the inner GMRES */
 
 typedef struct vie_handle vie_handle;
 
@@ -71,7 +76,7 @@ typedef struct {
     int converged;       /* 1 if resid <= tol */
     int iterations;      /* GMRES (Arnoldi) steps taken, all precisions */
     int fp64_matvecs;    /* FP64 operator applications (refinement residuals, plain FP64 steps) */
-    int fp32_matvecs;    /* FP32 operator applications */
+    int fp32_matvecs;    /* FP32 (or BF16x3) operator applications */
     int refinements;     /* outer refinement sweeps (mode VIE_SOLVE_FP32_REFINE) */
     double resid;        /* final ||P^-1 (b - A x)|| / ||P^-1 b||, recomputed in FP64 */
     double true_resid;   /* final ||b - A x|| / ||b|| in FP64 when requested (flags bit 1), else -1 */
@@ -127,8 +132,8 @@ void vie_destroy(vie_handle* h);
  * point, inverse FFT, crop, then the per-voxel material and Gram terms.
  *   nrhs      : number of vectors >= 1
  *   x, y      : [nrhs][12][nz][ny][nx] complex, element type by `precision`
- *               (VIE_FP64: double pairs, VIE_FP32: float pairs); x and y must not overlap
- *   precision : VIE_FP64 or VIE_FP32 (VIE_OP_K: VIE_FP64 only)
+ *               (VIE_FP64: double pairs, VIE_FP32 and VIE_BF16X3: float pairs); x and y must not overlap
+ *   precision : VIE_FP64, VIE_FP32 or VIE_BF16X3 (VIE_OP_K: VIE_FP64 only)
  *   op        : VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT or VIE_OP_K.  VIE_OP_K transforms the 30
  *               tensors of vie_green_toeplitz_k once per handle (kept until vie_destroy) and
  *               applies the K block (96 signed entries) on full circulant spectra, in FP64.
@@ -199,7 +204,9 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *             (flags & 1), else ignored (zero guess); on exit the solution
  *   restart : Krylov dimension m in [1, 128];  maxit: cap on restart cycles, counted
  *             over all refinement sweeps in mixed mode
- *   mode    : VIE_SOLVE_FP64 (plain FP64: every restart recomputes the residual with
+ *   mode    : VIE_SOLVE_BF16X3_REFINE is VIE_SOLVE_FP32_REFINE below with the VIE_BF16X3 matvec in
+ *             the FP32 GMRES cycles (the refinement residuals unchanged);
+ *             VIE_SOLVE_FP64 (plain FP64: every restart recomputes the residual with
  *             the FP64 matvec) or VIE_SOLVE_FP32_REFINE (FP32 GMRES with FP64 iterative
  *             refinement: each sweep takes the residual in FP64, then runs FP32 cycles
  *             on the correction until every right-hand side is below

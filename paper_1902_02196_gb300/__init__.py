@@ -18,9 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvie.so")
 
 VIE_OK, VIE_EINVAL, VIE_ENOMEM, VIE_EDEVICE, VIE_ETIMEOUT, VIE_NOT_CONVERGED = 0, -1, -2, -3, -4, 1
-VIE_FP64, VIE_FP32 = 0, 1
+VIE_FP64, VIE_FP32, VIE_BF16X3 = 0, 1, 2
 VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT, VIE_OP_K = 0, 1, 2, 3
-VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE = 0, 1
+VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE, VIE_SOLVE_BF16X3_REFINE = 0, 1, 2
 VIE_INJECT_NONE, VIE_INJECT_OOM = 0, 1
 
 EXPORTS = (

@@ -108,6 +108,7 @@ void release(vie_handle* h) {
         cudaFree(h->green32);
         cudaFree(h->green32t);
         cudaFree(h->green64t);
+        cudaFree(h->greenbf);
         cudaFree(h->colmap);
         cudaFree(h->colkx32);
         cudaFree(h->tw64);
@@ -212,7 +213,7 @@ int vie_setup_green_external(const vie_grid* grid, double freq_hz, const double*
 
 size_t handle_green_bytes(const vie_handle* h) {
     const size_t ov = (size_t)h->O[0] * h->O[1] * h->O[2];
-    return 60 * ov * (2 * sizeof(double2) + 2 * sizeof(float2)) + 60 * h->nv * sizeof(double2) +
+    return 60 * ov * (2 * sizeof(double2) + 2 * sizeof(float2) + sizeof(uint2)) + 60 * h->nv * sizeof(double2) +
            2048 * (sizeof(double2) + sizeof(float2)) + 2 * (size_t)h->L[0];
 }
 
@@ -305,6 +306,7 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
         h->green32 = share->green32;
         h->green32t = share->green32t;
         h->green64t = share->green64t;
+        h->greenbf = share->greenbf;
         h->colmap = share->colmap;
         h->colkx32 = share->colkx32;
         h->colpos32 = share->colpos32;
@@ -363,7 +365,7 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
     g_last_error.clear();
     REQUIRE(h && x && y, "NULL argument");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-    REQUIRE(precision == VIE_FP64 || precision == VIE_FP32, "unknown precision");
+    REQUIRE(precision == VIE_FP64 || precision == VIE_FP32 || precision == VIE_BF16X3, "unknown precision");
     REQUIRE(op == VIE_OP_A || op == VIE_OP_PA || op == VIE_OP_NSCAT || op == VIE_OP_K, "unknown operator");
     REQUIRE(op != VIE_OP_K || precision == VIE_FP64, "the K operator is FP64 only");
     REQUIRE(x != y, "x and y must not overlap");
@@ -421,7 +423,8 @@ int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int r
     REQUIRE(std::isfinite(tol) && tol > 0 && tol < 1, "tol must be in (0, 1)");
     REQUIRE(restart >= 1 && restart <= 128, "restart must be in [1, 128]");
     REQUIRE(maxit >= 1, "maxit must be >= 1");
-    REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE, "unknown mode");
+    REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE || mode == VIE_SOLVE_BF16X3_REFINE,
+            "unknown mode");
     REQUIRE((flags & ~7) == 0, "unknown flags");
     const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);

@@ -113,6 +113,9 @@ struct vie_handle {
     float2* green32t;
     // FP64 copy in the same layout, for the FP64 fused z pass
     double2* green64t;
+    // bf16 split of green32t in the same layout, for the BF16x3 z pass: per tensor (hi, lo),
+    // each a bf16 (re, im) pair with hi = bf16(v), lo = bf16(v - hi)
+    uint2* greenbf;
     // stored column order of that path's spectrum: [Lx] kx per stored column, then [Lx]
     // positions of those kx in the x transform's output order (square L <= 128 only, else null)
     unsigned char* colmap;
@@ -209,6 +212,7 @@ int solve_device_bytes(double out[3], bool reset);
 // ---------------------------------------------------------------------------
 int green_setup(vie_handle* h);                 // green.cu
 int green_setup_external(vie_handle* h, const double2* ext);  // green.cu, ext on the device
+int green_split_bf16(vie_handle* h);            // zpass_bf16.cu: greenbf from green32t
 int twiddle_setup(vie_handle* h);               // matvec.cu
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);

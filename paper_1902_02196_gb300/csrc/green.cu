@@ -644,9 +644,10 @@ int green_embed(vie_handle* h, double2* T) {
     if (cudaMalloc(&h->green64, sizeof(double2) * 60 * ovol) != cudaSuccess ||
         cudaMalloc(&h->green32, sizeof(float2) * 60 * ovol) != cudaSuccess ||
         cudaMalloc(&h->green32t, sizeof(float2) * 60 * ovol) != cudaSuccess ||
-        cudaMalloc(&h->green64t, sizeof(double2) * 60 * ovol) != cudaSuccess)
+        cudaMalloc(&h->green64t, sizeof(double2) * 60 * ovol) != cudaSuccess ||
+        cudaMalloc(&h->greenbf, sizeof(uint2) * 60 * ovol) != cudaSuccess)
         return fail((set_error("green alloc"), VIE_ENOMEM));
-    h->bytes_held += (2 * sizeof(double2) + 2 * sizeof(float2)) * 60 * ovol;
+    h->bytes_held += (2 * sizeof(double2) + 2 * sizeof(float2) + sizeof(uint2)) * 60 * ovol;
     int chunk = (int)std::max<long long>(1, std::min<long long>(60, (4LL << 30) / (vol * (long long)sizeof(double2))));
     if (cudaMalloc(&C, sizeof(double2) * vol * chunk) != cudaSuccess) return fail((set_error("embed alloc"), VIE_ENOMEM));
     for (int t0 = 0; t0 < 60; t0 += chunk) {
@@ -662,6 +663,8 @@ int green_embed(vie_handle* h, double2* T) {
                                                                      h->green64t));
         if (cudaGetLastError() != cudaSuccess) return fail((set_error("octant launch"), VIE_EDEVICE));
     }
+    rc = green_split_bf16(h);
+    if (rc < 0) return fail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail((set_error("green setup sync"), VIE_EDEVICE));
     cudaFree(C);
     // The Toeplitz table is kept for inspection (vie_green_toeplitz)

@@ -24,6 +24,8 @@
 #include "zpass_f32.cuh"
 #include "zpass_f64.cuh"
 
+int zpass_bf16_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s);  // zpass_bf16.cu
+
 // y[12] = B(k) x[12] at one frequency point; xv/acc in registers, Green values streamed once.
 template <typename C>
 __device__ __forceinline__ void block_product(C* xv, C* acc, const C* __restrict__ gp, long long tstride) {
@@ -531,10 +533,11 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
 
 // ws: scratch of at least matvec_workspace_bytes(h, R, precision) bytes (spectrum buffers W1, W2);
 // sp: support of x and y (only the FP32 three-kernel path takes vectors on a support)
+// bf16: the FP32 path with the BF16x3 block product in the z pass (T = float only)
 template <typename T>
 static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws,
                        const Support& sp = Support{}, const double2* shift = nullptr, void* conv = nullptr,
-                       const int* rmap = nullptr, int nact = 0) {
+                       const int* rmap = nullptr, int nact = 0, bool bf16 = false) {
     using C = typename CT<T>::C;
     const int nx = h->nx, ny = h->ny, nz = h->nz, Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
     // rmap (fused xy path only): transform only the nact right-hand sides it lists
@@ -578,7 +581,12 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
             z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            if (bf16) return zpass_bf16_fused(h, z, s);
             return zpass_f32_fused(h, z, s);
+        }
+        if (bf16) {
+            set_error("the BF16x3 matvec needs an FFT length along z of 8..512");
+            return VIE_EINVAL;
         }
         if (sizeof(T) == 8 && zfused_ok(h)) {
             ZDArgs z{};
@@ -664,7 +672,8 @@ static int matvec_full(vie_handle* h, int nrhs, const void* x, void* y, int prec
                        void* conv) {
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, nrhs, precision)));
     if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv);
-    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv);
+    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv, nullptr, 0,
+                              precision == VIE_BF16X3);
 }
 
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s) {
@@ -747,7 +756,8 @@ int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, 
     if (xy_ok(h) || !sp.rows)
         return precision == VIE_FP64
                    ? matvec_impl<double>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift, conv, rmap, nact)
-                   : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift, conv, rmap, nact);
+                   : matvec_impl<float>(h, R, x, y, op, s, h->fft_ws.ptr, sp, shift, conv, rmap, nact,
+                                        precision == VIE_BF16X3);
     const size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     void* tx = tmp;
     void* ty = static_cast<char*>(tmp) + c * (size_t)R * 12 * h->nv;

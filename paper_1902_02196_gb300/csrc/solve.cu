@@ -772,7 +772,8 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         return VIE_OK;
     }
     const long long n = 12LL * sp.ns;
-    const bool mixed = mode == VIE_SOLVE_FP32_REFINE;
+    const bool mixed = mode == VIE_SOLVE_FP32_REFINE || mode == VIE_SOLVE_BF16X3_REFINE;
+    const int inner = mode == VIE_SOLVE_BF16X3_REFINE ? VIE_BF16X3 : VIE_FP32;  // matvec of the inner GMRES
     const size_t vc = mixed ? sizeof(float2) : sizeof(double2);
     const int kpt = mixed ? Prec<float2>::K : Prec<double2>::K;
     const int nblk = (int)((n + kThreads * kpt - 1) / (kThreads * kpt));
@@ -1016,7 +1017,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             float2* U32 = reinterpret_cast<float2*>(base + oU);
             for (;;) {
                 int still = 0;
-                VIE_TRY(run_cycle<float2>(S, U32, xs, r64, rn2, VIE_FP32, it_rhs.data(), &mv32, pinned, &still));
+                VIE_TRY(run_cycle<float2>(S, U32, xs, r64, rn2, inner, it_rhs.data(), &mv32, pinned, &still));
                 ++cyc;
                 x_is_zero = false;
                 if (still == 0 || cyc >= maxit) break;

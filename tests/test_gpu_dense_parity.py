@@ -98,6 +98,19 @@ def test_dense_matvec_fp32(vie, case, green, op):
         assert rel(y[r], refs[op][r]) <= 1e-5
 
 
+@pytest.mark.parametrize("op", ["A", "PA", "NSCAT"])
+def test_dense_matvec_bf16x3(vie, case, op):
+    """The BF16x3 tensor-core block product (bound 5e-5, from 3 * 2^-16 per real product)."""
+    g, x, refs, h_dev, h_ext = case
+    code = {"A": vie.VIE_OP_A, "PA": vie.VIE_OP_PA, "NSCAT": vie.VIE_OP_NSCAT}[op]
+    y = gpu_matvec(vie, h_ext, x, vie.VIE_BF16X3, code)
+    err = rel(y, refs[op])
+    print(f"bf16x3 {g.nx}x{g.ny}x{g.nz} {op}: {err:.2e}")
+    assert err <= 5e-5, err
+    for r in range(R):
+        assert rel(y[r], refs[op][r]) <= 5e-5
+
+
 def test_external_green_toeplitz_roundtrip(vie, case):
     """The 60 tensors the external handle keeps are the oracle's representative entries (N - G)."""
     g, _, _, h_dev, h_ext = case

@@ -39,7 +39,7 @@ def setup(vie, g, freq, eps, sig):
 
 
 def gpu_matvec(vie, h, x, precision, op):
-    dt = torch.complex128 if precision == vie.VIE_FP64 else torch.complex64
+    dt = torch.complex128 if precision == vie.VIE_FP64 else torch.complex64  # FP32 and BF16X3: complex64
     xd = torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dt)
     yd = torch.empty_like(xd)
     vie.vie_matvec(h, xd, yd, precision, op)
@@ -199,6 +199,27 @@ def test_matvec_fp32_parity(vie, cases, shape):
         assert rel(y, ref) <= 1e-5
 
 
+# BF16x3 block product: each real product within 3 * 2^-16 of exact (bf16 hi/lo splits of both
+# operands, the lo x lo term dropped), FP32 transforms and accumulation; bound on the matvec's
+# relative 2-norm error: 5e-5
+BF16X3_TOL = 5e-5
+
+
+@pytest.mark.parametrize("shape", [c[0] for c in CASES])
+def test_matvec_bf16x3_parity(vie, cases, shape):
+    g, prob, Nop, h, x = cases[shape]
+    G = prob.gram_vector()[:, None, None, None]
+    for op, code in (("A", vie.VIE_OP_A), ("PA", vie.VIE_OP_PA), ("NSCAT", vie.VIE_OP_NSCAT)):
+        if op == "A":
+            ref = O.apply_A(prob, Nop, x)
+        elif op == "PA":
+            ref = O.apply_PA(prob, Nop, x)
+        else:
+            ref = Nop.apply(x) - G * x
+        y = gpu_matvec(vie, h, x, vie.VIE_BF16X3, code)
+        assert rel(y, ref) <= BF16X3_TOL
+
+
 def test_matvec_host_buffers_equal_device_buffers(vie, cases):
     g, prob, Nop, h, x = cases[(7, 5, 9)]
     yh = np.zeros_like(x)
@@ -247,12 +268,12 @@ def sphere(vie):
     h.close()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "bf16x3"])
 def test_solve_parity_sphere(vie, sphere, mode):
     g, prob, Nop, e_inc, b, xo, h = sphere
     bd = torch.from_numpy(b[None].copy()).cuda()
     xd = torch.empty_like(bd)
-    m = vie.VIE_SOLVE_FP64 if mode == "fp64" else vie.VIE_SOLVE_FP32_REFINE
+    m = {"fp64": vie.VIE_SOLVE_FP64, "mixed": vie.VIE_SOLVE_FP32_REFINE, "bf16x3": vie.VIE_SOLVE_BF16X3_REFINE}[mode]
     rc, info = vie.vie_solve(h, bd, xd, tol=1e-8, restart=50, maxit=40, mode=m)
     assert rc == vie.VIE_OK, info
     assert info[0]["resid"] <= 1e-8
@@ -269,6 +290,7 @@ def test_solve_parity_sphere(vie, sphere, mode):
     # FP64 product at the refinement point plus the FP32 product of the later correction d,
     # an error of at most about 1e-6 |d| / |x| <= 1e-9, three orders below the 1e-6 field
     # tolerance.
+    # (BF16x3 mode: the same FP32 correction of the field map as the mixed mode)
     assert rel(ef.cpu().numpy()[0], e_ref) <= (1e-12 if mode == "fp64" else 1e-9)
     assert rel(pa.cpu().numpy()[0], p_ref) <= 1e-12
     assert abs(P[0] - P_ref) <= 1e-12 * abs(P_ref)
