@@ -544,6 +544,7 @@ def run_ours(args, ws, rank, local):
                     bf16x3_ms=mv16_ms,
                     alg_bytes=mv_bytes),
         roofline=roofline, kernels=share, gpu_launches=total_launches, launches_before_timed=launches_before,
+        autotune=vie.vie_tuning(), cycle_graphs=True,
         setup_s=setup_s, clocks=clk,
         wall_s=wall,
     )

@@ -218,7 +218,12 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
  *             min(1e-3, 1e5 tol) |x| for every right-hand side, else the FP64 matvec)
  *   flags   : bit 0 = use x as initial guess; bit 1 = also compute true_resid
  *             (one more FP64 matvec), else true_resid = -1; bit 2 = keep no point for
- *             vie_fields (below)
+ *             vie_fields (below); bit 3 = launch every kernel directly instead of replaying
+ *             each restart cycle as a CUDA graph (same results, bit for bit)
+ * Each restart cycle runs on the device without host round trips: the Arnoldi steps work on a
+ * device list of the right-hand sides still above their target, and the host reads the list
+ * once per cycle.  On a stream other than the legacy or per-thread default stream, the cycle is
+ * captured once per solve as a CUDA graph (m Arnoldi steps of about 15 kernels each) and replayed.
  * Where chi, b and the guess all vanish (air), the rows of P^-1 A are the identity and
  * the solution is zero; the solver's vectors cover only each grid row's span of the
  * other voxels (the whole grid when that span covers it), so air costs no iterations'
@@ -317,6 +322,10 @@ int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes);
  * each launch must read and write at minimum: its inputs once, its outputs
  * once); *n_entries rows written and *total_launches over all names.  Any
  * output pointer may be NULL.  Host memory.  Counters are process-wide.
+ * Launches inside a solver cycle that find no active right-hand side return at once: they are
+ * not in the per-name counts but are in *total_launches (every launch issued).  Kernels
+ * replayed from a CUDA graph are counted (and timed) per replay.
+ * vie_stats_read synchronises the device first.
  */
 int vie_stats_reset(int enable_timing);
 int vie_stats_read(int max_entries, char* names, long long* launches, double* ms, double* bytes, int* n_entries,
@@ -399,6 +408,17 @@ int vie_server_stats(vie_server* s, int* queued, int* running, size_t* bytes_in_
 #define VIE_INJECT_NONE 0
 #define VIE_INJECT_OOM 1
 int vie_fault_inject(int kind, int count);
+
+/*
+ * vie_tuning -- the launch configurations the library's autotuner measured and chose (no
+ * counterpart in the paper).  The z-pass kernels are compiled for several tile widths (column
+ * lines per CTA); the first time a grid shape and right-hand side class (the count rounded up to
+ * a power of two, at most 8) is seen outside stream capture, each width runs on a scratch
+ * spectrum of that many right-hand sides (allocated for the measurement) and the fastest median
+ * device time wins for the process.  Writes one line per measured shape, NUL-terminated,
+ * into out[len] (truncated to fit; out may be NULL); returns the full text length.
+ */
+int vie_tuning(char* out, size_t len);
 
 /* Static description of an error code. */
 const char* vie_strerror(int code);

@@ -26,7 +26,7 @@ VIE_INJECT_NONE, VIE_INJECT_OOM = 0, 1
 EXPORTS = (
     "vie_setup", "vie_setup_green_external", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
     "vie_fields", "vie_green_toeplitz", "vie_green_toeplitz_k", "vie_rhs_dipoles_h", "vie_hfields", "vie_info", "vie_strerror", "vie_last_error",
-    "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc", "vie_fault_inject",
+    "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc", "vie_fault_inject", "vie_tuning",
     "vie_server_create", "vie_server_destroy", "vie_submit", "vie_poll", "vie_server_stats",
 )
 
@@ -108,6 +108,7 @@ def _lib():
     lib.vie_stats_reset.argtypes = [I]
     lib.vie_stats_read.argtypes = [I, P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)]
     lib.vie_fault_inject.argtypes = [I, I]
+    lib.vie_tuning.argtypes = [P, S]
     lib.vie_last_error.argtypes = []
     lib.vie_last_error.restype = ctypes.c_char_p
     lib.vie_server_create.argtypes = [S, I, ctypes.POINTER(P)]
@@ -238,12 +239,13 @@ def vie_rhs_dipoles(h, pos, mom, e_inc=None, b=None, stream=None):
 
 
 def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFINE, guess=False, true_resid=False,
-              keep_point=True, stream=None):
+              keep_point=True, graph=True, stream=None):
     """Returns (rc, [info dict per right-hand side]); rc is VIE_OK or VIE_NOT_CONVERGED.
-    keep_point=False: the handle keeps no residual point for vie_fields (flags bit 2)."""
+    keep_point=False: the handle keeps no residual point for vie_fields (flags bit 2).
+    graph=False: direct launches instead of a CUDA graph per restart cycle (flags bit 3)."""
     n = _nrhs(b, h.nv)
     info = (vie_solve_info * n)()
-    flags = (1 if guess else 0) | (2 if true_resid else 0) | (0 if keep_point else 4)
+    flags = (1 if guess else 0) | (2 if true_resid else 0) | (0 if keep_point else 4) | (0 if graph else 8)
     rc = _check(_lib().vie_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
                                  flags, info, _stream(stream)), "vie_solve")
     return rc, [i.as_dict() for i in info]
@@ -297,6 +299,15 @@ def vie_info(h):
 def vie_fault_inject(kind, count=1):
     """Host-side fault injection (VIE_INJECT_OOM: the next `count` workspace growths fail)."""
     return _check(_lib().vie_fault_inject(int(kind), int(count)), "vie_fault_inject")
+
+
+def vie_tuning():
+    """Lines of the autotuner's measurements and choices (one per grid shape seen)."""
+    lib = _lib()
+    n = lib.vie_tuning(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.vie_tuning(ctypes.addressof(buf), n + 1)
+    return buf.value.decode().splitlines()
 
 
 def vie_strerror(code):

@@ -425,7 +425,7 @@ int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int r
     REQUIRE(maxit >= 1, "maxit must be >= 1");
     REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE || mode == VIE_SOLVE_BF16X3_REFINE,
             "unknown mode");
-    REQUIRE((flags & ~7) == 0, "unknown flags");
+    REQUIRE((flags & ~15) == 0, "unknown flags");
     const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};

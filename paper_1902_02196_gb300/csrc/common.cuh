@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/vie.h"
 
@@ -207,6 +208,36 @@ struct LaunchScope {
 // [0] gs_dots, [1] gs_update, [2] solution_update; optionally reset
 int solve_device_bytes(double out[3], bool reset);
 
+// Launches whose right-hand side count is known only on the device (the solver's active list)
+// count themselves on the device, per kernel name: ctr[0] += algorithmic bytes and ctr[1] += 1
+// when the launch has work (a launch whose list is empty returns at once and is not counted).
+// dev_bytes_ptr(name) is the pair's address on the current device (NULL if it cannot be had);
+// such launches pass kDevCounted as their host-side bytes, and vie_stats_read adds the counters in.
+constexpr double kDevCounted = -1.0;
+unsigned long long* dev_bytes_ptr(const char* name);
+__device__ __forceinline__ void dev_bytes_add(unsigned long long* ctr, double bytes, bool work) {
+    if (ctr && work && blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(ctr, (unsigned long long)bytes);
+        atomicAdd(ctr + 1, 1ull);
+    }
+}
+
+// Launch accounting of CUDA graphs.  Between stats_capture_begin and stats_capture_end (on the
+// capturing thread) every LaunchScope appends a record to `list` instead of counting, with
+// event-record nodes around the launch when timing is on; each replay of the graph is then
+// counted by stats_graph_replayed, and its device times are added by stats_graph_harvest
+// once the replay has finished.  stats_capture_release destroys the records' events.
+struct CapRec {
+    std::string name;
+    double bytes;
+    cudaEvent_t ev0, ev1;
+};
+void stats_capture_begin(std::vector<CapRec>* list);
+void stats_capture_end();
+void stats_graph_replayed(const std::vector<CapRec>& list);
+void stats_graph_harvest(const std::vector<CapRec>& list);
+void stats_capture_release(std::vector<CapRec>& list);
+
 // ---------------------------------------------------------------------------
 // Entry points between translation units
 // ---------------------------------------------------------------------------
@@ -216,6 +247,7 @@ int green_split_bf16(vie_handle* h);            // zpass_bf16.cu: greenbf from g
 int twiddle_setup(vie_handle* h);               // matvec.cu
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);
+int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s);  // z-pass autotuner, outside capture
 
 // Support of a solve: per (z, y) row of the grid the voxel interval [x0, x1) whose
 // unknowns are kept and the offset of voxel (x0, y, z) within a component block of ns
@@ -232,12 +264,12 @@ struct Support {
 // (the shifted operator of the solver's Arnoldi steps).
 // conv (optional): full-grid [nrhs][12][nz][ny][nx] output of the convolution (N - G) x at
 // every voxel, support or not (the operator's value before its voxel-wise terms).
-// rmap, nact (optional, device list of nact < nrhs right-hand sides): compute y only for the
-// listed right-hand sides, leaving the others' y untouched (used on the fused xy path; the
-// other paths compute all of them).
+// rmap, nact (optional, device memory): compute y only for the *nact right-hand sides listed in
+// rmap, leaving the others' y untouched; the launches are sized for nrhs and skip the rest on the
+// device, so no host round trip is needed (fused xy path; the other paths compute all of them).
 int matvec_support(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, const Support& sp,
                    void* tmp, cudaStream_t s, const double2* shift = nullptr, void* conv = nullptr,
-                   const int* rmap = nullptr, int nact = 0);
+                   const int* rmap = nullptr, const int* nact = nullptr);
 // full-grid vector <-> vector on a support (values outside the support dropped / set to zero)
 int support_gather(const vie_handle* h, int nrhs, const void* full, void* part, int precision, const Support& sp,
                    cudaStream_t s);

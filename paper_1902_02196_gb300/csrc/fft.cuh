@@ -141,6 +141,11 @@ struct MatvecEpi {
     const double2* shift;  // op PA only, optional: y -= shift[r] x per right-hand side r
     void* conv;            // optional: full-grid (N - G) x at every voxel, before the voxel-wise terms
     const int* rmap;       // optional (fused xy path): spectrum right-hand side k holds right-hand side rmap[k]
+    // optional with rmap: the number of listed right-hand sides kept on the device (planes of the
+    // others are skipped); the launch's algorithmic bytes bfix + bper * count go to *bctr
+    const int* nact;
+    unsigned long long* bctr;
+    double bfix, bper;
 };
 
 template <int L>

@@ -25,6 +25,8 @@
 #include "zpass_f64.cuh"
 
 int zpass_bf16_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s);  // zpass_bf16.cu
+int zpass_bf16_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s);   // zpass_bf16.cu
+int zpass_f32_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s);    // zpass_f32.cu
 
 // y[12] = B(k) x[12] at one frequency point; xv/acc in registers, Green values streamed once.
 template <typename C>
@@ -162,7 +164,7 @@ template <int L, typename C>
 __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     xy_fwd_kernel(const C* __restrict__ x, C* __restrict__ w, int nx, int ny, int nz, const int4* __restrict__ rows,
                   long long ns, const unsigned char* __restrict__ cpos, const C* __restrict__ twg,
-                  const int* __restrict__ rmap) {
+                  const int* __restrict__ rmap, MatvecEpi dc) {
     using Cfg = XYCfg<L, C>;
     constexpr int A = fft2::Split<L>::A, B = fft2::Split<L>::B, NT = kXYThreads, RS = Cfg::RS, CW = Cfg::CW;
     constexpr int EPV = Cfg::EPV;
@@ -173,11 +175,16 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     int4* rw = reinterpret_cast<int4*>(tw + L);  // [H] support rows of this plane
     unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
+    const long long p = blockIdx.x;  // spectrum plane; the input plane is pin (rmap: active right-hand sides)
+    if (dc.nact) {  // planes of right-hand sides beyond the device count are skipped
+        const int cnt = *dc.nact;
+        dev_bytes_add(dc.bctr, dc.bfix + dc.bper * cnt, cnt > 0);
+        if (p / (12LL * nz) >= cnt) return;
+    }
     for (int m = tid; m < L; m += NT) {
         tw[m] = twg[m];
         pos[m] = cpos[m];
     }
-    const long long p = blockIdx.x;  // spectrum plane; the input plane is pin (rmap: active right-hand sides)
     const long long pin = rmap ? (long long)rmap[p / (12LL * nz)] * 12 * nz + p % (12LL * nz) : p;
     if (rows) {
         const int z = (int)(p % nz);
@@ -255,12 +262,17 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     int4* rw = reinterpret_cast<int4*>(tw + L);
     unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
+    const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
+    const long long p = blockIdx.x;  // spectrum plane (r * 12 + alpha) * nz + z; output plane po
+    if (epi.nact) {
+        const int cnt = *epi.nact;
+        dev_bytes_add(epi.bctr, epi.bfix + epi.bper * cnt, cnt > 0);
+        if (p / (12LL * nz) >= cnt) return;
+    }
     for (int m = tid; m < L; m += NT) {
         tw[m] = twg[m];
         pos[m] = cpos[m];
     }
-    const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
-    const long long p = blockIdx.x;  // spectrum plane (r * 12 + alpha) * nz + z; output plane po
     const long long po = epi.rmap ? (long long)epi.rmap[p / (12LL * nz)] * 12 * nz + p % (12LL * nz) : p;
     if (epi.rows)
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = epi.rows[(p % nz) * ny + yy];
@@ -482,25 +494,46 @@ static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out,
     const unsigned char* cpos = h->colmap + L;
     const C* tw = reinterpret_cast<const C*>(f32 ? (const void*)(h->tw32 + L) : (const void*)(h->tw64 + L));
     const double c = sizeof(C), plane_full = (double)L * L;
-    if (fwd)
-        VIE_KLAUNCH_B(f32 ? "fft_xy_f32" : "fft_xy_f64", s, c * (in_elems + planes * plane_full),
+    // with a device count of right-hand sides (e.nact) the kernel adds its bytes on the device:
+    // the part proportional to the planes transformed, per right-hand side of the grid, plus a fixed part
+    const double rg = (double)planes / (12.0 * h->nz);  // right-hand sides of the launch grid
+    MatvecEpi ee = e;
+    if (fwd) {
+        const char* name = f32 ? "fft_xy_f32" : "fft_xy_f64";
+        double bytes = c * (in_elems + planes * plane_full);
+        if (e.nact) {
+            ee.bctr = dev_bytes_ptr(name);
+            ee.bfix = 0.0;
+            ee.bper = bytes / rg;
+            bytes = kDevCounted;
+        }
+        VIE_KLAUNCH_B(name, s, bytes,
                       xy_fwd_kernel<L, C><<<(unsigned)planes, kXYThreads, smem, s>>>(
-                          (const C*)in, (C*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, tw, e.rmap));
-    else {
-        const double bytes = c * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
-                                  (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0) +
-                                  (e.conv ? (double)planes * nx * ny : 0.0));
+                          (const C*)in, (C*)out, nx, ny, h->nz, sp.rows, sp.ns, cpos, tw, e.rmap, ee));
+    } else {
+        const double fixed = c * (double)h->nv * (e.op == VIE_OP_PA ? 2 : e.op == VIE_OP_A ? 1 : 0);
+        const double per = c * (planes * plane_full + in_elems * (e.op == VIE_OP_NSCAT ? 1 : 2) +
+                                (e.conv ? (double)planes * nx * ny : 0.0));
+        double bytes = fixed + per;
+        const bool conv64 = sizeof(C) == 16 && e.conv;
+        const char* name = f32 ? "ifft_xy_epilogue_f32" : "ifft_xy_epilogue_f64";
+        if (e.nact) {
+            ee.bctr = dev_bytes_ptr(name);
+            ee.bfix = fixed;
+            ee.bper = per / rg;
+            bytes = kDevCounted;
+        }
         if constexpr (sizeof(C) == 16) {
-            if (e.conv) {
-                VIE_KLAUNCH_B("ifft_xy_epilogue_f64", s, bytes,
+            if (conv64) {
+                VIE_KLAUNCH_B(name, s, bytes,
                               xy_inv_kernel<L, C, true><<<(unsigned)planes, kXYThreads, smem, s>>>(
-                                  (const C*)in, (C*)out, e, cpos, tw));
+                                  (const C*)in, (C*)out, ee, cpos, tw));
                 VIE_CHECK_LAUNCH();
                 return VIE_OK;
             }
         }
-        VIE_KLAUNCH_B(f32 ? "ifft_xy_epilogue_f32" : "ifft_xy_epilogue_f64", s, bytes,
-                      xy_inv_kernel<L, C, false><<<(unsigned)planes, kXYThreads, smem, s>>>((const C*)in, (C*)out, e,
+        VIE_KLAUNCH_B(name, s, bytes,
+                      xy_inv_kernel<L, C, false><<<(unsigned)planes, kXYThreads, smem, s>>>((const C*)in, (C*)out, ee,
                                                                                            cpos, tw));
     }
     VIE_CHECK_LAUNCH();
@@ -537,12 +570,14 @@ size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
 template <typename T>
 static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cudaStream_t s, void* ws,
                        const Support& sp = Support{}, const double2* shift = nullptr, void* conv = nullptr,
-                       const int* rmap = nullptr, int nact = 0, bool bf16 = false) {
+                       const int* rmap = nullptr, const int* nact = nullptr, bool bf16 = false) {
     using C = typename CT<T>::C;
     const int nx = h->nx, ny = h->ny, nz = h->nz, Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
-    // rmap (fused xy path only): transform only the nact right-hand sides it lists
-    if (!xy_ok(h) || nact <= 0 || nact >= R) rmap = nullptr;
-    const int Rs = rmap ? nact : R;  // right-hand sides in the spectrum
+    // rmap with its device count nact (fused xy path only): transform only the *nact right-hand
+    // sides it lists; the launches are sized for all R and skip the rest on the device
+    if (!xy_ok(h) || !nact) rmap = nullptr;
+    if (!rmap) nact = nullptr;
+    const int Rs = R;  // right-hand sides the spectrum has room for
     const long long comps = (long long)Rs * 12 * nz;
     // W1 exists on the line-transform path only (matvec_workspace_bytes)
     C* W1 = reinterpret_cast<C*>(ws);
@@ -566,9 +601,11 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     e.shift = op == VIE_OP_PA ? shift : nullptr;
     e.conv = conv;
     e.rmap = rmap;
+    e.nact = nact;
     MatvecEpi noepi{};
-    MatvecEpi fwdmap{};  // the forward kernel reads only rmap
+    MatvecEpi fwdmap{};  // the forward kernel reads only rmap and the count
     fwdmap.rmap = rmap;
+    fwdmap.nact = nact;
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
@@ -581,6 +618,8 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
             z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            z.nact = nact;
+            z.bctr = nact ? dev_bytes_ptr(bf16 ? "zpass_block_bf16x3" : "zpass_block_f32") : nullptr;
             if (bf16) return zpass_bf16_fused(h, z, s);
             return zpass_f32_fused(h, z, s);
         }
@@ -597,6 +636,8 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
             z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
             z.ay = ay, z.by = by;
             z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            z.nact = nact;
+            z.bctr = nact ? dev_bytes_ptr("zpass_block_f64") : nullptr;
             return zpass_f64_fused(h, z, s);
         }
         ZArgs z{};
@@ -668,11 +709,27 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     return VIE_OK;
 }
 
+// Runs the z-pass autotuner for nrhs right-hand sides of this precision now (outside any stream
+// capture), so that a CUDA graph captured later launches the tuned tile width.
+int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s) {
+    if (precision == VIE_FP64 || !zfused_ok(h)) return VIE_OK;
+    ZFArgs z{};
+    z.w = nullptr;
+    z.green_t = h->green32t;
+    z.colkx = h->colkx32;
+    z.R = nrhs, z.nz = h->nz, z.Lx = h->L[0], z.Ly = h->L[1];
+    z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+    const int ay = xy_ok(h) ? fft2::split_a(h->L[1]) : 1, by = xy_ok(h) ? h->L[1] / fft2::split_a(h->L[1]) : h->L[1];
+    z.ay = ay, z.by = by;
+    z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+    return precision == VIE_BF16X3 ? zpass_bf16_tune(h, z, s) : zpass_f32_tune(h, z, s);
+}
+
 static int matvec_full(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s,
                        void* conv) {
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, nrhs, precision)));
     if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv);
-    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv, nullptr, 0,
+    return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv, nullptr, nullptr,
                               precision == VIE_BF16X3);
 }
 
@@ -750,7 +807,7 @@ __global__ void shift_sub_kernel(C* __restrict__ y, const C* __restrict__ x, con
 }
 
 int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, int op, const Support& sp, void* tmp,
-                   cudaStream_t s, const double2* shift, void* conv, const int* rmap, int nact) {
+                   cudaStream_t s, const double2* shift, void* conv, const int* rmap, const int* nact) {
     if (op != VIE_OP_PA) shift = nullptr;
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, precision)));
     if (xy_ok(h) || !sp.rows)

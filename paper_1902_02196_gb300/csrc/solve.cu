@@ -638,9 +638,34 @@ int build_support(vie_handle* h, int R, const double2* b, const double2* guess, 
     return VIE_OK;
 }
 
+// Arnoldi steps per chunk of a cycle (run_cycle), and chunks at most (restart <= 128)
+constexpr int kChunk = 8;
+constexpr int kMaxChunks = (kMaxV + kChunk - 1) / kChunk;
+
+// A captured piece of a GMRES cycle (run_cycle) and the launch records of its kernels.
+struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<CapRec> recs;
+    bool replayed = false;  // replayed since its device times were last harvested
+    ~CycleGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        stats_capture_release(recs);
+    }
+};
+
 struct Solver {
     vie_handle* h;
-    cudaStream_t st;
+    cudaStream_t st = nullptr;
+    bool use_graph = false;
+    // per matvec precision (VIE_FP64, VIE_FP32, VIE_BF16X3): the chunks of a cycle, then its end
+    CycleGraph graph[3][kMaxChunks + 1];
+    int* pinned = nullptr;                // [kMaxChunks] active counts after each chunk (pinned host memory)
+    cudaEvent_t chunk_ev[kMaxChunks] = {};  // end of each queued chunk
+    ~Solver() {  // nothing of this solve may still run when its graphs and events go
+        if (st) cudaStreamSynchronize(st);
+        for (auto& e : chunk_ev)
+            if (e) cudaEventDestroy(e);
+    }
     int R, m;
     long long n;
     int nblk;
@@ -687,31 +712,31 @@ struct Solver {
     }
 };
 
-// One GMRES(m) cycle from the residual r64 (squared norms rn2); x64 += V y.  *still = number
-// of right-hand sides that ended the cycle above their target.
+// Arnoldi steps [j0, j1) of a GMRES(m) cycle from the residual r64 (squared norms rn2), enqueued
+// on the stream with no host read inside: every step works on the device's list of active
+// right-hand sides (count_active before each step), so a step after every right-hand side has
+// stopped finds an empty list and its kernels return at once.  The first chunk starts the cycle;
+// every chunk ends by counting the right-hand sides still active.
 template <typename VC>
-int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* rn2, int precision, int* it_rhs,
-              int* mv_count, int* host_i, int* still) {
+int enqueue_steps(Solver& S, VC* U, const double2* r64, const double* rn2, int precision, int j0, int j1) {
     vie_handle* h = S.h;
-    const int R = S.R, m = S.m;
+    const int R = S.R;
     const long long n = S.n, ustride = (long long)R * n;
     cudaStream_t st = S.st;
-    VIE_KLAUNCH("cycle_init", st, cycle_init_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R, rn2));
-    const dim3 ge((unsigned)((n + 255) / 256), R);
-    VIE_KLAUNCH("basis_init", st, scale_from64_kernel<VC><<<ge, 256, 0, st>>>(r64, U, n, S.gs.scale));
-    VIE_CHECK_LAUNCH();
     const unsigned gr = (unsigned)((R + 127) / 128);
-    for (int j = 0; j < m; ++j) {
+    if (j0 == 0) {
+        VIE_KLAUNCH("cycle_init", st, cycle_init_kernel<<<(R + 127) / 128, 128, 0, st>>>(S.gs, R, rn2));
+        const dim3 ge((unsigned)((n + 255) / 256), R);
+        VIE_KLAUNCH("basis_init", st, scale_from64_kernel<VC><<<ge, 256, 0, st>>>(r64, U, n, S.gs.scale));
+        VIE_CHECK_LAUNCH();
+    }
+    for (int j = j0; j < j1; ++j) {
         VIE_KLAUNCH("count_active", st, count_active_kernel<<<1, 1, 0, st>>>(S.gs.active, R, S.gs.nactive));
-        VIE_CUDA(cudaMemcpyAsync(host_i, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
-        VIE_CUDA(cudaStreamSynchronize(st));
-        if (*host_i == 0) break;
         VC* uj = U + j * ustride;
         VC* w = U + (j + 1) * ustride;
         // only the active right-hand sides (the others' w is never read)
         VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift, nullptr,
-                               S.gs.nactive + 1, *host_i));
-        ++*mv_count;
+                               S.gs.nactive + 1, S.gs.nactive));
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
         VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<R, 128, 0, st>>>(S.gs, R, j));
         VIE_TRY(S.update<VC>(U, ustride, w, j + 1, S.gs.active));
@@ -722,18 +747,107 @@ int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* 
         VIE_KLAUNCH("givens", st, givens_kernel<<<gr, 128, 0, st>>>(S.gs, R, j));
         VIE_CHECK_LAUNCH();
     }
+    VIE_KLAUNCH("count_active", st, count_active_kernel<<<1, 1, 0, st>>>(S.gs.active, R, S.gs.nactive));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+// end of a cycle: H y = g, x64 += V y
+template <typename VC>
+int enqueue_finish(Solver& S, VC* U, double2* x64) {
+    const int R = S.R, m = S.m;
+    const long long n = S.n, ustride = (long long)R * n;
+    cudaStream_t st = S.st;
+    const unsigned gr = (unsigned)((R + 127) / 128);
     VIE_KLAUNCH("trisolve", st, trisolve_kernel<<<gr, 128, 0, st>>>(S.gs, R));
     const dim3 gx((unsigned)((n + kThreads * Prec<VC>::K - 1) / (kThreads * Prec<VC>::K)), R);
     VIE_KLAUNCH("solution_update", st,
                 xupdate_kernel<VC><<<gx, kThreads, 0, st>>>(U, ustride, x64, n, S.gs.y, m, S.gs.k, 0));
-    VIE_KLAUNCH("count_active", st, count_active_kernel<<<1, 1, 0, st>>>(S.gs.active, R, S.gs.nactive));
     VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+// Runs `enqueue` on the stream: directly, or (S.use_graph) by replaying the CUDA graph G, which
+// is captured from `enqueue` on first use (the buffers it touches stay the same for the solve).
+template <class F>
+int run_graph(Solver& S, CycleGraph& G, F enqueue) {
+    cudaStream_t st = S.st;
+    if (!S.use_graph) return enqueue();
+    if (!G.exec) {
+        cudaGraph_t graph = nullptr;
+        VIE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+        stats_capture_begin(&G.recs);
+        const int rc = enqueue();
+        stats_capture_end();
+        const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+        if (rc < 0 || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (rc < 0) return rc;
+            set_error(std::string("cycle graph capture failed: ") + cudaGetErrorString(ec));
+            return VIE_EDEVICE;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            G.exec = nullptr;
+            set_error(std::string("cycle graph instantiation failed: ") + cudaGetErrorString(ei));
+            return VIE_EDEVICE;
+        }
+    }
+    VIE_CUDA(cudaGraphLaunch(G.exec, st));
+    stats_graph_replayed(G.recs);
+    G.replayed = true;
+    return VIE_OK;
+}
+
+// One GMRES(m) cycle from r64: the Arnoldi steps in chunks of kChunk, each (with S.use_graph) a
+// CUDA graph replayed every cycle.  The host keeps one chunk queued ahead of the one it waits
+// for, and stops queueing once a finished chunk left no right-hand side active, so the GPU does
+// not wait for the host and at most one chunk of empty steps runs after the last right-hand side
+// stops.  Then x64 += V y and the host reads each right-hand side's step count k.
+// *still = number of right-hand sides that ended the cycle above their target.
+template <typename VC>
+int run_cycle(Solver& S, VC* U, double2* x64, const double2* r64, const double* rn2, int precision, int* it_rhs,
+              int* mv_count, int* still) {
+    const int R = S.R, m = S.m;
+    cudaStream_t st = S.st;
+    const int nch = (m + kChunk - 1) / kChunk;
+    CycleGraph* G = S.graph[precision];
+    int queued = 0;
+    auto queue = [&](int c) -> int {
+        const int j0 = c * kChunk, j1 = std::min(m, j0 + kChunk);
+        VIE_TRY(run_graph(S, G[c], [&] { return enqueue_steps<VC>(S, U, r64, rn2, precision, j0, j1); }));
+        VIE_CUDA(cudaMemcpyAsync(S.pinned + c, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VIE_CUDA(cudaEventRecord(S.chunk_ev[c], st));
+        ++queued;
+        return VIE_OK;
+    };
+    VIE_TRY(queue(0));
+    for (int c = 0; c < nch; ++c) {
+        if (queued < nch && queued == c + 1) VIE_TRY(queue(c + 1));  // keep one chunk ahead
+        VIE_CUDA(cudaEventSynchronize(S.chunk_ev[c]));
+        if (S.pinned[c] == 0) break;  // every right-hand side stopped in chunk c (or before)
+    }
+    VIE_TRY(run_graph(S, G[kMaxChunks], [&] { return enqueue_finish<VC>(S, U, x64); }));
     std::vector<int> k(R);
+    int act = 0;
     VIE_CUDA(cudaMemcpyAsync(k.data(), S.gs.k, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-    VIE_CUDA(cudaMemcpyAsync(host_i, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VIE_CUDA(cudaMemcpyAsync(&act, S.gs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     VIE_CUDA(cudaStreamSynchronize(st));
-    for (int r = 0; r < R; ++r) it_rhs[r] += k[r];
-    *still = *host_i;
+    if (S.use_graph)
+        for (int c = 0; c <= kMaxChunks; ++c)
+            if (G[c].replayed) {
+                stats_graph_harvest(G[c].recs);
+                G[c].replayed = false;
+            }
+    int kmax = 0;
+    for (int r = 0; r < R; ++r) {
+        it_rhs[r] += k[r];
+        kmax = std::max(kmax, k[r]);
+    }
+    *mv_count += kmax;  // matvecs that transformed at least one right-hand side
+    *still = act;
     return VIE_OK;
 }
 
@@ -828,6 +942,15 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     Solver S;
     S.h = h;
     S.st = st;
+    // CUDA graphs for the cycles unless flags bit 3 asks for direct launches; the legacy and
+    // per-thread default streams cannot be captured
+    S.use_graph = !(flags & 8) && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    // the largest spectrum scratch any matvec of this solve takes (FP64), reserved before the
+    // first cycle is captured so that no later reservation moves the buffer under the graph
+    VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, VIE_FP64)));
+    dev_bytes_ptr("zpass_block_f32");  // looks the counters' address up outside any capture
+    if (mode == VIE_SOLVE_FP32_REFINE) VIE_TRY(matvec_tune(h, R, VIE_FP32, st));
+    if (mode == VIE_SOLVE_BF16X3_REFINE) VIE_TRY(matvec_tune(h, R, VIE_BF16X3, st));
     S.R = R;
     S.m = m;
     S.n = n;
@@ -867,12 +990,16 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     int* done = reinterpret_cast<int*>(base + oDone);
     double* rel = reinterpret_cast<double*>(base + oRel);
     int* k1 = reinterpret_cast<int*>(base + oK1);
-    int* pinned = nullptr;
-    VIE_CUDA(cudaMallocHost(&pinned, sizeof(int) * 4));
+    VIE_CUDA(cudaMallocHost(&S.pinned, sizeof(int) * kMaxChunks));
     struct PinGuard {
         int* p;
-        ~PinGuard() { cudaFreeHost(p); }
-    } guard{pinned};
+        cudaStream_t s;
+        ~PinGuard() {  // after the copies into it have finished
+            cudaStreamSynchronize(s);
+            cudaFreeHost(p);
+        }
+    } guard{S.pinned, st};
+    for (auto& e : S.chunk_ev) VIE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
     const long long total = (long long)R * n, total_full = (long long)R * nfull;
     const unsigned gt = (unsigned)((total + 255) / 256);
@@ -1017,7 +1144,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             float2* U32 = reinterpret_cast<float2*>(base + oU);
             for (;;) {
                 int still = 0;
-                VIE_TRY(run_cycle<float2>(S, U32, xs, r64, rn2, inner, it_rhs.data(), &mv32, pinned, &still));
+                VIE_TRY(run_cycle<float2>(S, U32, xs, r64, rn2, inner, it_rhs.data(), &mv32, &still));
                 ++cyc;
                 x_is_zero = false;
                 if (still == 0 || cyc >= maxit) break;
@@ -1026,7 +1153,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         } else {
             int still = 0;
             VIE_TRY(run_cycle<double2>(S, reinterpret_cast<double2*>(base + oU), xs, r64, rn2, VIE_FP64,
-                                       it_rhs.data(), &mv64, pinned, &still));
+                                       it_rhs.data(), &mv64, &still));
             ++cyc;
             x_is_zero = false;
         }

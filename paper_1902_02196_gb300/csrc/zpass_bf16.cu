@@ -24,13 +24,14 @@
 
 #include "block.cuh"
 #include "fft2.cuh"
+#include "autotune.h"
 #include "zpass_f32.cuh"
 
 namespace {
 
-template <int LZ>
+template <int LZ, int TB_>
 struct ZBCfg {
-    static constexpr int TB = LZ <= 256 ? 8 : 4;  // column lines per component: 2 columns x TB/2 right-hand sides
+    static constexpr int TB = TB_;  // column lines per component: 2 columns x TB/2 right-hand sides (8 or 4)
     static constexpr int RG = TB / 2;             // right-hand sides per group
     static constexpr int NT = 256;
     static constexpr int GS = LZ * TB + 4;  // component stride in float2, 4 mod 16
@@ -62,10 +63,10 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int LZ>
-__global__ void __launch_bounds__(256, ZBCfg<LZ>::MINB)
+template <int LZ, int TB_>
+__global__ void __launch_bounds__(256, ZBCfg<LZ, TB_>::MINB)
     zbf16_kernel(ZFArgs z, const uint2* __restrict__ gbf, const float2* __restrict__ twg) {
-    using Cfg = ZBCfg<LZ>;
+    using Cfg = ZBCfg<LZ, TB_>;
     constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = Cfg::NT, TB = Cfg::TB, RG = Cfg::RG;
     constexpr int GS = Cfg::GS;
     constexpr int NWARP = NT / 32;
@@ -73,6 +74,9 @@ __global__ void __launch_bounds__(256, ZBCfg<LZ>::MINB)
     float2* s = reinterpret_cast<float2*>(smem_raw);
     float2* tw = s + 12 * GS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int R = z.nact ? min(*z.nact, z.R) : z.R;
+    dev_bytes_add(z.bctr, 8.0 * (2.0 * R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz), R > 0);
+    if (R <= 0) return;
     for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
     const int npair = z.Lx / 2;
     const int py = blockIdx.x / npair, cp = blockIdx.x % npair, sc0 = 2 * cp;
@@ -110,11 +114,11 @@ __global__ void __launch_bounds__(256, ZBCfg<LZ>::MINB)
 
     auto line = [](int n) { return (n / TB) * GS + n % TB; };
 #pragma unroll 1
-    for (int rb = 0; rb < z.R; rb += RG) {
+    for (int rb = 0; rb < R; rb += RG) {
         // loads: slot pair (2 rr, 2 rr + 1) of component a, plane l = 16 contiguous bytes
         for (int idx = tid; idx < 12 * nz * RG; idx += NT) {
             const int rr = idx % RG, l = (idx / RG) % nz, a = idx / (RG * nz);
-            const bool in = rb + rr < z.R;
+            const bool in = rb + rr < R;
             const float2* src = in ? z.w + ((long long)(rb + rr) * 12 * nz + (long long)a * nz + l) * plane +
                                          (long long)py * z.Lx + sc0
                                    : z.w;
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(256, ZBCfg<LZ>::MINB)
         fft2::inverse<LZ, NT>(s, 12 * TB, line, TB, tw, nz);
         for (int idx = tid; idx < 12 * nz * RG; idx += NT) {
             const int rr = idx % RG, l = (idx / RG) % nz, a = idx / (RG * nz);
-            if (rb + rr >= z.R) continue;
+            if (rb + rr >= R) continue;
             float2* dst = z.w + ((long long)(rb + rr) * 12 * nz + (long long)a * nz + l) * plane + (long long)py * z.Lx + sc0;
             *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(s + a * GS + l * TB + 2 * rr);
         }
@@ -233,16 +237,39 @@ __global__ void __launch_bounds__(256, ZBCfg<LZ>::MINB)
     }
 }
 
-template <int LZ>
-int launch_zb_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
-    constexpr size_t smem = ZBCfg<LZ>::smem;
-    VIE_CUDA(cudaFuncSetAttribute(zbf16_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <int LZ, int TB>
+int launch_zb_LT(const vie_handle* h, const ZFArgs& z, cudaStream_t s, const char* name) {
+    using Cfg = ZBCfg<LZ, TB>;
+    constexpr size_t smem = Cfg::smem;
+    VIE_CUDA(cudaFuncSetAttribute(zbf16_kernel<LZ, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long blocks = (long long)z.Ly * (z.Lx / 2);
-    const double bytes = 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
-    VIE_KLAUNCH_B("zpass_block_bf16x3", s, bytes,
-                  zbf16_kernel<LZ><<<(unsigned)blocks, ZBCfg<LZ>::NT, smem, s>>>(z, h->greenbf, h->tw32 + LZ));
+    const double bytes = z.nact ? kDevCounted : 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
+    VIE_KLAUNCH_B(name, s, bytes,
+                  zbf16_kernel<LZ, TB><<<(unsigned)blocks, Cfg::NT, smem, s>>>(z, h->greenbf, h->tw32 + LZ));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
+}
+
+int launch_zb(const vie_handle* h, const ZFArgs& z, cudaStream_t s, int tb, const char* name) {
+#define VIE_ZB(L)                                              \
+    case L:                                                    \
+        if (tb == 8) return launch_zb_LT<L, 8>(h, z, s, name); \
+        if (tb == 4) return launch_zb_LT<L, 4>(h, z, s, name); \
+        break;
+    switch (h->L[2]) {
+        VIE_ZB(8)
+        VIE_ZB(16)
+        VIE_ZB(32)
+        VIE_ZB(64)
+        VIE_ZB(128)
+        VIE_ZB(256)
+        case 512:
+            if (tb == 4) return launch_zb_LT<512, 4>(h, z, s, name);
+            break;
+    }
+#undef VIE_ZB
+    set_error("z pass: unsupported length or tile width");
+    return VIE_EINVAL;
 }
 
 // bf16 (hi, lo) pairs of the FP32 octant tensors in the [Oy][Ox][Oz][60] layout
@@ -264,20 +291,28 @@ int green_split_bf16(vie_handle* h) {
     return VIE_OK;
 }
 
+// tile rows: 4 right-hand sides x 2 columns x 2 kz positions (TB = 8), or 2 x 2 x 2 in half a tile
+// (TB = 4); the width for this launch is measured on first use of the shape (autotune.h)
+static int zb_pick(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    int tb[2], n = 0;
+    if (h->L[2] <= 256) tb[n++] = 8;
+    tb[n++] = 4;
+    const int key[5] = {1, h->L[2], z.Lx, z.Ly, z.nz};
+    const int pick = autotune_pick(key, n, s, [&](int c, cudaStream_t ts, const ZFArgs& zt) {
+        return launch_zb(h, zt, ts, tb[c], "autotune_zpass_bf16x3");
+    }, z, [&](int c) { return "TB=" + std::to_string(tb[c]); });
+    return tb[pick];
+}
+
 int zpass_bf16_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
     if (!h->greenbf) {
         set_error("internal: no bf16 Green tensors");
         return VIE_EINVAL;
     }
-    switch (h->L[2]) {
-        case 8: return launch_zb_L<8>(h, z, s);
-        case 16: return launch_zb_L<16>(h, z, s);
-        case 32: return launch_zb_L<32>(h, z, s);
-        case 64: return launch_zb_L<64>(h, z, s);
-        case 128: return launch_zb_L<128>(h, z, s);
-        case 256: return launch_zb_L<256>(h, z, s);
-        case 512: return launch_zb_L<512>(h, z, s);
-    }
-    set_error("z pass: unsupported length");
-    return VIE_EINVAL;
+    return launch_zb(h, z, s, zb_pick(h, z, s), "zpass_block_bf16x3");
+}
+
+int zpass_bf16_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    zb_pick(h, z, s);
+    return VIE_OK;
 }

@@ -2,6 +2,7 @@
 // between the forward and inverse z transforms, on the spectrum left by xy_fwd_kernel.
 #include "block.cuh"
 #include "fft2.cuh"
+#include "autotune.h"
 #include "zpass_f32.cuh"
 
 // ---------------------------------------------------------------------------
@@ -17,18 +18,19 @@
 // kz = 0 with kz = Lz/2 keeps the second point's values in shared memory; the last
 // tile's self-mirrored columns 0 and Lx/2 reload theirs for each right-hand side.
 // ---------------------------------------------------------------------------
-// Tiles of TB stored columns (TB / 2 mirror pairs): 4 for Lz <= 128, 2 for Lz = 256, 512.
-// One thread per (pair, kz item): NT = max(TB/2 * Lz/2, 128); two CTAs per SM when NT = 128.
-template <int LZ>
+// Tiles of TB stored columns (TB / 2 mirror pairs): 4 or 8 for Lz <= 128, 2 or 4 for Lz = 256,
+// 2 for Lz = 512 (the autotuner below picks one per grid).  One thread per (pair, kz item):
+// NT = max(TB/2 * Lz/2, 128); two CTAs per SM when NT = 128 and the two buffers fit twice.
+template <int LZ, int TB_>
 struct ZFCfg {
-    static constexpr int TB = LZ <= 128 ? 4 : 2;
+    static constexpr int TB = TB_;
     static constexpr int NPAIR = TB / 2;
     static constexpr int NT0 = NPAIR * LZ / 2;
     static constexpr int NT = NT0 < 128 ? 128 : NT0;
-    static constexpr int MINB = NT == 128 ? 2 : 1;
     static constexpr int GS = LZ * TB + TB;  // component stride: TB float2 of padding keep half-warps apart
     static constexpr int BUF = 12 * GS;
-    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 4 * 60);
+    static constexpr size_t smem = sizeof(float2) * (size_t)(2 * BUF + LZ + 2 * NPAIR * 60);
+    static constexpr int MINB = (NT == 128 && smem <= 113 * 1024) ? 2 : 1;
 };
 
 // the 60 Green values of one octant point, streamed from the [..][60] layout
@@ -78,16 +80,20 @@ __device__ __forceinline__ void col_point2(const float2* u, float2* s, int gs, i
         s[a * gs + off] = xflip(make_float2(a1[a].x - a2[a].y, a1[a].y + a2[a].x), sign_bit(m, a));
 }
 
-template <int LZ>
-__global__ void __launch_bounds__(ZFCfg<LZ>::NT, ZFCfg<LZ>::MINB) zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
-    using Cfg = ZFCfg<LZ>;
+template <int LZ, int TB_>
+__global__ void __launch_bounds__(ZFCfg<LZ, TB_>::NT, ZFCfg<LZ, TB_>::MINB)
+    zfused_kernel(ZFArgs z, const float2* __restrict__ twg) {
+    using Cfg = ZFCfg<LZ, TB_>;
     constexpr int A = fft2::Split<LZ>::A, B = fft2::Split<LZ>::B, NT = Cfg::NT, TB = Cfg::TB;
     constexpr int NPAIR = Cfg::NPAIR, GS = Cfg::GS, BUF = Cfg::BUF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sb = reinterpret_cast<float2*>(smem_raw);
     float2* tw = sb + 2 * BUF;
-    float2* gsec = tw + LZ;  // [2 pairs][2 sets][60] Green values of the item that holds kz = LZ/2
+    float2* gsec = tw + LZ;  // [NPAIR pairs][2 sets][60] Green values of the item that holds kz = LZ/2
     const int tid = threadIdx.x;
+    const int R = z.nact ? min(*z.nact, z.R) : z.R;
+    dev_bytes_add(z.bctr, 8.0 * (2.0 * R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz), R > 0);
+    if (R <= 0) return;
     for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
     const int ntile = z.Lx / TB;
     const int py = blockIdx.x / ntile, ct = blockIdx.x % ntile, sc0 = ct * TB;
@@ -154,9 +160,9 @@ __global__ void __launch_bounds__(ZFCfg<LZ>::NT, ZFCfg<LZ>::MINB) zfused_kernel(
 
     issue(0, sb);
 #pragma unroll 1
-    for (int r = 0; r < z.R; ++r) {
+    for (int r = 0; r < R; ++r) {
         float2* s = sb + (r & 1) * BUF;
-        if (r + 1 < z.R) {
+        if (r + 1 < R) {
             issue(r + 1, sb + ((r + 1) & 1) * BUF);
             cp_async_wait<1>();
         } else {
@@ -201,30 +207,77 @@ __global__ void __launch_bounds__(ZFCfg<LZ>::NT, ZFCfg<LZ>::MINB) zfused_kernel(
     }
 }
 
-template <int LZ>
-static int launch_zf_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
-    constexpr size_t smem = ZFCfg<LZ>::smem;
+template <int LZ, int TB>
+static int launch_zf_LT(const vie_handle* h, const ZFArgs& z, cudaStream_t s, const char* name) {
+    using Cfg = ZFCfg<LZ, TB>;
+    constexpr size_t smem = Cfg::smem;
     // set on every call: the attribute is per device and launches may come from several threads
-    VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long blocks = (long long)z.Ly * (z.Lx / ZFCfg<LZ>::TB);
-    const double bytes = 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
-    VIE_KLAUNCH_B("zpass_block_f32", s, bytes,
-                  zfused_kernel<LZ><<<(unsigned)blocks, ZFCfg<LZ>::NT, smem, s>>>(z, h->tw32 + LZ));
+    VIE_CUDA(cudaFuncSetAttribute(zfused_kernel<LZ, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long blocks = (long long)z.Ly * (z.Lx / TB);
+    // with a device count the kernel adds its bytes to z.bctr
+    const double bytes = z.nact ? kDevCounted : 8.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
+    VIE_KLAUNCH_B(name, s, bytes, zfused_kernel<LZ, TB><<<(unsigned)blocks, Cfg::NT, smem, s>>>(z, h->tw32 + LZ));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
 
-int zpass_f32_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+// tile widths the kernel is built for at each Lz (the first is the default)
+static int zf_candidates(int Lz, int Lx, int* tb) {
+    int n = 0;
+    if (Lz <= 128) {
+        tb[n++] = 4;
+        if (Lx >= 8) tb[n++] = 8;
+    } else if (Lz == 256) {
+        tb[n++] = 2;
+        tb[n++] = 4;
+    } else {
+        tb[n++] = 2;
+    }
+    return n;
+}
+
+template <int L>
+static int launch_zf_L(const vie_handle* h, const ZFArgs& z, cudaStream_t s, int tb, const char* name) {
+    if constexpr (L >= 256)
+        if (tb == 2) return launch_zf_LT<L, 2>(h, z, s, name);
+    if constexpr (L <= 256)
+        if (tb == 4) return launch_zf_LT<L, 4>(h, z, s, name);
+    if constexpr (L <= 128)
+        if (tb == 8) return launch_zf_LT<L, 8>(h, z, s, name);
+    set_error("z pass: unsupported tile width");
+    return VIE_EINVAL;
+}
+
+static int launch_zf(const vie_handle* h, const ZFArgs& z, cudaStream_t s, int tb, const char* name) {
     switch (h->L[2]) {
-        case 8: return launch_zf_L<8>(h, z, s);
-        case 16: return launch_zf_L<16>(h, z, s);
-        case 32: return launch_zf_L<32>(h, z, s);
-        case 64: return launch_zf_L<64>(h, z, s);
-        case 128: return launch_zf_L<128>(h, z, s);
-        case 256: return launch_zf_L<256>(h, z, s);
-        case 512: return launch_zf_L<512>(h, z, s);
+        case 8: return launch_zf_L<8>(h, z, s, tb, name);
+        case 16: return launch_zf_L<16>(h, z, s, tb, name);
+        case 32: return launch_zf_L<32>(h, z, s, tb, name);
+        case 64: return launch_zf_L<64>(h, z, s, tb, name);
+        case 128: return launch_zf_L<128>(h, z, s, tb, name);
+        case 256: return launch_zf_L<256>(h, z, s, tb, name);
+        case 512: return launch_zf_L<512>(h, z, s, tb, name);
     }
     set_error("z pass: unsupported length");
     return VIE_EINVAL;
 }
 
+// the tile width for this launch (measured on first use of the shape, see autotune.h)
+static int zf_pick(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    int tb[4];
+    const int n = zf_candidates(h->L[2], z.Lx, tb);
+    const int key[5] = {0, h->L[2], z.Lx, z.Ly, z.nz};
+    const int pick = autotune_pick(key, n, s, [&](int c, cudaStream_t ts, const ZFArgs& zt) {
+        return launch_zf(h, zt, ts, tb[c], "autotune_zpass_f32");
+    }, z, [&](int c) { return "TB=" + std::to_string(tb[c]); });
+    return tb[pick];
+}
+
+int zpass_f32_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    return launch_zf(h, z, s, zf_pick(h, z, s), "zpass_block_f32");
+}
+
+int zpass_f32_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s) {
+    zf_pick(h, z, s);
+    return VIE_OK;
+}

@@ -10,6 +10,10 @@ struct ZFArgs {
     int R, nz, Lx, Ly, Ox, Oy, Oz;
     int ay, by;                   // split of Ly: row py holds ky = py / by + ay * (py % by)
     unsigned mx, my, mz;
+    // optional: right-hand sides transformed = min(*nact, R) (a count kept on the device), with
+    // the launch's algorithmic bytes added to *bctr
+    const int* nact;
+    unsigned long long* bctr;
 };
 
 // Launches the z pass (Lz in 8..512, Lx >= 4) on a spectrum whose row py holds

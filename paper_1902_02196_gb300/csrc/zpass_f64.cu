@@ -64,6 +64,9 @@ __global__ void __launch_bounds__(ZDCfg<LZ>::NT) zfused64_kernel(ZDArgs z, const
     double2* s = reinterpret_cast<double2*>(smem_raw);
     double2* tw = s + Cfg::BUF;
     const int tid = threadIdx.x;
+    const int R = z.nact ? min(*z.nact, z.R) : z.R;
+    dev_bytes_add(z.bctr, 16.0 * (2.0 * R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz), R > 0);
+    if (R <= 0) return;
     for (int m = tid; m < LZ; m += NT) tw[m] = twg[m];
     const int ntile = z.Lx / TB;
     const int py = blockIdx.x / ntile, ct = blockIdx.x % ntile, sc0 = ct * TB;
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(ZDCfg<LZ>::NT) zfused64_kernel(ZDArgs z, const
     const double2* gcol1 = z.green_t + ((long long)kyo * z.Ox + kxo1) * z.Oz * 60;
 
 #pragma unroll 1
-    for (int r = 0; r < z.R; ++r) {
+    for (int r = 0; r < R; ++r) {
         const double2* base = z.w + (long long)r * 12 * nz * plane + (long long)py * z.Lx + sc0;
         for (int idx = tid; idx < 12 * nz * TB; idx += NT) {
             const int c = idx % TB, l = (idx / TB) % nz, a = idx / (TB * nz);
@@ -143,7 +146,7 @@ int launch_zd_L(const vie_handle* h, const ZDArgs& z, cudaStream_t s) {
     // set on every call: the attribute is per device and launches may come from several threads
     VIE_CUDA(cudaFuncSetAttribute(zfused64_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const long long blocks = (long long)z.Ly * (z.Lx / ZDCfg<LZ>::TB);
-    const double bytes = 16.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
+    const double bytes = z.nact ? kDevCounted : 16.0 * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
     VIE_KLAUNCH_B("zpass_block_f64", s, bytes,
                   zfused64_kernel<LZ><<<(unsigned)blocks, ZDCfg<LZ>::NT, smem, s>>>(z, h->tw64 + LZ));
     VIE_CHECK_LAUNCH();

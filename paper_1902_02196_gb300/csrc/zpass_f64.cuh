@@ -10,6 +10,8 @@ struct ZDArgs {
     int R, nz, Lx, Ly, Ox, Oy, Oz;
     int ay, by;                // row py holds ky = py / by + ay * (py % by)
     unsigned mx, my, mz;
+    const int* nact;             // optional device count of the right-hand sides (as ZFArgs)
+    unsigned long long* bctr;
 };
 
 // Launches the FP64 z pass (Lz in 8..512, Lx >= 4).
