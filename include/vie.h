@@ -65,6 +65,9 @@ extern "C" {
 #define VIE_SOLVE_FP32_REFINE 1  /* FP32 inner GMRES inside FP64 iterative refinement */
 #define VIE_SOLVE_BF16X3_REFINE 2 /* as VIE_SOLVE_FP32_REFINE with the VIE_BF16X3 matvec in the inner GMRES */
 
+/* vie_setup flags */
+#define VIE_SETUP_PWC 1 /* piecewise-constant basis: 3 unknowns per voxel (Section V-A comparison) */
+
 typedef struct vie_handle vie_handle;
 
 typedef struct {
@@ -96,8 +99,15 @@ typedef struct {
  *   freq_hz       : frequency f > 0; omega = 2 pi f, k0 = omega / c0
  *   eps_real      : double[nz][ny][nx], eps' >= 1 (1 in air), host or device
  *   sigma         : double[nz][ny][nx], conductivity in S/m >= 0, host or device
- *   flags         : 0 (reserved)
+ *   flags         : 0, or VIE_SETUP_PWC for the piecewise-constant system (below)
  *   out           : receives the handle; release with vie_destroy
+ * VIE_SETUP_PWC: the comparison solver of Section V-A with one constant basis function per
+ * vector component and voxel (3 unknowns per voxel), whose Galerkin system is exactly the
+ * l = 1 sub-block of the PWL system (Eq. 19-22, 24, 33 with l = l' = 1).  Every vector of the
+ * handle is then [nrhs][3][nz][ny][nx] (component p = x, y, z), the block product is the 3 x 3
+ * block of the six (1,1) tensors, and the Gram entry of every component is DV.  vie_matvec
+ * (VIE_FP64, VIE_FP32; not VIE_BF16X3 or VIE_OP_K), vie_solve, vie_rhs_planewave,
+ * vie_rhs_dipoles and vie_fields accept it; the magnetic-field calls do not.
  * Synchronous.  Returns VIE_EINVAL on bad sizes/NaN, VIE_ENOMEM, VIE_EDEVICE.
  */
 int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma, int flags,

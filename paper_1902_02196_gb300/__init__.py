@@ -22,6 +22,7 @@ VIE_FP64, VIE_FP32, VIE_BF16X3 = 0, 1, 2
 VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT, VIE_OP_K = 0, 1, 2, 3
 VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE, VIE_SOLVE_BF16X3_REFINE = 0, 1, 2
 VIE_INJECT_NONE, VIE_INJECT_OOM = 0, 1
+VIE_SETUP_PWC = 1
 
 EXPORTS = (
     "vie_setup", "vie_setup_green_external", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
@@ -143,13 +144,14 @@ def _stream(s):
     return int(s)
 
 
-def _nrhs(a, nv):
+def _nrhs(a, h):
+    """Right-hand sides in a vector batch of handle h (h.nc components per voxel: 12 PWL, 3 PWC)."""
     n = 1
     for d in a.shape:
         n *= int(d)
-    if n % (12 * nv):
-        raise ValueError("array size is not a multiple of 12 * N_V")
-    return n // (12 * nv)
+    if n % (h.nc * h.nv):
+        raise ValueError(f"array size is not a multiple of {h.nc} * N_V")
+    return n // (h.nc * h.nv)
 
 
 def _check(rc, where):
@@ -161,11 +163,12 @@ def _check(rc, where):
 class Handle:
     """Owns a vie_handle (one grid, frequency and material map)."""
 
-    def __init__(self, ptr, grid, freq):
+    def __init__(self, ptr, grid, freq, nc=12):
         self.ptr = ptr
         self.grid = grid
         self.freq = freq
         self.nv = grid[0] * grid[1] * grid[2]
+        self.nc = nc  # unknowns per voxel: 12 (PWL) or 3 (PWC)
 
     def close(self):
         if self.ptr:
@@ -180,13 +183,14 @@ class Handle:
 
 
 def vie_setup(grid, freq_hz, eps_real, sigma, flags=0):
-    """grid = (nx, ny, nz, dx, dy, dz); eps_real, sigma: float64 (nz, ny, nx) maps (host or device)."""
+    """grid = (nx, ny, nz, dx, dy, dz); eps_real, sigma: float64 (nz, ny, nx) maps (host or device).
+    flags = VIE_SETUP_PWC: the piecewise-constant system, vectors [nrhs][3][nz][ny][nx]."""
     lib = _lib()
     g = vie_grid(*[int(v) for v in grid[:3]], *[float(v) for v in grid[3:]])
     out = ctypes.c_void_p()
     _check(lib.vie_setup(ctypes.byref(g), float(freq_hz), _ptr(eps_real), _ptr(sigma), int(flags), ctypes.byref(out)),
            "vie_setup")
-    return Handle(out.value, (g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), freq_hz)
+    return Handle(out.value, (g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), freq_hz, 3 if flags & VIE_SETUP_PWC else 12)
 
 
 def vie_setup_green_external(grid, freq_hz, eps_real, sigma, toeplitz):
@@ -211,14 +215,14 @@ def vie_destroy(h):
 
 
 def vie_matvec(h, x, y, precision=VIE_FP64, op=VIE_OP_A, stream=None):
-    return _check(_lib().vie_matvec(h.ptr, _nrhs(x, h.nv), _ptr(x), _ptr(y), int(precision), int(op), _stream(stream)),
+    return _check(_lib().vie_matvec(h.ptr, _nrhs(x, h), _ptr(x), _ptr(y), int(precision), int(op), _stream(stream)),
                   "vie_matvec")
 
 
 def vie_matvec_noalloc(h, x, y, precision=VIE_FP64, op=VIE_OP_A, stream=None):
     """vie_matvec for callers that cannot allocate GPU memory: device tensors only, scratch in a fixed
     64 MiB static device array; oversized calls raise VieError (VIE_EINVAL)."""
-    return _check(_lib().vie_matvec_noalloc(h.ptr, _nrhs(x, h.nv), _ptr(x), _ptr(y), int(precision), int(op),
+    return _check(_lib().vie_matvec_noalloc(h.ptr, _nrhs(x, h), _ptr(x), _ptr(y), int(precision), int(op),
                                             _stream(stream)), "vie_matvec_noalloc")
 
 
@@ -243,7 +247,7 @@ def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFI
     """Returns (rc, [info dict per right-hand side]); rc is VIE_OK or VIE_NOT_CONVERGED.
     keep_point=False: the handle keeps no residual point for vie_fields (flags bit 2).
     graph=False: direct launches instead of a CUDA graph per restart cycle (flags bit 3)."""
-    n = _nrhs(b, h.nv)
+    n = _nrhs(b, h)
     info = (vie_solve_info * n)()
     flags = (1 if guess else 0) | (2 if true_resid else 0) | (0 if keep_point else 4) | (0 if graph else 8)
     rc = _check(_lib().vie_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
@@ -253,7 +257,7 @@ def vie_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP32_REFI
 
 def vie_fields(h, x, e_inc, e_coeff=None, p_abs=None, stream=None):
     """Returns the absorbed power P_abs (W) per right-hand side as a list."""
-    n = _nrhs(x, h.nv)
+    n = _nrhs(x, h)
     P = (ctypes.c_double * n)()
     _check(_lib().vie_fields(h.ptr, n, _ptr(x), _ptr(e_inc), _ptr(e_coeff), _ptr(p_abs), P, _stream(stream)),
            "vie_fields")
@@ -273,7 +277,7 @@ def vie_rhs_dipoles_h(h, pos, mom, h_inc, stream=None):
 
 def vie_hfields(h, x, h_inc, h_coeff=None, b1_plus=None, stream=None):
     """Magnetic field coefficients, b1+ and the magnetic energy; returns W_m (J) per right-hand side."""
-    n = _nrhs(x, h.nv)
+    n = _nrhs(x, h)
     W = (ctypes.c_double * n)()
     _check(_lib().vie_hfields(h.ptr, n, _ptr(x), _ptr(h_inc), _ptr(h_coeff), _ptr(b1_plus), W, _stream(stream)),
            "vie_hfields")

@@ -196,8 +196,8 @@ int vie_setup(const vie_grid* grid, double freq_hz, const double* eps_real, cons
     g_last_error.clear();
     REQUIRE(out, "out is NULL");
     *out = nullptr;
-    REQUIRE(flags == 0, "flags must be 0");
-    return handle_create(grid, freq_hz, eps_real, sigma, nullptr, out);
+    REQUIRE((flags & ~VIE_SETUP_PWC) == 0, "unknown flags");
+    return handle_create(grid, freq_hz, eps_real, sigma, nullptr, out, nullptr, (flags & VIE_SETUP_PWC) ? 3 : 12);
 }
 
 int vie_setup_green_external(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
@@ -218,7 +218,7 @@ size_t handle_green_bytes(const vie_handle* h) {
 }
 
 int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
-                  const vie_handle* share, vie_handle** out, const void* ext) {
+                  const vie_handle* share, vie_handle** out, const void* ext, int nc) {
     *out = nullptr;
     REQUIRE(grid && eps_real && sigma, "NULL argument");
     REQUIRE(grid->nx >= 1 && grid->ny >= 1 && grid->nz >= 1, "grid sizes must be >= 1");
@@ -238,6 +238,7 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
     }
     std::memset(static_cast<void*>(h), 0, sizeof(vie_handle));
     h->nx = grid->nx, h->ny = grid->ny, h->nz = grid->nz;
+    h->nc = nc == 3 ? 3 : 12;
     h->dx = grid->dx, h->dy = grid->dy, h->dz = grid->dz;
     h->freq = freq_hz;
     h->omega = 2.0 * VIE_PI * freq_hz;
@@ -368,8 +369,9 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
     REQUIRE(precision == VIE_FP64 || precision == VIE_FP32 || precision == VIE_BF16X3, "unknown precision");
     REQUIRE(op == VIE_OP_A || op == VIE_OP_PA || op == VIE_OP_NSCAT || op == VIE_OP_K, "unknown operator");
     REQUIRE(op != VIE_OP_K || precision == VIE_FP64, "the K operator is FP64 only");
+    REQUIRE(op != VIE_OP_K || h->nc == 12, "the K operator is built for the PWL system only");
     REQUIRE(x != y, "x and y must not overlap");
-    const size_t bytes = (size_t)nrhs * 12 * h->nv * (precision == VIE_FP64 ? sizeof(double2) : sizeof(float2));
+    const size_t bytes = (size_t)nrhs * h->nc * h->nv * (precision == VIE_FP64 ? sizeof(double2) : sizeof(float2));
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(x, bytes, false);
@@ -387,7 +389,7 @@ int vie_rhs_planewave(vie_handle* h, const double pol[3], const double dir[3], v
     g_last_error.clear();
     REQUIRE(h && pol && dir, "NULL argument");
     for (int i = 0; i < 3; ++i) REQUIRE(std::isfinite(pol[i]) && std::isfinite(dir[i]), "non-finite source");
-    const size_t bytes = 12 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)h->nc * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(e_inc, bytes, true);
@@ -404,7 +406,7 @@ int vie_rhs_dipoles(vie_handle* h, int nrhs, const double* pos, const double* mo
     REQUIRE(h && pos && mom, "NULL argument");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     for (int i = 0; i < 3 * nrhs; ++i) REQUIRE(std::isfinite(pos[i]) && std::isfinite(mom[i]), "non-finite source");
-    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * h->nc * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(e_inc, bytes, true);
@@ -425,8 +427,9 @@ int vie_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int r
     REQUIRE(maxit >= 1, "maxit must be >= 1");
     REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE || mode == VIE_SOLVE_BF16X3_REFINE,
             "unknown mode");
+    REQUIRE(mode != VIE_SOLVE_BF16X3_REFINE || h->nc == 12, "the BF16x3 mode is built for the PWL system only");
     REQUIRE((flags & ~15) == 0, "unknown flags");
-    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * h->nc * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(b, bytes, false);
@@ -446,7 +449,7 @@ int vie_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, void* 
     g_last_error.clear();
     REQUIRE(h && x && e_inc, "NULL argument");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * h->nc * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(x, bytes, false);
@@ -472,9 +475,10 @@ int vie_green_toeplitz(vie_handle* h, void* out) {
 int vie_rhs_dipoles_h(vie_handle* h, int nrhs, const double* pos, const double* mom, void* h_inc, void* stream) {
     g_last_error.clear();
     REQUIRE(h && pos && mom && h_inc, "NULL argument");
+    REQUIRE(h->nc == 12, "magnetic fields are built for the PWL system only");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     for (int i = 0; i < 3 * nrhs; ++i) REQUIRE(std::isfinite(pos[i]) && std::isfinite(mom[i]), "non-finite source");
-    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * h->nc * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(h_inc, bytes, true);
@@ -488,8 +492,9 @@ int vie_hfields(vie_handle* h, int nrhs, const void* x, const void* h_inc, void*
                 void* stream) {
     g_last_error.clear();
     REQUIRE(h && x && h_inc, "NULL argument");
+    REQUIRE(h->nc == 12, "magnetic fields are built for the PWL system only");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
-    const size_t bytes = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * h->nc * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(x, bytes, false);

@@ -78,6 +78,10 @@ __host__ __device__ constexpr int sign_of(int a, int b) {
 __host__ __device__ constexpr int parity_of(int a, int i) {
     return ((a / 4 == i) ? -1 : 1) * ((a % 4 == i + 1) ? -1 : 1);
 }
+// Gram entry of component alpha (Eq. 33): G^1 = DV for the constant function, DV/12 for the
+// linear ones; in the PWC layout (nc = 3 components per voxel) every component is a constant function
+__host__ __device__ __forceinline__ bool comp_is_constant(int alpha, int nc) { return nc == 3 || alpha % 4 == 0; }
+
 // bit mask over the 12 components of parity -1 under reflection of axis i
 __host__ __device__ constexpr unsigned flip_mask(int i) {
     unsigned m = 0;
@@ -96,6 +100,7 @@ struct Workspace {
 
 struct vie_handle {
     int nx, ny, nz;
+    int nc;  // unknowns per voxel: 12 (PWL, 4 scalar functions x 3 components) or 3 (PWC: l = 1 only)
     double dx, dy, dz;
     double freq, omega, k0;
     int L[3];   // FFT lengths (x, y, z), powers of two >= 2N - 1
@@ -153,8 +158,9 @@ struct vie_handle {
 // ext (optional, no template): the caller's Toeplitz table [144][2nz-1][2ny-1][2nx-1] complex128
 // (host or device) from which the Green tensors are taken instead of being computed
 // (vie_setup_green_external).
+// nc: unknowns per voxel, 12 (PWL) or 3 (PWC, vie_setup flag VIE_SETUP_PWC).
 int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, const double* sigma,
-                  const vie_handle* share, vie_handle** out, const void* ext = nullptr);
+                  const vie_handle* share, vie_handle** out, const void* ext = nullptr, int nc = 12);
 // device bytes held by a handle's Green tensors, twiddles and column map (shared part)
 size_t handle_green_bytes(const vie_handle* h);
 

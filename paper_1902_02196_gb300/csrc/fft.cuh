@@ -146,6 +146,7 @@ struct MatvecEpi {
     const int* nact;
     unsigned long long* bctr;
     double bfix, bper;
+    int nc;  // components per voxel and right-hand side: 12 (PWL) or 3 (PWC: the l = 1 functions only)
 };
 
 template <int L>
@@ -207,11 +208,11 @@ __global__ void __launch_bounds__(LineCfg<L>::NT) line_fft_kernel(LineArgs a, co
         long long o = ai * a.oa + (a.pout ? a.pout[l] : l) * a.ol + (long long)b * a.ob;
         if (EPI && epi.conv) reinterpret_cast<C*>(epi.conv)[o] = v;  // full-grid output: o is the voxel index
         if (EPI) {
-            // line b = ((r * 12 + alpha) * nz + z) * ny + y, element l = x
-            int alpha = (b / (epi.ny * epi.nz)) % 12;
+            // line b = ((r * nc + alpha) * nz + z) * ny + y, element l = x
+            int alpha = (b / (epi.ny * epi.nz)) % epi.nc;
             long long vox = (long long)(b % (epi.ny * epi.nz)) * epi.nx + l;
             C xv = reinterpret_cast<const C*>(epi.x)[o];
-            T gl = (T)((alpha % 4) == 0 ? epi.g1 : epi.g234);
+            T gl = (T)(comp_is_constant(alpha, epi.nc) ? epi.g1 : epi.g234);
             if (epi.op == VIE_OP_A) {
                 C c2 = reinterpret_cast<const C*>(epi.c2)[vox];
                 v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2, v));
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(LineCfg<L>::NT) line_fft_kernel(LineArgs a, co
                 C t = cmul(c2, v);
                 T ig = T(1) / gl;
                 if (epi.shift) {
-                    const double2 sh = epi.shift[b / (12 * epi.ny * epi.nz)];
+                    const double2 sh = epi.shift[b / (epi.nc * epi.ny * epi.nz)];
                     c1 = csub(c1, mk((T)sh.x, (T)sh.y));
                 }
                 v = csub(cmul(c1, xv), mk(ig * t.x, ig * t.y));

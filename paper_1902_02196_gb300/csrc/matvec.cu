@@ -28,6 +28,18 @@ int zpass_bf16_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s);  // 
 int zpass_bf16_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s);   // zpass_bf16.cu
 int zpass_f32_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s);    // zpass_f32.cu
 
+// y[3] = B(k) x[3] of the PWC system (the l = 1 sub-block): entry (p, q) is tensor 10 pq + 0
+// (scalar pair (1, 1)) with sign +1
+template <typename C>
+__device__ __forceinline__ void block_product_pwc(C* xv, C* acc, const C* __restrict__ gp, long long tstride) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] = mk(decltype(xv[0].x)(0), decltype(xv[0].x)(0));
+#pragma unroll
+        for (int b = 0; b < 3; ++b) cfma(acc[a], gp[10 * pq_index(a, b) * tstride], xv[b]);
+    }
+}
+
 // y[12] = B(k) x[12] at one frequency point; xv/acc in registers, Green values streamed once.
 template <typename C>
 __device__ __forceinline__ void block_product(C* xv, C* acc, const C* __restrict__ gp, long long tstride) {
@@ -47,7 +59,7 @@ __device__ __forceinline__ void block_product(C* xv, C* acc, const C* __restrict
     }
 }
 
-template <typename T, int L>
+template <typename T, int L, int NC = 12>
 struct ZCfg {
     static constexpr int TB0 = (sizeof(T) == 4 ? 1024 : 512) / L;
     static constexpr int TB = TB0 < 1 ? 1 : TB0;
@@ -68,13 +80,13 @@ struct ZArgs {
     int ay, by;
 };
 
-template <typename T, int L>
-__global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const typename CT<T>::C* twg) {
+template <typename T, int L, int NC>
+__global__ void __launch_bounds__(ZCfg<T, L, NC>::NT) zpass_kernel(ZArgs z, const typename CT<T>::C* twg) {
     using C = typename CT<T>::C;
-    constexpr int TB = ZCfg<T, L>::TB, GS = ZCfg<T, L>::GS, NT = ZCfg<T, L>::NT;
+    constexpr int TB = ZCfg<T, L, NC>::TB, GS = ZCfg<T, L, NC>::GS, NT = ZCfg<T, L, NC>::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    C* tw = s + 12 * GS;
+    C* tw = s + NC * GS;
     const int tid = threadIdx.x;
     for (int m = tid; m < L; m += NT) tw[m] = twg[m];
 
@@ -91,8 +103,8 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
     const unsigned fy = ky > z.Ly / 2 ? z.my : 0u;
 
     for (int r = 0; r < z.R; ++r) {
-        C* base = w + (long long)r * 12 * z.nz * plane + (long long)py * z.Lx + kx0;
-        for (int idx = tid; idx < 12 * L * TB; idx += NT) {
+        C* base = w + (long long)r * NC * z.nz * plane + (long long)py * z.Lx + kx0;
+        for (int idx = tid; idx < NC * L * TB; idx += NT) {
             int tb = idx % TB;
             int l = (idx / TB) % L;
             int a = idx / (TB * L);
@@ -101,7 +113,7 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
             s[a * GS + l * TB + tb] = v;
         }
         __syncthreads();
-        fft_smem<C, L, 12, TB, TB, GS, NT>(s, tw, -1);
+        fft_smem<C, L, NC, TB, TB, GS, NT>(s, tw, -1);
         for (int p = tid; p < L * TB; p += NT) {
             int tb = p % TB;
             int kz = p / TB;
@@ -110,20 +122,23 @@ __global__ void __launch_bounds__(ZCfg<T, L>::NT) zpass_kernel(ZArgs z, const ty
             int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
             int kzo = kz <= Lz / 2 ? kz : Lz - kz;
             unsigned mask = fy ^ (kx > z.Lx / 2 ? z.mx : 0u) ^ (kz > Lz / 2 ? z.mz : 0u);
-            C xv[12], acc[12];
+            C xv[NC], acc[NC];
 #pragma unroll
-            for (int b = 0; b < 12; ++b) {
+            for (int b = 0; b < NC; ++b) {
                 C v = s[b * GS + kz * TB + tb];
                 xv[b] = ((mask >> b) & 1u) ? cneg(v) : v;
             }
             const C* gp = green + ((long long)kzo * z.Oy + kyo) * z.Ox + kxo;
-            block_product(xv, acc, gp, z.tstride);
+            if constexpr (NC == 12)
+                block_product(xv, acc, gp, z.tstride);
+            else
+                block_product_pwc(xv, acc, gp, z.tstride);
 #pragma unroll
-            for (int a = 0; a < 12; ++a) s[a * GS + kz * TB + tb] = ((mask >> a) & 1u) ? cneg(acc[a]) : acc[a];
+            for (int a = 0; a < NC; ++a) s[a * GS + kz * TB + tb] = ((mask >> a) & 1u) ? cneg(acc[a]) : acc[a];
         }
         __syncthreads();
-        fft_smem<C, L, 12, TB, TB, GS, NT>(s, tw, +1);
-        for (int idx = tid; idx < 12 * z.nz * TB; idx += NT) {
+        fft_smem<C, L, NC, TB, TB, GS, NT>(s, tw, +1);
+        for (int idx = tid; idx < NC * z.nz * TB; idx += NT) {
             int tb = idx % TB;
             int l = (idx / TB) % z.nz;
             int a = idx / (TB * z.nz);
@@ -176,16 +191,17 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
     const long long p = blockIdx.x;  // spectrum plane; the input plane is pin (rmap: active right-hand sides)
+    const long long rplanes = (long long)dc.nc * nz;  // planes per right-hand side
     if (dc.nact) {  // planes of right-hand sides beyond the device count are skipped
         const int cnt = *dc.nact;
         dev_bytes_add(dc.bctr, dc.bfix + dc.bper * cnt, cnt > 0);
-        if (p / (12LL * nz) >= cnt) return;
+        if (p / rplanes >= cnt) return;
     }
     for (int m = tid; m < L; m += NT) {
         tw[m] = twg[m];
         pos[m] = cpos[m];
     }
-    const long long pin = rmap ? (long long)rmap[p / (12LL * nz)] * 12 * nz + p % (12LL * nz) : p;
+    const long long pin = rmap ? (long long)rmap[p / rplanes] * rplanes + p % rplanes : p;
     if (rows) {
         const int z = (int)(p % nz);
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = rows[(long long)z * ny + yy];
@@ -263,17 +279,19 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
     unsigned char* pos = reinterpret_cast<unsigned char*>(rw + Cfg::H);
     const int tid = threadIdx.x;
     const int nx = epi.nx, ny = epi.ny, nz = epi.nz;
-    const long long p = blockIdx.x;  // spectrum plane (r * 12 + alpha) * nz + z; output plane po
+    const long long p = blockIdx.x;  // spectrum plane (r * nc + alpha) * nz + z; output plane po
+    const int nc = epi.nc;
+    const long long rplanes = (long long)nc * nz;  // planes per right-hand side
     if (epi.nact) {
         const int cnt = *epi.nact;
         dev_bytes_add(epi.bctr, epi.bfix + epi.bper * cnt, cnt > 0);
-        if (p / (12LL * nz) >= cnt) return;
+        if (p / rplanes >= cnt) return;
     }
     for (int m = tid; m < L; m += NT) {
         tw[m] = twg[m];
         pos[m] = cpos[m];
     }
-    const long long po = epi.rmap ? (long long)epi.rmap[p / (12LL * nz)] * 12 * nz + p % (12LL * nz) : p;
+    const long long po = epi.rmap ? (long long)epi.rmap[p / rplanes] * rplanes + p % rplanes : p;
     if (epi.rows)
         for (int yy = tid; yy < ny; yy += NT) rw[yy] = epi.rows[(p % nz) * ny + yy];
     const C* src = w + p * (long long)L * L;
@@ -340,15 +358,15 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         cp_async_wait<0>();
         __syncthreads();
     }
-    const int alpha = (int)((p / nz) % 12);
+    const int alpha = (int)((p / nz) % nc);
     const long long zoff = (p % nz) * (long long)ny * nx;
-    const R gl = (R)((alpha % 4) == 0 ? epi.g1 : epi.g234);
+    const R gl = (R)(comp_is_constant(alpha, nc) ? epi.g1 : epi.g234);
     const R ig = (R)1 / gl;
     const C* c1 = reinterpret_cast<const C*>(epi.c1);
     const C* c2 = reinterpret_cast<const C*>(epi.c2);
     C sh = mk((R)0, (R)0);  // shift of op PA for this plane's right-hand side
     if (epi.shift) {
-        const double2 d = epi.shift[po / (12 * (long long)nz)];
+        const double2 d = epi.shift[po / rplanes];
         sh = mk((R)d.x, (R)d.y);
     }
     C* conv = CONV ? reinterpret_cast<C*>(epi.conv) : nullptr;
@@ -433,34 +451,36 @@ static int launch_line(const char* name, const vie_handle* h, int L, const LineA
     return VIE_EINVAL;
 }
 
-template <typename T, int L>
+template <typename T, int L, int NC>
 static int launch_z_L(const char* name, const vie_handle* h, const ZArgs& z, cudaStream_t s) {
     using C = typename CT<T>::C;
-    constexpr int TB = ZCfg<T, L>::TB;
-    size_t smem = sizeof(C) * (size_t)(12 * ZCfg<T, L>::GS + L);
+    using Cfg = ZCfg<T, L, NC>;
+    constexpr int TB = Cfg::TB;
+    size_t smem = sizeof(C) * (size_t)(NC * Cfg::GS + L);
     // set on every call: the attribute is per device and launches may come from several threads
-    VIE_CUDA(cudaFuncSetAttribute(zpass_kernel<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA(cudaFuncSetAttribute(zpass_kernel<T, L, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     long long blocks = (long long)z.Ly * ((z.Lx + TB - 1) / TB);
-    const double bytes = (double)sizeof(C) * (2.0 * z.R * 12 * z.nz * z.Ly * z.Lx + 60.0 * z.Ox * z.Oy * z.Oz);
-    VIE_KLAUNCH_B(name, s, bytes,
-                  zpass_kernel<T, L><<<(unsigned)blocks, ZCfg<T, L>::NT, smem, s>>>(z, twiddles<T>(h, L)));
+    // the z lines read and written once, and the octant tensors the block reads (60 or 6)
+    const double bytes = (double)sizeof(C) * (2.0 * z.R * NC * z.nz * z.Ly * z.Lx +
+                                              (NC == 12 ? 60.0 : 6.0) * z.Ox * z.Oy * z.Oz);
+    VIE_KLAUNCH_B(name, s, bytes, zpass_kernel<T, L, NC><<<(unsigned)blocks, Cfg::NT, smem, s>>>(z, twiddles<T>(h, L)));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
 
-template <typename T>
+template <typename T, int NC = 12>
 static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z, cudaStream_t s) {
     switch (L) {
-        case 2: return launch_z_L<T, 2>(name, h, z, s);
-        case 4: return launch_z_L<T, 4>(name, h, z, s);
-        case 8: return launch_z_L<T, 8>(name, h, z, s);
-        case 16: return launch_z_L<T, 16>(name, h, z, s);
-        case 32: return launch_z_L<T, 32>(name, h, z, s);
-        case 64: return launch_z_L<T, 64>(name, h, z, s);
-        case 128: return launch_z_L<T, 128>(name, h, z, s);
-        case 256: return launch_z_L<T, 256>(name, h, z, s);
-        case 512: return launch_z_L<T, 512>(name, h, z, s);
-        case 1024: return launch_z_L<T, 1024>(name, h, z, s);
+        case 2: return launch_z_L<T, 2, NC>(name, h, z, s);
+        case 4: return launch_z_L<T, 4, NC>(name, h, z, s);
+        case 8: return launch_z_L<T, 8, NC>(name, h, z, s);
+        case 16: return launch_z_L<T, 16, NC>(name, h, z, s);
+        case 32: return launch_z_L<T, 32, NC>(name, h, z, s);
+        case 64: return launch_z_L<T, 64, NC>(name, h, z, s);
+        case 128: return launch_z_L<T, 128, NC>(name, h, z, s);
+        case 256: return launch_z_L<T, 256, NC>(name, h, z, s);
+        case 512: return launch_z_L<T, 512, NC>(name, h, z, s);
+        case 1024: return launch_z_L<T, 1024, NC>(name, h, z, s);
     }
     set_error("unsupported FFT length " + std::to_string(L));
     return VIE_EINVAL;
@@ -496,7 +516,7 @@ static int launch_xy_L(bool fwd, const vie_handle* h, const void* in, void* out,
     const double c = sizeof(C), plane_full = (double)L * L;
     // with a device count of right-hand sides (e.nact) the kernel adds its bytes on the device:
     // the part proportional to the planes transformed, per right-hand side of the grid, plus a fixed part
-    const double rg = (double)planes / (12.0 * h->nz);  // right-hand sides of the launch grid
+    const double rg = (double)planes / ((double)h->nc * h->nz);  // right-hand sides of the launch grid
     MatvecEpi ee = e;
     if (fwd) {
         const char* name = f32 ? "fft_xy_f32" : "fft_xy_f64";
@@ -558,7 +578,7 @@ static int launch_xy(bool fwd, const vie_handle* h, const void* in, void* out, l
 // [R*12][Nz][Ny][Lx] in front of it on the line-transform path (the only one that uses W1).
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision) {
     size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
-    size_t comps = (size_t)nrhs * 12 * h->nz;
+    size_t comps = (size_t)nrhs * h->nc * h->nz;
     size_t w2 = comps * h->L[1] * h->L[0];
     size_t w1 = xy_ok(h) ? 0 : comps * h->ny * h->L[0];
     return c * (w1 + w2) + 256;
@@ -578,13 +598,15 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     if (!xy_ok(h) || !nact) rmap = nullptr;
     if (!rmap) nact = nullptr;
     const int Rs = R;  // right-hand sides the spectrum has room for
-    const long long comps = (long long)Rs * 12 * nz;
+    const int nc = h->nc;
+    const long long comps = (long long)Rs * nc * nz;
     // W1 exists on the line-transform path only (matvec_workspace_bytes)
     C* W1 = reinterpret_cast<C*>(ws);
     C* W2 = xy_ok(h) ? W1 : W1 + comps * ny * Lx;
     MatvecEpi e{};
     e.x = x;
     e.op = op;
+    e.nc = nc;
     e.nx = nx, e.ny = ny, e.nz = nz;
     const double dV = h->dx * h->dy * h->dz;
     e.g1 = dV;
@@ -603,12 +625,31 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     e.rmap = rmap;
     e.nact = nact;
     MatvecEpi noepi{};
-    MatvecEpi fwdmap{};  // the forward kernel reads only rmap and the count
+    noepi.nc = nc;
+    MatvecEpi fwdmap{};  // the forward kernel reads only rmap, the count and nc
     fwdmap.rmap = rmap;
     fwdmap.nact = nact;
+    fwdmap.nc = nc;
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
+        if (nc == 3) {  // PWC: the generic z pass with the 3 x 3 block of the l = 1 tensors
+            if (bf16) {
+                set_error("the BF16x3 matvec is built for the PWL system only");
+                return VIE_EINVAL;
+            }
+            ZArgs z{};
+            z.w = W2;
+            z.green = sizeof(T) == 8 ? (const void*)h->green64 : (const void*)h->green32;
+            z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+            z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
+            // reflection parity of component p (the constant function) under axis i: -1 iff p = i
+            z.mx = 1u, z.my = 2u, z.mz = 4u;
+            z.colkx = h->colkx32;
+            z.ay = ay, z.by = by;
+            return launch_z<T, 3>(sizeof(T) == 8 ? "zpass_block_pwc_f64" : "zpass_block_pwc_f32", h, Lz, z, s);
+        }
         if (sizeof(T) == 4 && zfused_ok(h)) {
             ZFArgs z{};
             z.w = reinterpret_cast<float2*>(W2);
@@ -652,7 +693,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         return launch_z<T>(sizeof(T) == 8 ? "zpass_block_f64" : "zpass_block_f32", h, Lz, z, s);
     };
     if (xy_ok(h)) {
-        const double in_elems = sp.rows ? (double)Rs * 12 * sp.ns : (double)comps * ny * nx;
+        const double in_elems = sp.rows ? (double)Rs * nc * sp.ns : (double)comps * ny * nx;
         VIE_TRY(launch_xy<C>(true, h, x, W2, comps, nx, ny, fwdmap, sp, in_elems, s));
         VIE_TRY(zpass(fft2::split_a(Ly), Ly / fft2::split_a(Ly)));
         return launch_xy<C>(false, h, W2, y, comps, nx, ny, e, sp, in_elems, s);
@@ -712,7 +753,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
 // Runs the z-pass autotuner for nrhs right-hand sides of this precision now (outside any stream
 // capture), so that a CUDA graph captured later launches the tuned tile width.
 int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s) {
-    if (precision == VIE_FP64 || !zfused_ok(h)) return VIE_OK;
+    if (precision == VIE_FP64 || !zfused_ok(h) || h->nc != 12) return VIE_OK;
     ZFArgs z{};
     z.w = nullptr;
     z.green_t = h->green32t;
@@ -764,7 +805,7 @@ __global__ void support_scatter_kernel(const C* __restrict__ part, C* __restrict
 template <typename C>
 static int support_copy(const vie_handle* h, int R, const void* src, void* dst, const Support& sp, bool gather,
                         cudaStream_t s) {
-    const long long total = (long long)R * 12 * (long long)h->nv;
+    const long long total = (long long)R * h->nc * (long long)h->nv;
     if (!sp.rows) {
         VIE_CUDA(cudaMemcpyAsync(dst, src, sizeof(C) * (size_t)total, cudaMemcpyDeviceToDevice, s));
         return VIE_OK;
@@ -817,12 +858,12 @@ int matvec_support(vie_handle* h, int R, const void* x, void* y, int precision, 
                                         precision == VIE_BF16X3);
     const size_t c = precision == VIE_FP64 ? sizeof(double2) : sizeof(float2);
     void* tx = tmp;
-    void* ty = static_cast<char*>(tmp) + c * (size_t)R * 12 * h->nv;
+    void* ty = static_cast<char*>(tmp) + c * (size_t)R * h->nc * h->nv;
     VIE_TRY(support_scatter(h, R, x, tx, precision, sp, s));
     VIE_TRY(matvec_full(h, R, tx, ty, precision, op, s, conv));
     VIE_TRY(support_gather(h, R, ty, y, precision, sp, s));
     if (shift) {
-        const long long n = 12LL * sp.ns;
+        const long long n = (long long)h->nc * sp.ns;
         const dim3 g((unsigned)((n + 255) / 256), R);
         if (precision == VIE_FP64)
             VIE_KLAUNCH("matvec_shift", s,

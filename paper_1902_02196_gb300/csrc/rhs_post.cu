@@ -92,7 +92,7 @@ __device__ __forceinline__ void centre(const GridD& g, long long m, double* r) {
 }
 
 __global__ void planewave_kernel(GridD g, double k0, double px, double py, double pz, double ux, double uy, double uz,
-                                 double2 ce, const double2* __restrict__ chi, double2* e, double2* b) {
+                                 double2 ce, const double2* __restrict__ chi, int nc, double2* e, double2* b) {
     const long long nv = (long long)g.nx * g.ny * g.nz;
     long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nv) return;
@@ -111,13 +111,13 @@ __global__ void planewave_kernel(GridD g, double k0, double px, double py, doubl
     const double dV = g.dx * g.dy * g.dz;
     const double pol[3] = {px, py, pz};
     const double2 cc = cmuld(ce, chi[m]);
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < (nc == 12 ? 4 : 1); ++l) {  // PWC (nc = 3): the constant function only
         double2 fac = make_double2(dV, 0.0);
         for (int i = 0; i < 3; ++i) fac = cmuld(fac, (l == i + 1) ? f1[i] : f0[i]);
         fac = cmuld(fac, phase);
         for (int p = 0; p < 3; ++p) {
             const double2 v = make_double2(pol[p] * fac.x, pol[p] * fac.y);
-            const long long o = (long long)(4 * p + l) * nv + m;
+            const long long o = (long long)(nc == 12 ? 4 * p + l : p) * nv + m;
             if (e) e[o] = v;
             if (b) b[o] = cmuld(cc, v);
         }
@@ -126,8 +126,8 @@ __global__ void planewave_kernel(GridD g, double k0, double px, double py, doubl
 
 // Tested fields of one z-, y- or x-moment dipole per right-hand side; thread per (voxel, rhs).
 __global__ void dipole_kernel(GridD g, double k0, double2 ice, int R, const double* __restrict__ pos,
-                              const double* __restrict__ mom, double2 ce, const double2* __restrict__ chi, double2* e,
-                              double2* b) {
+                              const double* __restrict__ mom, double2 ce, const double2* __restrict__ chi, int nc,
+                              double2* e, double2* b) {
     const long long nv = (long long)g.nx * g.ny * g.nz;
     long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= nv * R) return;
@@ -172,7 +172,8 @@ __global__ void dipole_kernel(GridD g, double k0, double2 ice, int R, const doub
             }
     const double2 cc = cmuld(ce, chi[m]);
     for (int a = 0; a < 12; ++a) {
-        const long long o = ((long long)rr * 12 + a) * nv + m;
+        if (nc == 3 && a % 4) continue;  // PWC: the constant functions' components only
+        const long long o = ((long long)rr * nc + (nc == 12 ? a : a / 4)) * nv + m;
         if (e) e[o] = acc[a];
         if (b) b[o] = cmuld(cc, acc[a]);
     }
@@ -183,16 +184,16 @@ __global__ void dipole_kernel(GridD g, double k0, double2 ice, int R, const doub
 __global__ void fields_kernel(long long nv, int R, const double2* __restrict__ x, const double2* __restrict__ einc,
                               const double2* __restrict__ nx_, const float2* __restrict__ corr,
                               const double2* __restrict__ chi, double2 ice, double g1, double g234, double dV,
-                              double2* e, double* pabs, double* partial) {
+                              int nc, double2* e, double* pabs, double* partial) {
     __shared__ double sh[256];
     const int rr = blockIdx.y;
     long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double pv = 0.0;
     if (m < nv) {
         double q = 0.0;
-        for (int a = 0; a < 12; ++a) {
-            const long long o = ((long long)rr * 12 + a) * nv + m;
-            const double G = (a % 4 == 0) ? g1 : g234;
+        for (int a = 0; a < nc; ++a) {
+            const long long o = ((long long)rr * nc + a) * nv + m;
+            const double G = comp_is_constant(a, nc) ? g1 : g234;
             const double2 xv = x[o];
             q += G * (xv.x * xv.x + xv.y * xv.y);
             if (e) {
@@ -380,7 +381,7 @@ int rhs_planewave_device(vie_handle* h, const double pol[3], const double dir[3]
     const long long nv = (long long)h->nv;
     const double2 ce = make_double2(0.0, h->omega * VIE_EPS0);
     VIE_KLAUNCH("planewave", s, planewave_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(gridd(h), h->k0, pol[0], pol[1], pol[2], dir[0] / n,
-                                                                  dir[1] / n, dir[2] / n, ce, h->chi64, e, b));
+                                                                  dir[1] / n, dir[2] / n, ce, h->chi64, h->nc, e, b));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
@@ -397,7 +398,7 @@ int rhs_dipoles_device(vie_handle* h, int R, const double* pos, const double* mo
     const double2 ice = make_double2(0.0, -1.0 / (h->omega * VIE_EPS0));
     const long long th = nv * R;
     VIE_KLAUNCH("dipole", s, dipole_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(gridd(h), h->k0, ice, R, dbuf, dbuf + 3 * R, ce,
-                                                               h->chi64, e, b));
+                                                               h->chi64, h->nc, e, b));
     cudaError_t err = cudaGetLastError();
     cudaStreamSynchronize(s);
     cudaFree(dbuf);
@@ -416,9 +417,10 @@ int rhs_dipoles_device(vie_handle* h, int R, const double* pos, const double* mo
 int fields_device(vie_handle* h, int R, const double2* x, const double2* e_inc, double2* e_out, double* p_abs,
                   double* P_abs_host, cudaStream_t s) {
     const long long nv = (long long)h->nv;
-    const long long total = nv * 12 * R;
+    const int nc = h->nc;
+    const long long total = nv * nc * R;
     const int nblk = (int)((nv + 255) / 256);
-    const int ndb = (int)std::min<long long>((12 * nv + 255) / 256, 1024);
+    const int ndb = (int)std::min<long long>((nc * nv + 255) / 256, 1024);
     auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t oPart = a256(sizeof(double2) * (size_t)total);  // product (FP64), or d and its product (FP32)
     const size_t oDiff = oPart + a256(sizeof(double) * ((size_t)nblk * R + R));
@@ -435,7 +437,7 @@ int fields_device(vie_handle* h, int R, const double2* x, const double2* e_inc, 
         const double2* x1 = static_cast<const double2*>(h->fcache_ws.ptr);
         float2* d32 = reinterpret_cast<float2*>(base);
         float2* c32 = d32 + total;
-        VIE_KLAUNCH("fields_diff", s, fields_diff_kernel<<<dim3(ndb, R), 256, 0, s>>>(12 * nv, x, x1, d32, dpart));
+        VIE_KLAUNCH("fields_diff", s, fields_diff_kernel<<<dim3(ndb, R), 256, 0, s>>>(nc * nv, x, x1, d32, dpart));
         VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<2 * R, 256, 0, s>>>(dpart, ndb, dtot));
         VIE_CHECK_LAUNCH();
         std::vector<double> hn(2 * (size_t)R);
@@ -465,7 +467,7 @@ int fields_device(vie_handle* h, int R, const double2* x, const double2* e_inc, 
     dim3 grid(nblk, R);
     VIE_KLAUNCH("fields", s,
                 fields_kernel<<<grid, 256, 0, s>>>(nv, R, x, e_inc, conv, corr, h->chi64, ice, dV, dV / 12.0, dV,
-                                                   e_out, p_abs, part));
+                                                   nc, e_out, p_abs, part));
     VIE_KLAUNCH("sum_partials", s, sum_partials_kernel<<<R, 256, 0, s>>>(part, nblk, tot));
     if (cudaGetLastError() != cudaSuccess) rc = VIE_EDEVICE;
     if (rc == VIE_OK && P_abs_host) {

@@ -66,11 +66,15 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// 16-byte aligned address (a vector of nc ns float pairs per right-hand side starts on an odd
+// element when nc ns is odd, as for the PWC system with an odd support)
+__device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // K consecutive complex values starting at element e0 of p (zero past n); 16-byte loads
-// when the chunk is complete (vectors start on even elements, so float pairs are aligned).
+// when the chunk is complete and aligned.
 template <typename C, int K>
 __device__ __forceinline__ void load_chunk(const C* __restrict__ p, long long e0, long long n, C* v) {
-    if (e0 + K <= n) {
+    if (e0 + K <= n && (sizeof(C) != 8 || al16(p + e0))) {
         if constexpr (sizeof(C) == 8) {
             const float4* q = reinterpret_cast<const float4*>(p + e0);
 #pragma unroll
@@ -90,7 +94,7 @@ __device__ __forceinline__ void load_chunk(const C* __restrict__ p, long long e0
 }
 template <typename C, int K>
 __device__ __forceinline__ void store_chunk(C* __restrict__ p, long long e0, long long n, const C* v) {
-    if (e0 + K <= n) {
+    if (e0 + K <= n && (sizeof(C) != 8 || al16(p + e0))) {
         if constexpr (sizeof(C) == 8) {
             float4* q = reinterpret_cast<float4*>(p + e0);
 #pragma unroll
@@ -329,12 +333,12 @@ __global__ void sub_kernel(const double2* __restrict__ a, const double2* __restr
 
 // b~ = P^-1 b = b / (eps G_alpha)
 __global__ void precond_rhs_kernel(const double2* __restrict__ b, const double2* __restrict__ ieps, double2* out,
-                                   long long nv, int R, double g1, double g234) {
+                                   long long nv, int R, int nc, double g1, double g234) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nv * 12 * R) return;
+    if (e >= nv * nc * R) return;
     const long long vox = e % nv;
-    const int alpha = (int)((e / nv) % 12);
-    const double ig = 1.0 / (alpha % 4 == 0 ? g1 : g234);
+    const int alpha = (int)((e / nv) % nc);
+    const double ig = 1.0 / (comp_is_constant(alpha, nc) ? g1 : g234);
     const double2 v = b[e], c = ieps[vox];
     out[e] = make_double2(ig * (v.x * c.x - v.y * c.y), ig * (v.x * c.y + v.y * c.x));
 }
@@ -613,7 +617,7 @@ int build_support(vie_handle* h, int R, const double2* b, const double2* guess, 
     int2* span = reinterpret_cast<int2*>(rows + nrows);
     const unsigned g = (unsigned)((nrows + 7) / 8);
     VIE_KLAUNCH("support_rows", st,
-                support_rows_kernel<<<g, 256, 0, st>>>(h->chi64, b, guess, R * 12, h->nx, nrows, (long long)h->nv,
+                support_rows_kernel<<<g, 256, 0, st>>>(h->chi64, b, guess, R * h->nc, h->nx, nrows, (long long)h->nv,
                                                        span));
     VIE_CHECK_LAUNCH();
     std::vector<int2> hs(nrows);
@@ -875,17 +879,17 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     }
     h->fcache_valid = 0;  // a new solve replaces the point kept for vie_fields
     const bool keep = !(flags & 4);
-    // vectors live on the support of the solve: [R][12][ns]
+    // vectors live on the support of the solve: [R][nc][ns] (nc = 12 PWL, 3 PWC)
     Support sp;
     VIE_TRY(build_support(h, R, b, (flags & 1) ? x : nullptr, &sp, st));
-    const long long nfull = 12LL * (long long)h->nv;
+    const long long nfull = (long long)h->nc * (long long)h->nv;
     if (sp.ns == 0) {  // chi = 0 everywhere and b = 0: x = 0
         VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)(R * nfull), st));
         VIE_CUDA(cudaStreamSynchronize(st));
         for (int r = 0; info && r < R; ++r) info[r] = vie_solve_info{1, 0, 0, 0, 0, 0.0, (flags & 2) ? 0.0 : -1.0, 0.0};
         return VIE_OK;
     }
-    const long long n = 12LL * sp.ns;
+    const long long n = (long long)h->nc * sp.ns;
     const bool mixed = mode == VIE_SOLVE_FP32_REFINE || mode == VIE_SOLVE_BF16X3_REFINE;
     const int inner = mode == VIE_SOLVE_BF16X3_REFINE ? VIE_BF16X3 : VIE_FP32;  // matvec of the inner GMRES
     const size_t vc = mixed ? sizeof(float2) : sizeof(double2);
@@ -1007,7 +1011,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const unsigned gr = (unsigned)((R + 127) / 128);
     const double dV = h->dx * h->dy * h->dz;
     VIE_KLAUNCH("precond_rhs", st,
-                precond_rhs_kernel<<<gtf, 256, 0, st>>>(b, h->ieps64, full0, (long long)h->nv, R, dV, dV / 12.0));
+                precond_rhs_kernel<<<gtf, 256, 0, st>>>(b, h->ieps64, full0, (long long)h->nv, R, h->nc, dV, dV / 12.0));
     VIE_CHECK_LAUNCH();
     VIE_TRY(support_gather(h, R, full0, bt, VIE_FP64, sp, st));
     VIE_TRY(S.norm2_64(bt, bn2));
