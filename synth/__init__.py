@@ -2,7 +2,7 @@
 
 This package holds no arithmetic of the integral-equation method: it only
 produces material maps (relative permittivity real part and conductivity per
-voxel), source positions/moments and random coefficient vectors, all from
+voxel, and a relative permeability for the magnetic tests), source positions/moments and random coefficient vectors, all from
 seeded NumPy PCG64 generators.  The complex permittivity, the susceptibility,
 the Green tensors and everything else the method computes are derived
 independently by each side from these raw inputs.
@@ -15,6 +15,7 @@ from .phantoms import (  # noqa: F401
     body_phantom,
     inclusion_phantom,
     random_tissue,
+    random_permeability,
     ring_dipoles,
     body_dipoles,
     inclusion_dipoles,

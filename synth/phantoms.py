@@ -141,6 +141,19 @@ def random_tissue(grid: Grid, seed, air_fraction=0.2):
     return eps, sig
 
 
+def random_permeability(grid: Grid, seed, nonmagnetic_fraction=0.3):
+    """Independent random relative permeability per voxel, mu = mu_real - i mu_imag with
+    mu_real in [1, 4] and mu_imag in [0, 1], and mu = 1 in some voxels (synthetic
+    magnetodielectric material for the full JM-VIE; tissue itself is non-magnetic)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mr = rng.uniform(1.0, 4.0, grid.shape)
+    mi = rng.uniform(0.0, 1.0, grid.shape)
+    plain = rng.uniform(0.0, 1.0, grid.shape) < nonmagnetic_fraction
+    mr[plain] = 1.0
+    mi[plain] = 0.0
+    return mr, mi
+
+
 def ring_dipoles(n, radius, z=0.0):
     """n z-directed unit (1 A m) Hertzian dipoles equally spaced on a horizontal ring."""
     phi = 2.0 * math.pi * np.arange(n) / n
