@@ -383,6 +383,10 @@ typedef struct {
     double queued_s;   /* seconds from vie_submit to the start of the solve */
     double run_s;      /* seconds of setup, solve and post-processing */
     double resid;      /* largest final relative residual */
+    double start_s, end_s;          /* host span of the request, seconds since vie_server_create */
+    double dev_start_s, dev_end_s;  /* device span: CUDA events on the request's stream before its
+                                       first and after its last kernel, seconds after an event
+                                       recorded at vie_server_create (-1 if unavailable) */
 } vie_result;
 
 /*

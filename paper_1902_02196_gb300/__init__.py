@@ -57,7 +57,8 @@ class vie_request(ctypes.Structure):
 class vie_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("nrhs", ctypes.c_int), ("iterations", ctypes.c_int),
                 ("green_cached", ctypes.c_int), ("queued_s", ctypes.c_double), ("run_s", ctypes.c_double),
-                ("resid", ctypes.c_double)]
+                ("resid", ctypes.c_double), ("start_s", ctypes.c_double), ("end_s", ctypes.c_double),
+                ("dev_start_s", ctypes.c_double), ("dev_end_s", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

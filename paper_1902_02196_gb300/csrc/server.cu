@@ -62,6 +62,7 @@ struct Req {
     size_t work = 0, green = 0;
     int bypassed = 0;
     Clock::time_point t_submit, t_start, t_end;
+    float dev_ms[2] = {-1.f, -1.f};  // device span after the server's reference event
     bool done = false;
     vie_result res{};
 };
@@ -112,6 +113,8 @@ struct vie_server {
     unsigned long long next_id = 1, clock = 0;
     bool stop = false;
     std::vector<std::thread> workers;
+    Clock::time_point t0;          // creation: origin of the host spans
+    cudaEvent_t ref = nullptr;     // recorded at creation: origin of the device spans
 };
 
 namespace {
@@ -219,6 +222,21 @@ int run_request(vie_server* s, Req& r, bool builder, vie_solve_info* info) {
     }
     g.bufs.push_back(pa);
     void* st = h->stream;
+    // device span of the request's work on its stream
+    struct Span {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Span() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } sp;
+    if (s->ref && (cudaEventCreate(&sp.e0) != cudaSuccess || cudaEventCreate(&sp.e1) != cudaSuccess ||
+                   cudaEventRecord(sp.e0, h->stream) != cudaSuccess)) {
+        cudaGetLastError();
+        if (sp.e0) cudaEventDestroy(sp.e0);
+        if (sp.e1) cudaEventDestroy(sp.e1);
+        sp.e0 = sp.e1 = nullptr;
+    }
     SRV_TRY(vie_rhs_dipoles(h, r.nrhs, r.pos.data(), r.mom.data(), e, b, st));
     // flags 4: the request's vie_fields takes no field map, so the solve keeps no point for it
     const int rc = vie_solve(h, r.nrhs, b, x, r.tol, r.restart, r.maxit, r.mode, 4, info, st);
@@ -228,7 +246,13 @@ int run_request(vie_server* s, Req& r, bool builder, vie_solve_info* info) {
     if (r.x_out) VIE_CUDA(cudaMemcpyAsync(r.x_out, x, 16 * n, cudaMemcpyDeviceToHost, h->stream));
     if (r.p_abs_out)
         VIE_CUDA(cudaMemcpyAsync(r.p_abs_out, pa, 8 * (size_t)r.nrhs * h->nv, cudaMemcpyDeviceToHost, h->stream));
+    if (sp.e1 && cudaEventRecord(sp.e1, h->stream) != cudaSuccess) cudaGetLastError();
     VIE_CUDA(cudaStreamSynchronize(h->stream));
+    if (sp.e1 && (cudaEventElapsedTime(&r.dev_ms[0], s->ref, sp.e0) != cudaSuccess ||
+                  cudaEventElapsedTime(&r.dev_ms[1], s->ref, sp.e1) != cudaSuccess)) {
+        cudaGetLastError();
+        r.dev_ms[0] = r.dev_ms[1] = -1.f;
+    }
     if (r.P_abs_out) std::memcpy(r.P_abs_out, P.data(), sizeof(double) * r.nrhs);
     return rc;  // VIE_OK or VIE_NOT_CONVERGED
 }
@@ -257,6 +281,10 @@ void worker(vie_server* s) {
         }
         r->res.queued_s = std::chrono::duration<double>(r->t_start - r->t_submit).count();
         r->res.run_s = std::chrono::duration<double>(r->t_end - r->t_start).count();
+        r->res.start_s = std::chrono::duration<double>(r->t_start - s->t0).count();
+        r->res.end_s = std::chrono::duration<double>(r->t_end - s->t0).count();
+        r->res.dev_start_s = r->dev_ms[0] >= 0.f ? 1e-3 * r->dev_ms[0] : -1.0;
+        r->res.dev_end_s = r->dev_ms[1] >= 0.f ? 1e-3 * r->dev_ms[1] : -1.0;
         r->done = true;
         s->in_use -= r->work;
         auto it = s->cache.find(key_of(*r));
@@ -301,6 +329,14 @@ int vie_server_create(size_t hbm_budget_bytes, int max_concurrent, vie_server** 
     s->device = dev;
     s->budget = hbm_budget_bytes;
     s->slots = max_concurrent;
+    s->t0 = Clock::now();
+    // the origin of the device spans: an event that has completed before any request starts
+    if (cudaEventCreate(&s->ref) != cudaSuccess || cudaEventRecord(s->ref, cudaStreamPerThread) != cudaSuccess ||
+        cudaEventSynchronize(s->ref) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->ref) cudaEventDestroy(s->ref);
+        s->ref = nullptr;
+    }
     for (int i = 0; i < max_concurrent; ++i) s->workers.emplace_back(worker, s);
     *out = s;
     return VIE_OK;
@@ -317,6 +353,7 @@ void vie_server_destroy(vie_server* s) {
     for (auto& t : s->workers) t.join();
     for (auto& kv : s->cache)
         if (kv.second.tmpl) vie_destroy(kv.second.tmpl);
+    if (s->ref) cudaEventDestroy(s->ref);
     delete s;
 }
 

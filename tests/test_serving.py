@@ -77,6 +77,16 @@ def test_mix_equals_alone_and_direct_calls(vie):
     # requests 0 and 2 share one Green cache entry: exactly one of them built it
     assert res_mix[0]["green_cached"] + res_mix[2]["green_cached"] == 1
     assert res_mix[1]["green_cached"] == 0 and res_mix[3]["green_cached"] == 0
+    # the requests were on the device at the same time: with four slots, the device spans (CUDA
+    # events on each request's stream before its first and after its last kernel) of at least
+    # two requests intersect, and so do their host spans
+    spans = [(r["dev_start_s"], r["dev_end_s"]) for r in res_mix]
+    assert all(0.0 <= a < b for a, b in spans), spans
+    pairs = [(i, j) for i in range(4) for j in range(i + 1, 4)
+             if max(spans[i][0], spans[j][0]) < min(spans[i][1], spans[j][1])]
+    assert pairs, spans
+    host = [(r["start_s"], r["end_s"]) for r in res_mix]
+    assert any(max(host[i][0], host[j][0]) < min(host[i][1], host[j][1]) for i, j in pairs), host
     for i, req in enumerate(reqs):
         s1 = vie.Server(max_concurrent=1)
         res1, out1 = run(s1, [req])
