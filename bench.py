@@ -71,6 +71,11 @@ def parse():
                          "times and the mixed-vs-FP64 difference; prints one JSON line")
     ap.add_argument("--no-ref", action="store_true",
                     help="config-run: skip the FP64 reference solve at 1e-10 (the arms' errors are then not reported)")
+    ap.add_argument("--tucker", default="", metavar="NAME",
+                    help="Tucker compression of the Green tensors of a workload (head64, body128): time, ranks, "
+                         "bytes, and the FP64 matvec / mixed solve with the compressed tensors")
+    ap.add_argument("--jm", action="store_true",
+                    help="full JM-VIE: a magnetodielectric sphere at 16^3-32^3 against the Mie series, FP64 solve time")
     ap.add_argument("--cufft-compare", action="store_true",
                     help="time a matvec built from torch.fft (cuFFT) and torch.einsum on the head64 sizes beside "
                          "vie_matvec (timing comparison only; its Green tensor is random data of the right shape)")
@@ -812,6 +817,109 @@ def run_config(args, local):
     print(json.dumps(out), flush=True)
 
 
+def run_tucker(args, local):
+    """Tucker compression (vie_green_tucker) of a workload's Green tensors at tol 1e-6 and 1e-7: device
+    time, ranks, bytes against the full table, and the FP64 matvec and mixed solve before / after."""
+    import numpy as np
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vie.build()
+    w = workload(args.tucker)
+    g = w["grid"]
+    R = int(w["dip_pos"].shape[0])
+    out = dict(mode="tucker", workload=args.tucker, grid=[g.nx, g.ny, g.nz], nrhs=R, data="synthetic",
+               table_bytes=60 * g.nv * 16)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    v = torch.randn((2, 12) + g.shape, dtype=torch.complex128, device=dev, generator=gen)
+    for tol in (1e-6, 1e-7):
+        t0 = time.perf_counter()
+        h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), w["freq"], w["eps_real"], w["sigma"])
+        setup_s = time.perf_counter() - t0
+        _, bytes0 = vie.vie_info(h)
+        y0 = torch.empty_like(v)
+        vie.vie_matvec(h, v, y0, vie.VIE_FP64, vie.VIE_OP_NSCAT)
+        shape = (R, 12) + g.shape
+        e_inc = torch.empty(shape, dtype=torch.complex128, device=dev)
+        b = torch.empty_like(e_inc)
+        vie.vie_rhs_dipoles(h, w["dip_pos"], w["dip_mom"], e_inc, b)
+        x0 = torch.empty_like(b)
+        torch.cuda.synchronize()
+        vie.vie_solve(h, b, x0, tol=TOL, restart=RESTART, maxit=400)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ranks, err, nbytes = vie.vie_green_tucker(h, tol, apply=True)
+        tucker_s = time.perf_counter() - t0
+        _, bytes1 = vie.vie_info(h)
+        y1 = torch.empty_like(v)
+        vie.vie_matvec(h, v, y1, vie.VIE_FP64, vie.VIE_OP_NSCAT)
+        x1 = torch.empty_like(b)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        rc, info = vie.vie_solve(h, b, x1, tol=TOL, restart=RESTART, maxit=400)
+        a1.record()
+        torch.cuda.synchronize()
+        h.close()
+        rs = np.asarray(ranks)
+        out[f"tol_{tol:g}"] = dict(
+            setup_s=setup_s, tucker_s=tucker_s, compressed_bytes=int(nbytes),
+            ratio=out["table_bytes"] / nbytes, max_rel_err=float(np.max(err)),
+            ranks_min=rs.min(0).tolist(), ranks_median=np.median(rs, 0).tolist(), ranks_max=rs.max(0).tolist(),
+            handle_bytes_before=int(bytes0), handle_bytes_after=int(bytes1),
+            matvec_fp64_rel_diff=float(torch.linalg.vector_norm(y1 - y0) / torch.linalg.vector_norm(y0)),
+            solve_rc=rc, solve_s=a0.elapsed_time(a1) / 1000,
+            iterations_max=max(i["iterations"] for i in info),
+            x_rel_diff=float(torch.linalg.vector_norm(x1 - x0) / torch.linalg.vector_norm(x0)))
+    print(json.dumps(out), flush=True)
+
+
+def run_jm(args, local):
+    """Full JM-VIE (vie_jm_*): a magnetodielectric sphere (eps_r 50, sigma 0.5 S/m, mu_r 2 - 0.5 i,
+    radius 0.1 m) in an x-polarised plane wave along z at 298 MHz on 16^3 .. 32^3: FP64 GMRES to
+    1e-8, the absorbed power (electric + magnetic loss) under refinement, and the solve time.  (The
+    comparison with the Mie series is a GPU test.)"""
+    import numpy as np
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import Grid, sphere_phantom
+
+    torch.cuda.set_device(local)
+    vie.build()
+    f, eta0 = 298e6, 1.0 / (8.8541878128e-12 * 299792458.0)
+    mu_s = 2.0 - 0.5j
+    rows = []
+    for n in (16, 24, 32):
+        hgt = 0.2 / n
+        g = Grid(n, n, n, hgt, hgt, hgt)
+        eps, sig = sphere_phantom(g, 0.1, 50.0, 0.5)
+        inside = eps != 1.0
+        h = vie.vie_setup((n, n, n, hgt, hgt, hgt), f, eps, sig)
+        vie.vie_set_permeability(h, np.where(inside, mu_s.real, 1.0), np.where(inside, -mu_s.imag, 0.0))
+        e_t = np.empty((1, 12) + g.shape, dtype=np.complex128)
+        h_t = np.empty_like(e_t)
+        vie.vie_rhs_planewave(h, [1.0, 0.0, 0.0], [0.0, 0.0, 1.0], e_t[0], None)
+        vie.vie_rhs_planewave(h, [0.0, 1.0 / eta0, 0.0], [0.0, 0.0, 1.0], h_t[0], None)
+        b = np.empty((1, 2, 12) + g.shape, dtype=np.complex128)
+        vie.vie_jm_rhs(h, e_t, h_t, b)
+        x = np.empty_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, info = vie.vie_jm_solve(h, b, x, tol=1e-8, restart=60, maxit=40)
+        sec = time.perf_counter() - t0
+        P = vie.vie_jm_fields(h, x, e_t, h_t)[0]
+        h.close()
+        rows.append(dict(n=n, rc=rc, seconds=sec, iterations=info[0]["iterations"], P_abs=P))
+    print(json.dumps(dict(mode="jm", workload="magnetodielectric sphere, plane wave", runs=rows,
+                          data="synthetic")), flush=True)
+
+
 def run_cufft_compare(args, local):
     """cuFFT (torch.fft) + einsum matvec of the head64 batch, timed beside the library's FP32 matvec."""
     import torch
@@ -882,6 +990,14 @@ def main():
     if args.config_run:
         if rank == 0:
             run_config(args, local)
+        return
+    if args.tucker:
+        if rank == 0:
+            run_tucker(args, local)
+        return
+    if args.jm:
+        if rank == 0:
+            run_jm(args, local)
         return
     if args.serving:
         if rank == 0:

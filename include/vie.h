@@ -273,9 +273,33 @@ int vie_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, void* 
  * out[t][dz][dy][dx] C128 with t = 10 * pq + ll, pq indexing the unordered
  * vector pair (xx,xy,xz,yy,yz,zz) and ll the ordered scalar pair l <= l'
  * ((1,1),(1,2),(1,3),(1,4),(2,2),(2,3),(2,4),(3,3),(3,4),(4,4)) (Section III-C: 6 x 10 = 60).
- * Entries for negative offsets follow from the reflection parities.  Synchronous.
+ * Entries for negative offsets follow from the reflection parities.  After vie_green_tucker with
+ * VIE_TUCKER_APPLY the table is the Tucker reconstruction.  Synchronous.
  */
 int vie_green_toeplitz(vie_handle* h, void* out);
+
+/*
+ * vie_green_tucker -- low multilinear rank (Tucker) compression of the handle's 60 Toeplitz
+ * tensors of N - G (Section III-C: the defining tensors compress by low multilinear rank
+ * decompositions).  Each tensor T [nz][ny][nx] becomes a core C [rz][ry][rx] and orthonormal
+ * factors U_x [nx][rx], U_y [ny][ry], U_z [nz][rz], T~ = C x_z U_z x_y U_y x_x U_x, with
+ * ||T - T~||_F <= tol ||T||_F: every factor spans its mode's unfolding up to a discarded energy of
+ * tol^2 ||T||^2 / 3 (range from the unfolding's Gram matrix by pivoted Cholesky, so the ranks are
+ * at least, and usually close to, those of the truncated HOSVD).  FP64 on the device.
+ *   tol   : relative tolerance in [1e-7, 1) (the Gram matrices square the singular values, so
+ *           smaller tolerances are not resolved in FP64)
+ *   flags : VIE_TUCKER_APPLY = rebuild the handle's Green spectra from T~ (every later matvec
+ *           and solve uses the compressed Green function) and keep the Tucker form in place of
+ *           the full table (vie_green_toeplitz then returns T~; vie_info's bytes drop by the
+ *           difference).  Without it the handle is unchanged apart from holding the form.
+ *   ranks : int[60][3] host output (rx, ry, rz) per tensor, or NULL
+ *   rel_err : double[60] host output ||T - T~||_F / ||T||_F per tensor, or NULL
+ *   compressed_bytes : bytes of the Tucker form (cores and factors), or NULL
+ * The K tensors are not compressed.  Synchronous.  Errors: VIE_EINVAL (tol out of range, a handle
+ * sharing a server template's tensors), VIE_ENOMEM.
+ */
+#define VIE_TUCKER_APPLY 1
+int vie_green_tucker(vie_handle* h, double tol, int flags, int* ranks, double* rel_err, size_t* compressed_bytes);
 
 /*
  * vie_green_toeplitz_k -- the 30 unique Toeplitz tensors of the K operator, K u = curl S u
@@ -317,6 +341,71 @@ int vie_rhs_dipoles_h(vie_handle* h, int nrhs, const double* pos, const double* 
  */
 int vie_hfields(vie_handle* h, int nrhs, const void* x, const void* h_inc, void* h_coeff, void* b1_plus, double* W_m,
                 void* stream);
+
+/*
+ * Full JM-VIE (Eq. 14-15): polarization current j and magnetization current m of a scatterer
+ * with relative permeability mu_r = mu' - i mu'' (Eq. 1-2; chi_m = mu_r - 1, Eq. 7).  PWL
+ * handles only, FP64 throughout (the K products are those of VIE_OP_K).
+ *
+ * Unknowns: both currents in the PWL functions of Section III, with the magnetization scaled,
+ * m' = m / eta0 (eta0 = sqrt(mu0/eps0)), and the second row of Eq. 15 divided by eta0.  Since
+ * c_e eta0 = c_m / eta0 = i k0 the Galerkin system reads
+ *     [ M_eps G - M_chie N      i k0 M_chie K      ] [j ]   [ c_e M_chie e_inc  ]
+ *     [ -i k0 M_chim K          M_mu G - M_chim N  ] [m'] = [ i k0 M_chim h_inc ]
+ * (the same solution as Eq. 15, with m = eta0 m'), preconditioned by P = diag(M_eps G, M_mu G).
+ * Vectors of this system: [nrhs][2][12][nz][ny][nx] C128, index 0 of the axis of length 2 = j,
+ * index 1 = m'.  With mu_r = 1 the second current vanishes and j solves Eq. 16.
+ * Host or device buffers as for vie_matvec; vie_jm_matvec and vie_jm_rhs follow the stream rule
+ * above, vie_jm_solve and vie_jm_fields are synchronous.  Scratch: 2 x 24 nrhs nv complex values
+ * for the two products plus the K path's padded spectra (VIE_OP_K).
+ */
+
+/*
+ * vie_set_permeability -- relative permeability per voxel, mu_r = mu_real - i mu_imag
+ * (mu_real > 0, mu_imag >= 0, finite; [nz][ny][nx] doubles, host or device).  Until it is
+ * called the JM calls take mu_r = 1.  Errors: VIE_EINVAL (NULL, a PWC handle, an entry out of
+ * range), VIE_ENOMEM.
+ */
+int vie_set_permeability(vie_handle* h, const double* mu_real, const double* mu_imag);
+
+/*
+ * vie_jm_matvec -- y = A x (op VIE_OP_A) or y = P^-1 A x (op VIE_OP_PA) of the JM system above
+ * for nrhs vectors.  x and y must not overlap.
+ */
+int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int op, void* stream);
+
+/*
+ * vie_jm_rhs -- right-hand sides b = (c_e chi_e e_inc, i k0 chi_m h_inc) (Eq. 14, second row
+ * divided by eta0) from tested incident fields e_inc, h_inc [nrhs][12][nz][ny][nx] C128
+ * (vie_rhs_dipoles / vie_rhs_planewave and vie_rhs_dipoles_h); b: [nrhs][2][12][nz][ny][nx].
+ */
+int vie_jm_rhs(vie_handle* h, int nrhs, const void* e_inc, const void* h_inc, void* b, void* stream);
+
+/*
+ * vie_jm_solve -- restarted GMRES(restart) on P^-1 A x = P^-1 b of the JM system, FP64, with the
+ * batched device Arnoldi steps of vie_solve (the restart cycles launched directly, not as CUDA
+ * graphs), stopping when ||P^-1 (b - A x)|| / ||P^-1 b|| <= tol.  The solver's vectors cover the
+ * voxels where chi_e, chi_m, b or the guess is non-zero (rows of the grid as for vie_solve).
+ *   b, x  : [nrhs][2][12][nz][ny][nx] C128; x is the initial guess when (flags & 1)
+ *   flags : bit 0 = use x as initial guess; bit 1 = also compute true_resid (||b - A x|| / ||b||)
+ *   info  : vie_solve_info[nrhs] or NULL
+ * Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
+ */
+int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int flags,
+                 vie_solve_info* info, void* stream);
+
+/*
+ * vie_jm_fields -- total fields of the JM solution (Eq. 13, tested, then divided by G):
+ *   e = (e_inc + (1/c_e)(N - G) j - eta0 K m') / G,   h = (h_inc + K j + (1/(i k0))(N - G) m') / G,
+ * and the absorbed power, electric plus magnetic loss:
+ *   P_abs = 1/2 Re{ j^* (c_e M_chie)^-1 G j } + 1/2 Re{ eta0 m'^* (i k0 M_chim)^-1 G m' }
+ * (Eq. 44 and its magnetic analogue, 1/2 int omega mu0 mu'' |h|^2), per voxel in W/m^3 and summed.
+ *   x            : [nrhs][2][12][nz][ny][nx] C128;  e_inc, h_inc : [nrhs][12][nz][ny][nx] C128
+ *   e_coeff, h_coeff : [nrhs][12][nz][ny][nx] C128 outputs or NULL
+ *   p_abs        : double[nrhs][nz][ny][nx] output or NULL;  P_abs : double[nrhs] host output or NULL
+ */
+int vie_jm_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, const void* h_inc, void* e_coeff,
+                  void* h_coeff, double* p_abs, double* P_abs, void* stream);
 
 /* Sizes used by the handle: FFT lengths per axis and bytes of device memory held. */
 int vie_info(vie_handle* h, int* fft_len_xyz, size_t* device_bytes);

@@ -23,11 +23,13 @@ VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT, VIE_OP_K = 0, 1, 2, 3
 VIE_SOLVE_FP64, VIE_SOLVE_FP32_REFINE, VIE_SOLVE_BF16X3_REFINE = 0, 1, 2
 VIE_INJECT_NONE, VIE_INJECT_OOM = 0, 1
 VIE_SETUP_PWC = 1
+VIE_TUCKER_APPLY = 1
 
 EXPORTS = (
     "vie_setup", "vie_setup_green_external", "vie_destroy", "vie_matvec", "vie_rhs_planewave", "vie_rhs_dipoles", "vie_solve",
     "vie_fields", "vie_green_toeplitz", "vie_green_toeplitz_k", "vie_rhs_dipoles_h", "vie_hfields", "vie_info", "vie_strerror", "vie_last_error",
     "vie_stats_reset", "vie_stats_read", "vie_matvec_noalloc", "vie_fault_inject", "vie_tuning",
+    "vie_set_permeability", "vie_jm_matvec", "vie_jm_rhs", "vie_jm_solve", "vie_jm_fields", "vie_green_tucker",
     "vie_server_create", "vie_server_destroy", "vie_submit", "vie_poll", "vie_server_stats",
 )
 
@@ -105,6 +107,12 @@ def _lib():
     lib.vie_rhs_dipoles_h.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D), P, P]
     lib.vie_hfields.argtypes = [P, I, P, P, P, P, ctypes.POINTER(D), P]
     lib.vie_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(S)]
+    lib.vie_set_permeability.argtypes = [P, P, P]
+    lib.vie_green_tucker.argtypes = [P, D, I, P, P, ctypes.POINTER(S)]
+    lib.vie_jm_matvec.argtypes = [P, I, P, P, I, P]
+    lib.vie_jm_rhs.argtypes = [P, I, P, P, P, P]
+    lib.vie_jm_solve.argtypes = [P, I, P, P, D, I, I, I, ctypes.POINTER(vie_solve_info), P]
+    lib.vie_jm_fields.argtypes = [P, I, P, P, P, P, P, P, ctypes.POINTER(D), P]
     lib.vie_strerror.argtypes = [I]
     lib.vie_strerror.restype = ctypes.c_char_p
     lib.vie_stats_reset.argtypes = [I]
@@ -285,8 +293,68 @@ def vie_hfields(h, x, h_inc, h_coeff=None, b1_plus=None, stream=None):
     return list(W)
 
 
+def _nrhs_jm(a, h):
+    """Right-hand sides in a JM-VIE vector batch [R][2][12][nz][ny][nx]."""
+    n = 1
+    for d in a.shape:
+        n *= int(d)
+    if n % (24 * h.nv):
+        raise ValueError("array size is not a multiple of 24 * N_V")
+    return n // (24 * h.nv)
+
+
+def vie_set_permeability(h, mu_real, mu_imag):
+    """Relative permeability mu_r = mu_real - i mu_imag per voxel, float64 [nz][ny][nx]."""
+    return _check(_lib().vie_set_permeability(h.ptr, _ptr(mu_real), _ptr(mu_imag)), "vie_set_permeability")
+
+
+def vie_jm_matvec(h, x, y, op=VIE_OP_A, stream=None):
+    """y = A x or P^-1 A x of the full JM-VIE system, x, y [R][2][12][nz][ny][nx] complex128."""
+    return _check(_lib().vie_jm_matvec(h.ptr, _nrhs_jm(x, h), _ptr(x), _ptr(y), int(op), _stream(stream)),
+                  "vie_jm_matvec")
+
+
+def vie_jm_rhs(h, e_inc, h_inc, b, stream=None):
+    """b = (c_e chi_e e_inc, i k0 chi_m h_inc) into b [R][2][12][nz][ny][nx]."""
+    return _check(_lib().vie_jm_rhs(h.ptr, _nrhs(e_inc, h), _ptr(e_inc), _ptr(h_inc), _ptr(b), _stream(stream)),
+                  "vie_jm_rhs")
+
+
+def vie_jm_solve(h, b, x, tol=1e-6, restart=50, maxit=200, guess=False, true_resid=False, stream=None):
+    """FP64 GMRES on the JM system; returns (rc, [info dict per right-hand side])."""
+    n = _nrhs_jm(b, h)
+    info = (vie_solve_info * n)()
+    flags = (1 if guess else 0) | (2 if true_resid else 0)
+    rc = _check(_lib().vie_jm_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), flags, info,
+                                    _stream(stream)), "vie_jm_solve")
+    return rc, [i.as_dict() for i in info]
+
+
+def vie_jm_fields(h, x, e_inc, h_inc, e_coeff=None, h_coeff=None, p_abs=None, stream=None):
+    """Field coefficients and absorbed power of a JM solution; returns P_abs (W) per right-hand side."""
+    n = _nrhs_jm(x, h)
+    P = (ctypes.c_double * n)()
+    _check(_lib().vie_jm_fields(h.ptr, n, _ptr(x), _ptr(e_inc), _ptr(h_inc), _ptr(e_coeff), _ptr(h_coeff),
+                                _ptr(p_abs), P, _stream(stream)), "vie_jm_fields")
+    return list(P)
+
+
 def vie_green_toeplitz(h, out):
     return _check(_lib().vie_green_toeplitz(h.ptr, _ptr(out)), "vie_green_toeplitz")
+
+
+def vie_green_tucker(h, tol, apply=False):
+    """Tucker compression of the handle's 60 Toeplitz tensors; returns (ranks [60][3] as (rx, ry, rz),
+    relative errors [60], compressed bytes).  apply=True: the Green spectra are rebuilt from the
+    compressed tensors (VIE_TUCKER_APPLY)."""
+    import numpy as np
+
+    ranks = np.zeros((60, 3), dtype=np.int32)
+    err = np.zeros(60)
+    nb = ctypes.c_size_t()
+    _check(_lib().vie_green_tucker(h.ptr, float(tol), VIE_TUCKER_APPLY if apply else 0, ranks.ctypes.data,
+                                   err.ctypes.data, ctypes.byref(nb)), "vie_green_tucker")
+    return ranks, err, nb.value
 
 
 def vie_green_toeplitz_k(h, out):

@@ -115,12 +115,15 @@ void release(vie_handle* h) {
         cudaFree(h->tw32);
         cudaFree(h->toeplitz);
     }
+    cudaFree(h->tucker);
     cudaFree(h->fft_ws.ptr);
     cudaFree(h->stage_ws.ptr);
     cudaFree(h->solve_ws.ptr);
     cudaFree(h->support_ws.ptr);
     cudaFree(h->post_ws.ptr);
     cudaFree(h->fcache_ws.ptr);
+    cudaFree(h->mu64);  // one allocation holds mu64, chim64, imu64 and jmsup64
+    cudaFree(h->jm_ws.ptr);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -468,8 +471,27 @@ int vie_green_toeplitz(vie_handle* h, void* out) {
     REQUIRE(h && out, "NULL argument");
     const size_t bytes = 60 * h->nv * sizeof(double2);
     VIE_CUDA(cudaStreamSynchronize(h->stream));
-    VIE_CUDA(cudaMemcpy(out, h->toeplitz, bytes, cudaMemcpyDefault));
-    return VIE_OK;
+    if (h->toeplitz) {
+        VIE_CUDA(cudaMemcpy(out, h->toeplitz, bytes, cudaMemcpyDefault));
+        return VIE_OK;
+    }
+    // the handle keeps the Tucker form only: reconstruct
+    Stager sg{h, h->stream};
+    sg.add(out, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(tucker_reconstruct(h, static_cast<double2*>(d[0]), h->stream));
+    return sg.finish(d);
+}
+
+int vie_green_tucker(vie_handle* h, double tol, int flags, int* ranks, double* rel_err, size_t* compressed_bytes) {
+    g_last_error.clear();
+    REQUIRE(h, "NULL handle");
+    REQUIRE(std::isfinite(tol) && tol >= 1e-7 && tol < 1, "tol must be in [1e-7, 1)");
+    REQUIRE((flags & ~VIE_TUCKER_APPLY) == 0, "unknown flags");
+    REQUIRE(!h->shared_green, "the handle shares another handle's Green tensors");
+    VIE_CUDA(cudaStreamSynchronize(h->stream));
+    return green_tucker(h, tol, (flags & VIE_TUCKER_APPLY) != 0, ranks, rel_err, compressed_bytes);
 }
 
 int vie_rhs_dipoles_h(vie_handle* h, int nrhs, const double* pos, const double* mom, void* h_inc, void* stream) {
@@ -505,6 +527,122 @@ int vie_hfields(vie_handle* h, int nrhs, const void* x, const void* h_inc, void*
     VIE_TRY(sg.bind(d));
     VIE_TRY(hfields_device(h, nrhs, static_cast<const double2*>(d[0]), static_cast<const double2*>(d[1]),
                            static_cast<double2*>(d[2]), static_cast<double2*>(d[3]), W_m, st));
+    return sg.finish(d);
+}
+
+int vie_set_permeability(vie_handle* h, const double* mu_real, const double* mu_imag) {
+    g_last_error.clear();
+    REQUIRE(h && mu_real && mu_imag, "NULL argument");
+    REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
+    std::vector<double> mr(h->nv), mi(h->nv);
+    const bool dev_in = is_device_ptr(mu_real);
+    if (dev_in) {
+        VIE_CUDA(cudaMemcpy(mr.data(), mu_real, sizeof(double) * h->nv, cudaMemcpyDeviceToHost));
+        VIE_CUDA(cudaMemcpy(mi.data(), mu_imag, sizeof(double) * h->nv, cudaMemcpyDefault));
+    } else {
+        std::memcpy(mr.data(), mu_real, sizeof(double) * h->nv);
+        std::memcpy(mi.data(), mu_imag, sizeof(double) * h->nv);
+    }
+    for (size_t m = 0; m < h->nv; ++m)
+        REQUIRE(std::isfinite(mr[m]) && std::isfinite(mi[m]) && mr[m] > 0.0 && mi[m] >= 0.0,
+                "permeability entry " + std::to_string(m) + " is not finite or out of range");
+    double* d = nullptr;
+    VIE_CUDA(cudaMalloc(&d, 2 * sizeof(double) * h->nv));
+    int rc = VIE_OK;
+    if (cudaMemcpy(d, mr.data(), sizeof(double) * h->nv, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + h->nv, mi.data(), sizeof(double) * h->nv, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cannot stage the permeability maps");
+        rc = VIE_EDEVICE;
+    }
+    if (rc == VIE_OK) rc = jm_materials(h, d, d + h->nv, h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    return rc;
+}
+
+int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int op, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && x && y, "NULL argument");
+    REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    REQUIRE(op == VIE_OP_A || op == VIE_OP_PA, "unknown operator (VIE_OP_A or VIE_OP_PA)");
+    REQUIRE(x != y, "x and y must not overlap");
+    const size_t bytes = (size_t)nrhs * 24 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(x, bytes, false);
+    sg.add(y, bytes, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(jm_matvec_full(h, nrhs, static_cast<const double2*>(d[0]), static_cast<double2*>(d[1]), op, st));
+    return sg.finish(d);
+}
+
+int vie_jm_rhs(vie_handle* h, int nrhs, const void* e_inc, const void* h_inc, void* b, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && e_inc && h_inc && b, "NULL argument");
+    REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    const size_t half = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(e_inc, half, false);
+    sg.add(h_inc, half, false);
+    sg.add(b, 2 * half, true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(jm_rhs_device(h, nrhs, static_cast<const double2*>(d[0]), static_cast<const double2*>(d[1]),
+                          static_cast<double2*>(d[2]), st));
+    return sg.finish(d);
+}
+
+int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int flags,
+                 vie_solve_info* info, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && b && x, "NULL argument");
+    REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    REQUIRE(std::isfinite(tol) && tol > 0 && tol < 1, "tol must be in (0, 1)");
+    REQUIRE(restart >= 1 && restart <= 128, "restart must be in [1, 128]");
+    REQUIRE(maxit >= 1, "maxit must be >= 1");
+    REQUIRE((flags & ~3) == 0, "unknown flags");
+    const size_t bytes = (size_t)nrhs * 24 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(b, bytes, false);
+    sg.add(x, bytes, (flags & 1) ? false : true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    sg.items[1].is_out = true;
+    int rc = solve_device(h, nrhs, (const double2*)d[0], (double2*)d[1], tol, restart, maxit, VIE_SOLVE_FP64,
+                          flags | 4, info, st, true);
+    if (rc < 0) return rc;
+    VIE_TRY(sg.finish(d));
+    VIE_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int vie_jm_fields(vie_handle* h, int nrhs, const void* x, const void* e_inc, const void* h_inc, void* e_coeff,
+                  void* h_coeff, double* p_abs, double* P_abs, void* stream) {
+    g_last_error.clear();
+    REQUIRE(h && x && e_inc && h_inc, "NULL argument");
+    REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
+    REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    const size_t half = (size_t)nrhs * 12 * h->nv * sizeof(double2);
+    cudaStream_t st = pick(h, stream);
+    Stager sg{h, st};
+    sg.add(x, 2 * half, false);
+    sg.add(e_inc, half, false);
+    sg.add(h_inc, half, false);
+    sg.add(e_coeff, half, true);
+    sg.add(h_coeff, half, true);
+    sg.add(p_abs, (size_t)nrhs * h->nv * sizeof(double), true);
+    std::vector<void*> d;
+    VIE_TRY(sg.bind(d));
+    VIE_TRY(jm_fields_device(h, nrhs, static_cast<const double2*>(d[0]), static_cast<const double2*>(d[1]),
+                             static_cast<const double2*>(d[2]), static_cast<double2*>(d[3]),
+                             static_cast<double2*>(d[4]), static_cast<double*>(d[5]), P_abs, st));
     return sg.finish(d);
 }
 

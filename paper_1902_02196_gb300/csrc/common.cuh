@@ -145,7 +145,18 @@ struct vie_handle {
     Workspace fcache_ws;
     int fcache_R;
     int fcache_valid;
-    double2* toeplitz;   // [60][nz][ny][nx] Toeplitz tensors of N - G for offsets d >= 0
+    // full JM-VIE (jmvie.cu), allocated together on first use: relative permeability mu, chi_m = mu - 1,
+    // 1/mu and the support indicator |chi_e| + |chi_m|, each [nz][ny][nx] (mu = 1 until set)
+    double2 *mu64, *chim64, *imu64, *jmsup64;
+    Workspace jm_ws;  // (N - G) x and K x of the stacked currents
+    double2* toeplitz;   // [60][nz][ny][nx] Toeplitz tensors of N - G for offsets d >= 0 (NULL once a
+                         // Tucker form replaced it, see tucker.cu)
+    // Tucker form of the 60 tensors (tucker.cu): per tensor t at element offset tucker_off[t] the
+    // core [rz][ry][rx], then U_z [nz][rz], U_y [ny][ry], U_x [nx][rx]; tucker_rank[t] = (rx, ry, rz)
+    void* tucker;
+    size_t tucker_bytes;
+    long long tucker_off[60];
+    int tucker_rank[60][3];
     size_t bytes_held;
     // set when green64/32/32t, toeplitz, the twiddle tables and colmap belong to another
     // handle (a template kept in a server's Green cache) and must not be freed with this one
@@ -283,13 +294,26 @@ int support_scatter(const vie_handle* h, int nrhs, const void* part, void* full,
                     cudaStream_t s);
 // full 3-D FFT of `batch` complex double volumes [batch][Lz][Ly][Lx] in place (forward, unscaled)
 int fft3d_inplace64(vie_handle* h, double2* data, int batch, cudaStream_t s);
+// jm: the full JM-VIE system (jmvie.cu; FP64 mode only), vectors [nrhs][2][12][nz][ny][nx]
 int solve_device(vie_handle* h, int nrhs, const double2* b, double2* x, double tol, int restart, int maxit,
-                 int mode, int flags, vie_solve_info* info, cudaStream_t s);
+                 int mode, int flags, vie_solve_info* info, cudaStream_t s, bool jm = false);
 int rhs_planewave_device(vie_handle* h, const double pol[3], const double dir[3], double2* e, double2* b,
                          cudaStream_t s);
 int rhs_dipoles_device(vie_handle* h, int nrhs, const double* pos, const double* mom, double2* e, double2* b,
                        cudaStream_t s);
 int materials_device(vie_handle* h, const double* eps_real, const double* sigma, cudaStream_t s);
+// jmvie.cu: the full JM-VIE (Eq. 14-15), FP64.  Vectors [R][2][12][nz][ny][nx] (j, then m' = m / eta0).
+int jm_materials(vie_handle* h, const double* mu_real, const double* mu_imag, cudaStream_t s);  // device maps or NULL
+int jm_matvec_full(vie_handle* h, int R, const double2* x, double2* y, int op, cudaStream_t s,
+                   const double2* shift = nullptr);
+int jm_matvec_support(vie_handle* h, int R, const double2* x, double2* y, int op, const Support& sp, void* tmp,
+                      cudaStream_t s, const double2* shift);
+int jm_rhs_device(vie_handle* h, int R, const double2* einc, const double2* hinc, double2* b, cudaStream_t s);
+int jm_fields_device(vie_handle* h, int R, const double2* x, const double2* einc, const double2* hinc, double2* eout,
+                     double2* hout, double* p_abs, double* P_abs_host, cudaStream_t s);
+// tucker.cu: Tucker compression of the handle's Green tensors (vie_green_tucker) and its reconstruction
+int green_tucker(vie_handle* h, double tol, bool apply, int* ranks, double* err, size_t* bytes);
+int tucker_reconstruct(vie_handle* h, double2* out, cudaStream_t s);
 int fields_device(vie_handle* h, int nrhs, const double2* x, const double2* e_inc, double2* e_out, double* p_abs,
                   double* P_abs_host, cudaStream_t s);
 

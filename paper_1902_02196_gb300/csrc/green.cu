@@ -575,7 +575,7 @@ static int quad_tables() {
     return VIE_OK;
 }
 
-int green_embed(vie_handle* h, double2* T);
+int green_embed(vie_handle* h, double2* T, bool keep_table = true);
 
 int green_setup(vie_handle* h) {
     VIE_TRY(quad_tables());
@@ -626,9 +626,10 @@ int green_setup(vie_handle* h) {
 }
 
 // Circulant embedding, 3-D FFT and octant storage of the 60 Toeplitz tensors T [60][nz][ny][nx]
-// (device, N - G at offsets d >= 0) in FP64 and FP32 (Section IV-A); the handle keeps T for
-// vie_green_toeplitz (it takes ownership of T, also on failure).
-int green_embed(vie_handle* h, double2* T) {
+// (device, N - G at offsets d >= 0) in FP64 and FP32 (Section IV-A).  Takes ownership of T, also
+// on failure: the handle keeps it for vie_green_toeplitz when keep_table is set, else frees it.
+// The spectra are allocated on the first call and overwritten by later ones.
+int green_embed(vie_handle* h, double2* T, bool keep_table) {
     cudaStream_t s = h->stream;
     const long long nd = (long long)h->nx * h->ny * h->nz;
     double2* C = nullptr;
@@ -641,13 +642,15 @@ int green_embed(vie_handle* h, double2* T) {
     const int Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
     const long long vol = (long long)Lx * Ly * Lz;
     const long long ovol = (long long)h->O[0] * h->O[1] * h->O[2];
-    if (cudaMalloc(&h->green64, sizeof(double2) * 60 * ovol) != cudaSuccess ||
-        cudaMalloc(&h->green32, sizeof(float2) * 60 * ovol) != cudaSuccess ||
-        cudaMalloc(&h->green32t, sizeof(float2) * 60 * ovol) != cudaSuccess ||
-        cudaMalloc(&h->green64t, sizeof(double2) * 60 * ovol) != cudaSuccess ||
-        cudaMalloc(&h->greenbf, sizeof(uint2) * 60 * ovol) != cudaSuccess)
-        return fail((set_error("green alloc"), VIE_ENOMEM));
-    h->bytes_held += (2 * sizeof(double2) + 2 * sizeof(float2) + sizeof(uint2)) * 60 * ovol;
+    if (!h->green64) {
+        if (cudaMalloc(&h->green64, sizeof(double2) * 60 * ovol) != cudaSuccess ||
+            cudaMalloc(&h->green32, sizeof(float2) * 60 * ovol) != cudaSuccess ||
+            cudaMalloc(&h->green32t, sizeof(float2) * 60 * ovol) != cudaSuccess ||
+            cudaMalloc(&h->green64t, sizeof(double2) * 60 * ovol) != cudaSuccess ||
+            cudaMalloc(&h->greenbf, sizeof(uint2) * 60 * ovol) != cudaSuccess)
+            return fail((set_error("green alloc"), VIE_ENOMEM));
+        h->bytes_held += (2 * sizeof(double2) + 2 * sizeof(float2) + sizeof(uint2)) * 60 * ovol;
+    }
     int chunk = (int)std::max<long long>(1, std::min<long long>(60, (4LL << 30) / (vol * (long long)sizeof(double2))));
     if (cudaMalloc(&C, sizeof(double2) * vol * chunk) != cudaSuccess) return fail((set_error("embed alloc"), VIE_ENOMEM));
     for (int t0 = 0; t0 < 60; t0 += chunk) {
@@ -667,6 +670,10 @@ int green_embed(vie_handle* h, double2* T) {
     if (rc < 0) return fail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail((set_error("green setup sync"), VIE_EDEVICE));
     cudaFree(C);
+    if (!keep_table) {
+        cudaFree(T);
+        return VIE_OK;
+    }
     // The Toeplitz table is kept for inspection (vie_green_toeplitz)
     h->toeplitz = T;
     h->bytes_held += sizeof(double2) * 60 * nd;

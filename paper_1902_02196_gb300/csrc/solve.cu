@@ -331,15 +331,19 @@ __global__ void sub_kernel(const double2* __restrict__ a, const double2* __restr
     out[e] = make_double2(a[e].x - b[e].x, a[e].y - b[e].y);
 }
 
-// b~ = P^-1 b = b / (eps G_alpha)
-__global__ void precond_rhs_kernel(const double2* __restrict__ b, const double2* __restrict__ ieps, double2* out,
-                                   long long nv, int R, int nc, double g1, double g234) {
+// b~ = P^-1 b = b / (eps G_alpha); for the JM system (imu != NULL, nc = 24) the magnetization
+// components 12..23 are divided by mu G_alpha instead
+__global__ void precond_rhs_kernel(const double2* __restrict__ b, const double2* __restrict__ ieps,
+                                   const double2* __restrict__ imu, double2* out, long long nv, int R, int nc,
+                                   double g1, double g234) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nv * nc * R) return;
     const long long vox = e % nv;
-    const int alpha = (int)((e / nv) % nc);
-    const double ig = 1.0 / (comp_is_constant(alpha, nc) ? g1 : g234);
-    const double2 v = b[e], c = ieps[vox];
+    int alpha = (int)((e / nv) % nc);
+    const bool mag = imu && alpha >= 12;
+    if (imu) alpha %= 12;
+    const double ig = 1.0 / (comp_is_constant(alpha, imu ? 12 : nc) ? g1 : g234);
+    const double2 v = b[e], c = mag ? imu[vox] : ieps[vox];
     out[e] = make_double2(ig * (v.x * c.x - v.y * c.y), ig * (v.x * c.y + v.y * c.x));
 }
 
@@ -610,14 +614,17 @@ __global__ void support_rows_kernel(const double2* __restrict__ chi, const doubl
 // Support of a solve (Section III: unknowns where chi = 0 vanish when b does, since those
 // rows of P^-1 A are the identity): rows of the grid restricted to the voxels where chi,
 // b or the guess is non-zero; the full grid when that covers every voxel.
-int build_support(vie_handle* h, int R, const double2* b, const double2* guess, Support* sp, cudaStream_t st) {
+// chi: the material indicator (non-zero where the operator differs from the identity);
+// ncomp: planes of nv values per right-hand side in b and the guess.
+int build_support(vie_handle* h, int R, const double2* b, const double2* guess, Support* sp, cudaStream_t st,
+                  const double2* chi, int ncomp) {
     const long long nrows = (long long)h->ny * h->nz;
     VIE_TRY(ws_reserve(h, h->support_ws, sizeof(int4) * (size_t)nrows + sizeof(int2) * (size_t)nrows));
     int4* rows = static_cast<int4*>(h->support_ws.ptr);
     int2* span = reinterpret_cast<int2*>(rows + nrows);
     const unsigned g = (unsigned)((nrows + 7) / 8);
     VIE_KLAUNCH("support_rows", st,
-                support_rows_kernel<<<g, 256, 0, st>>>(h->chi64, b, guess, R * h->nc, h->nx, nrows, (long long)h->nv,
+                support_rows_kernel<<<g, 256, 0, st>>>(chi, b, guess, R * ncomp, h->nx, nrows, (long long)h->nv,
                                                        span));
     VIE_CHECK_LAUNCH();
     std::vector<int2> hs(nrows);
@@ -661,6 +668,7 @@ struct Solver {
     vie_handle* h;
     cudaStream_t st = nullptr;
     bool use_graph = false;
+    bool jm = false;  // the full JM-VIE system (FP64, two currents per voxel)
     // per matvec precision (VIE_FP64, VIE_FP32, VIE_BF16X3): the chunks of a cycle, then its end
     CycleGraph graph[3][kMaxChunks + 1];
     int* pinned = nullptr;                // [kMaxChunks] active counts after each chunk (pinned host memory)
@@ -739,8 +747,12 @@ int enqueue_steps(Solver& S, VC* U, const double2* r64, const double* rn2, int p
         VC* uj = U + j * ustride;
         VC* w = U + (j + 1) * ustride;
         // only the active right-hand sides (the others' w is never read)
-        VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift, nullptr,
-                               S.gs.nactive + 1, S.gs.nactive));
+        if (S.jm)  // every right-hand side transformed (the others' w is never read)
+            VIE_TRY(jm_matvec_support(h, R, reinterpret_cast<const double2*>(uj), reinterpret_cast<double2*>(w),
+                                      VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift));
+        else
+            VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift, nullptr,
+                                   S.gs.nactive + 1, S.gs.nactive));
         VIE_TRY(S.dots<VC>(U, ustride, w, j + 1, S.gs.active));
         VIE_KLAUNCH("arnoldi_coef", st, coef1_kernel<<<R, 128, 0, st>>>(S.gs, R, j));
         VIE_TRY(S.update<VC>(U, ustride, w, j + 1, S.gs.active));
@@ -872,24 +884,33 @@ int krylov_residual(Solver& S, const VC* U, double2* r64, double* rn2, int* k1) 
 }  // namespace
 
 int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol, int m, int maxit, int mode,
-                 int flags, vie_solve_info* info, cudaStream_t st) {
+                 int flags, vie_solve_info* info, cudaStream_t st, bool jm) {
     if (m + 2 > kMaxV) {
         set_error("restart above 128 is not supported");
         return VIE_EINVAL;
     }
     h->fcache_valid = 0;  // a new solve replaces the point kept for vie_fields
-    const bool keep = !(flags & 4);
-    // vectors live on the support of the solve: [R][nc][ns] (nc = 12 PWL, 3 PWC)
+    // the JM system (FP64 only): unknowns per voxel 24 = two currents of 12, copied to and from the
+    // support as 2R vectors of 12 components; no point is kept for vie_fields
+    if (jm && mode != VIE_SOLVE_FP64) {
+        set_error("the JM-VIE system is solved in FP64 only");
+        return VIE_EINVAL;
+    }
+    if (jm && !h->mu64) VIE_TRY(jm_materials(h, nullptr, nullptr, st));
+    const int ncs = jm ? 24 : h->nc;  // unknowns per voxel of the system
+    const int Rv = jm ? 2 * R : R;     // right-hand sides as the support copies see them
+    const bool keep = !(flags & 4) && !jm;
+    // vectors live on the support of the solve: [R][ncs][ns] (ncs = 12 PWL, 3 PWC, 24 JM)
     Support sp;
-    VIE_TRY(build_support(h, R, b, (flags & 1) ? x : nullptr, &sp, st));
-    const long long nfull = (long long)h->nc * (long long)h->nv;
+    VIE_TRY(build_support(h, R, b, (flags & 1) ? x : nullptr, &sp, st, jm ? h->jmsup64 : h->chi64, ncs));
+    const long long nfull = (long long)ncs * (long long)h->nv;
     if (sp.ns == 0) {  // chi = 0 everywhere and b = 0: x = 0
         VIE_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)(R * nfull), st));
         VIE_CUDA(cudaStreamSynchronize(st));
         for (int r = 0; info && r < R; ++r) info[r] = vie_solve_info{1, 0, 0, 0, 0, 0.0, (flags & 2) ? 0.0 : -1.0, 0.0};
         return VIE_OK;
     }
-    const long long n = (long long)h->nc * sp.ns;
+    const long long n = (long long)ncs * sp.ns;
     const bool mixed = mode == VIE_SOLVE_FP32_REFINE || mode == VIE_SOLVE_BF16X3_REFINE;
     const int inner = mode == VIE_SOLVE_BF16X3_REFINE ? VIE_BF16X3 : VIE_FP32;  // matvec of the inner GMRES
     const size_t vc = mixed ? sizeof(float2) : sizeof(double2);
@@ -948,7 +969,8 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     S.st = st;
     // CUDA graphs for the cycles unless flags bit 3 asks for direct launches; the legacy and
     // per-thread default streams cannot be captured
-    S.use_graph = !(flags & 8) && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    S.use_graph = !(flags & 8) && !jm && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    S.jm = jm;
     // the largest spectrum scratch any matvec of this solve takes (FP64), reserved before the
     // first cycle is captured so that no later reservation moves the buffer under the graph
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, VIE_FP64)));
@@ -1011,12 +1033,13 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     const unsigned gr = (unsigned)((R + 127) / 128);
     const double dV = h->dx * h->dy * h->dz;
     VIE_KLAUNCH("precond_rhs", st,
-                precond_rhs_kernel<<<gtf, 256, 0, st>>>(b, h->ieps64, full0, (long long)h->nv, R, h->nc, dV, dV / 12.0));
+                precond_rhs_kernel<<<gtf, 256, 0, st>>>(b, h->ieps64, jm ? h->imu64 : nullptr, full0,
+                                                        (long long)h->nv, R, ncs, dV, dV / 12.0));
     VIE_CHECK_LAUNCH();
-    VIE_TRY(support_gather(h, R, full0, bt, VIE_FP64, sp, st));
+    VIE_TRY(support_gather(h, Rv, full0, bt, VIE_FP64, sp, st));
     VIE_TRY(S.norm2_64(bt, bn2));
     if (flags & 1)
-        VIE_TRY(support_gather(h, R, x, xs, VIE_FP64, sp, st));
+        VIE_TRY(support_gather(h, Rv, x, xs, VIE_FP64, sp, st));
     else
         VIE_CUDA(cudaMemsetAsync(xs, 0, sizeof(double2) * total, st));
     {
@@ -1112,8 +1135,11 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         if (!done_update) {
             // the matvec also leaves (N - G) x on the full grid, kept with x for vie_fields
             double2* cx = keep ? static_cast<double2*>(h->fcache_ws.ptr) : nullptr;
-            VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr,
-                                   keep ? cx + (size_t)R * nfull : nullptr));
+            if (jm)
+                VIE_TRY(jm_matvec_support(h, R, xs, t64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr));
+            else
+                VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr,
+                                       keep ? cx + (size_t)R * nfull : nullptr));
             ++mv64;
             VIE_KLAUNCH("residual_sub", st, sub_kernel<<<gt, 256, 0, st>>>(bt, t64, r64, total));
             if (keep) {
@@ -1169,13 +1195,16 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     std::vector<double> herr(R, 0.0);
     VIE_CUDA(cudaMemcpyAsync(herr.data(), err, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     VIE_CUDA(cudaStreamSynchronize(st));
-    VIE_TRY(support_scatter(h, R, xs, x, VIE_FP64, sp, st));
+    VIE_TRY(support_scatter(h, Rv, xs, x, VIE_FP64, sp, st));
     if (flags & 2) {
         // unpreconditioned residual ||b - A x|| / ||b|| on the full grid; its convolution at
         // the final x replaces the cached one for vie_fields
         double2* cx = keep ? static_cast<double2*>(h->fcache_ws.ptr) : nullptr;
-        VIE_TRY(matvec_support(h, R, x, full0, VIE_FP64, VIE_OP_A, Support{}, S.mv_tmp, st, nullptr,
-                               keep ? cx + (size_t)R * nfull : nullptr));
+        if (jm)
+            VIE_TRY(jm_matvec_full(h, R, x, full0, VIE_OP_A, st));
+        else
+            VIE_TRY(matvec_support(h, R, x, full0, VIE_FP64, VIE_OP_A, Support{}, S.mv_tmp, st, nullptr,
+                                   keep ? cx + (size_t)R * nfull : nullptr));
         ++mv64;
         if (keep) {
             VIE_CUDA(cudaMemcpyAsync(cx, x, sizeof(double2) * (size_t)R * nfull, cudaMemcpyDeviceToDevice, st));
