@@ -841,7 +841,6 @@ def run_tucker(args, local):
         t0 = time.perf_counter()
         h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), w["freq"], w["eps_real"], w["sigma"])
         setup_s = time.perf_counter() - t0
-        _, bytes0 = vie.vie_info(h)
         y0 = torch.empty_like(v)
         vie.vie_matvec(h, v, y0, vie.VIE_FP64, vie.VIE_OP_NSCAT)
         shape = (R, 12) + g.shape
@@ -852,6 +851,7 @@ def run_tucker(args, local):
         torch.cuda.synchronize()
         vie.vie_solve(h, b, x0, tol=TOL, restart=RESTART, maxit=400)
         torch.cuda.synchronize()
+        _, bytes0 = vie.vie_info(h)  # (after the solve's workspaces)
         t0 = time.perf_counter()
         ranks, err, nbytes = vie.vie_green_tucker(h, tol, apply=True)
         tucker_s = time.perf_counter() - t0

@@ -96,13 +96,13 @@ struct Stager {
 void release(vie_handle* h) {
     if (!h) return;
     kmatvec_release(h);
-    cudaFree(h->eps64);
-    cudaFree(h->chi64);
-    cudaFree(h->tau64);
-    cudaFree(h->ieps64);
-    cudaFree(h->chi32);
-    cudaFree(h->tau32);
-    cudaFree(h->ieps32);
+    dev_free(h, h->eps64);
+    dev_free(h, h->chi64);
+    dev_free(h, h->tau64);
+    dev_free(h, h->ieps64);
+    dev_free(h, h->chi32);
+    dev_free(h, h->tau32);
+    dev_free(h, h->ieps32);
     if (!h->shared_green) {
         cudaFree(h->green64);
         cudaFree(h->green32);
@@ -116,14 +116,14 @@ void release(vie_handle* h) {
         cudaFree(h->toeplitz);
     }
     cudaFree(h->tucker);
-    cudaFree(h->fft_ws.ptr);
-    cudaFree(h->stage_ws.ptr);
-    cudaFree(h->solve_ws.ptr);
-    cudaFree(h->support_ws.ptr);
-    cudaFree(h->post_ws.ptr);
-    cudaFree(h->fcache_ws.ptr);
+    dev_free(h, h->fft_ws.ptr);
+    dev_free(h, h->stage_ws.ptr);
+    dev_free(h, h->solve_ws.ptr);
+    dev_free(h, h->support_ws.ptr);
+    dev_free(h, h->post_ws.ptr);
+    dev_free(h, h->fcache_ws.ptr);
     cudaFree(h->mu64);  // one allocation holds mu64, chim64, imu64 and jmsup64
-    cudaFree(h->jm_ws.ptr);
+    dev_free(h, h->jm_ws.ptr);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -140,6 +140,18 @@ void release(vie_handle* h) {
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+cudaError_t dev_malloc(const vie_handle* h, void** p, size_t bytes) {
+    return h->async_alloc ? cudaMallocAsync(p, bytes, h->stream) : cudaMalloc(p, bytes);
+}
+
+void dev_free(const vie_handle* h, void* p) {
+    if (!p) return;
+    if (h->async_alloc)
+        cudaFreeAsync(p, h->stream);
+    else
+        cudaFree(p);
+}
+
 namespace {
 std::atomic<int> g_inject_oom{0};  // workspace allocations still to fail (vie_fault_inject)
 }
@@ -152,12 +164,12 @@ int ws_reserve(vie_handle* h, Workspace& w, size_t bytes) {
             return VIE_ENOMEM;
         }
     if (w.ptr) {
-        VIE_CUDA(cudaFree(w.ptr));
+        dev_free(h, w.ptr);
         h->bytes_held -= w.bytes;
         w.ptr = nullptr;
         w.bytes = 0;
     }
-    if (cudaMalloc(&w.ptr, bytes) != cudaSuccess) {
+    if (dev_malloc(h, &w.ptr, bytes) != cudaSuccess) {
         cudaGetLastError();
         w.ptr = nullptr;
         set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
@@ -257,6 +269,7 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
         release(h);
         return code;
     };
+    h->async_alloc = share != nullptr;  // a server request's handle
     if (cudaGetDevice(&h->device) != cudaSuccess || cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         set_error("no usable CUDA device");
@@ -281,28 +294,29 @@ int handle_create(const vie_grid* grid, double freq_hz, const double* eps_real, 
             return fail(VIE_EINVAL);
         }
     const size_t nv = h->nv;
-    if (cudaMalloc(&h->eps64, sizeof(double2) * nv) != cudaSuccess ||
-        cudaMalloc(&h->chi64, sizeof(double2) * nv) != cudaSuccess ||
-        cudaMalloc(&h->tau64, sizeof(double2) * nv) != cudaSuccess ||
-        cudaMalloc(&h->ieps64, sizeof(double2) * nv) != cudaSuccess ||
-        cudaMalloc(&h->chi32, sizeof(float2) * nv) != cudaSuccess ||
-        cudaMalloc(&h->tau32, sizeof(float2) * nv) != cudaSuccess ||
-        cudaMalloc(&h->ieps32, sizeof(float2) * nv) != cudaSuccess) {
+    if (dev_malloc(h, (void**)&h->eps64, sizeof(double2) * nv) != cudaSuccess ||
+        dev_malloc(h, (void**)&h->chi64, sizeof(double2) * nv) != cudaSuccess ||
+        dev_malloc(h, (void**)&h->tau64, sizeof(double2) * nv) != cudaSuccess ||
+        dev_malloc(h, (void**)&h->ieps64, sizeof(double2) * nv) != cudaSuccess ||
+        dev_malloc(h, (void**)&h->chi32, sizeof(float2) * nv) != cudaSuccess ||
+        dev_malloc(h, (void**)&h->tau32, sizeof(float2) * nv) != cudaSuccess ||
+        dev_malloc(h, (void**)&h->ieps32, sizeof(float2) * nv) != cudaSuccess) {
         cudaGetLastError();
         set_error("material allocation failed");
         return fail(VIE_ENOMEM);
     }
     h->bytes_held += nv * (4 * sizeof(double2) + 3 * sizeof(float2));
     double* dmat = nullptr;
-    if (cudaMalloc(&dmat, sizeof(double) * 2 * nv) != cudaSuccess) {
+    if (dev_malloc(h, (void**)&dmat, sizeof(double) * 2 * nv) != cudaSuccess) {
+        cudaGetLastError();
         set_error("material staging failed");
         return fail(VIE_ENOMEM);
     }
-    cudaMemcpy(dmat, er.data(), sizeof(double) * nv, cudaMemcpyHostToDevice);
-    cudaMemcpy(dmat + nv, sg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(dmat, er.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dmat + nv, sg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, h->stream);
     rc = materials_device(h, dmat, dmat + nv, h->stream);
-    cudaStreamSynchronize(h->stream);
-    cudaFree(dmat);
+    dev_free(h, dmat);
+    cudaStreamSynchronize(h->stream);  // er and sg are read by the copies above
     if (rc < 0) return fail(rc);
     if (share) {
         h->shared_green = 1;

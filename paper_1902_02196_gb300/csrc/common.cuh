@@ -161,6 +161,11 @@ struct vie_handle {
     // set when green64/32/32t, toeplitz, the twiddle tables and colmap belong to another
     // handle (a template kept in a server's Green cache) and must not be freed with this one
     int shared_green;
+    // set for a server request's handle: its own memory (material maps, workspaces) is
+    // allocated and freed in stream order on its stream (cudaMallocAsync / cudaFreeAsync from the
+    // device's memory pool), so that a request's allocations and frees do not synchronise the
+    // device under the other requests' work
+    int async_alloc;
 };
 
 // vie_setup with an optional template: when share != NULL the new handle takes the
@@ -196,6 +201,9 @@ void set_error(const std::string& msg);
     } while (0)
 
 int ws_reserve(vie_handle* h, Workspace& w, size_t bytes);
+// device memory owned by handle h: stream-ordered on h's stream when h->async_alloc, else plain
+cudaError_t dev_malloc(const vie_handle* h, void** p, size_t bytes);
+void dev_free(const vie_handle* h, void* p);
 
 // ---------------------------------------------------------------------------
 // Launch accounting (stats.cu): every kernel launch of the library is counted per

@@ -391,7 +391,7 @@ int rhs_dipoles_device(vie_handle* h, int R, const double* pos, const double* mo
     VIE_TRY(ensure_rule6());
     const long long nv = (long long)h->nv;
     double* dbuf = nullptr;
-    VIE_CUDA(cudaMalloc(&dbuf, sizeof(double) * 6 * R));
+    VIE_CUDA(dev_malloc(h, (void**)&dbuf, sizeof(double) * 6 * R));
     cudaMemcpyAsync(dbuf, pos, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dbuf + 3 * R, mom, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s);
     const double2 ce = make_double2(0.0, h->omega * VIE_EPS0);
@@ -401,7 +401,7 @@ int rhs_dipoles_device(vie_handle* h, int R, const double* pos, const double* mo
                                                                h->chi64, h->nc, e, b));
     cudaError_t err = cudaGetLastError();
     cudaStreamSynchronize(s);
-    cudaFree(dbuf);
+    dev_free(h, dbuf);
     if (err != cudaSuccess) {
         set_error(std::string("dipole kernel: ") + cudaGetErrorString(err));
         return VIE_EDEVICE;

@@ -115,6 +115,8 @@ struct vie_server {
     std::vector<std::thread> workers;
     Clock::time_point t0;          // creation: origin of the host spans
     cudaEvent_t ref = nullptr;     // recorded at creation: origin of the device spans
+    cudaMemPool_t pool = nullptr;  // the device's default memory pool, which requests allocate from
+    uint64_t pool_keep0 = 0;       // its release threshold before this server set it
 };
 
 namespace {
@@ -202,20 +204,23 @@ int run_request(vie_server* s, Req& r, bool builder, vie_solve_info* info) {
     }
     vie_handle* h = nullptr;
     SRV_TRY(handle_create(&r.grid, r.freq, r.eps.data(), r.sig.data(), tmpl, &h));
+    // the request's buffers come from the device's memory pool in the order of its stream (the
+    // handle allocates with cudaMallocAsync), so neither they nor the handle's workspaces
+    // synchronise the device when they are allocated or freed
     struct Guard {
         vie_handle* h;
         std::vector<void*> bufs;
         ~Guard() {
             if (h) cudaStreamSynchronize(h->stream);
-            for (void* p : bufs) cudaFree(p);
+            for (void* p : bufs) dev_free(h, p);
             vie_destroy(h);
         }
     } g{h, {}};
     const size_t n = (size_t)r.nrhs * 12 * h->nv;
     void *b = nullptr, *e = nullptr, *x = nullptr, *pa = nullptr;
-    if (cudaMalloc(&b, 16 * n) != cudaSuccess || (g.bufs.push_back(b), cudaMalloc(&e, 16 * n)) != cudaSuccess ||
-        (g.bufs.push_back(e), cudaMalloc(&x, 16 * n)) != cudaSuccess ||
-        (g.bufs.push_back(x), cudaMalloc(&pa, 8 * (size_t)r.nrhs * h->nv)) != cudaSuccess) {
+    if (dev_malloc(h, &b, 16 * n) != cudaSuccess || (g.bufs.push_back(b), dev_malloc(h, &e, 16 * n)) != cudaSuccess ||
+        (g.bufs.push_back(e), dev_malloc(h, &x, 16 * n)) != cudaSuccess ||
+        (g.bufs.push_back(x), dev_malloc(h, &pa, 8 * (size_t)r.nrhs * h->nv)) != cudaSuccess) {
         cudaGetLastError();
         set_error("request buffers: device allocation failed");
         return VIE_ENOMEM;
@@ -328,6 +333,19 @@ int vie_server_create(size_t hbm_budget_bytes, int max_concurrent, vie_server** 
     }
     s->device = dev;
     s->budget = hbm_budget_bytes;
+    // requests allocate from the device's default memory pool in stream order; keep up to the
+    // budget in the pool between requests instead of returning it at every synchronisation
+    // (a setting of this process's pool, not of the device; vie_server_destroy restores it and
+    // returns what the pool holds)
+    {
+        uint64_t keep = hbm_budget_bytes;
+        if (cudaDeviceGetDefaultMemPool(&s->pool, dev) != cudaSuccess ||
+            cudaMemPoolGetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &s->pool_keep0) != cudaSuccess ||
+            cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            s->pool = nullptr;
+        }
+    }
     s->slots = max_concurrent;
     s->t0 = Clock::now();
     // the origin of the device spans: an event that has completed before any request starts
@@ -354,6 +372,11 @@ void vie_server_destroy(vie_server* s) {
     for (auto& kv : s->cache)
         if (kv.second.tmpl) vie_destroy(kv.second.tmpl);
     if (s->ref) cudaEventDestroy(s->ref);
+    if (s->pool) {  // every request's frees have completed (their handles synchronised their streams)
+        if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &s->pool_keep0) != cudaSuccess ||
+            cudaMemPoolTrimTo(s->pool, 0) != cudaSuccess)
+            cudaGetLastError();
+    }
     delete s;
 }
 

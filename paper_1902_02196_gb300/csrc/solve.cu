@@ -1016,15 +1016,22 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     int* done = reinterpret_cast<int*>(base + oDone);
     double* rel = reinterpret_cast<double*>(base + oRel);
     int* k1 = reinterpret_cast<int*>(base + oK1);
-    VIE_CUDA(cudaMallocHost(&S.pinned, sizeof(int) * kMaxChunks));
-    struct PinGuard {
-        int* p;
-        cudaStream_t s;
-        ~PinGuard() {  // after the copies into it have finished
-            cudaStreamSynchronize(s);
-            cudaFreeHost(p);
+    // pinned host words for the chunk counts: one buffer per host thread, kept for the thread's
+    // lifetime (a solve is synchronous on its thread), so that solves do not allocate and free
+    // pinned memory, which would synchronise the device under other streams' work
+    struct PinnedCounts {
+        int* p = nullptr;
+        ~PinnedCounts() {
+            if (p) cudaFreeHost(p);
         }
-    } guard{S.pinned, st};
+    };
+    thread_local PinnedCounts pinned;
+    if (!pinned.p) VIE_CUDA(cudaMallocHost(&pinned.p, sizeof(int) * kMaxChunks));
+    S.pinned = pinned.p;
+    struct SyncGuard {  // the copies into the pinned words have finished when the solve returns
+        cudaStream_t s;
+        ~SyncGuard() { cudaStreamSynchronize(s); }
+    } guard{st};
     for (auto& e : S.chunk_ev) VIE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
     const long long total = (long long)R * n, total_full = (long long)R * nfull;

@@ -154,3 +154,18 @@ def test_poll_timeout_and_retired_ticket(vie):
         s.submit(grid_tuple(g), 128e6, eps, sig, pos, mom, restart=0)
     assert e.value.code == vie.VIE_EINVAL
     s.close()
+
+
+def test_closed_server_returns_its_pool_memory(vie):
+    """Requests allocate in stream order from the device's memory pool, which keeps freed memory
+    while the loop runs; closing the loop hands it back, so a later loop (or any other allocation)
+    sees the device memory it had before."""
+    reqs = requests()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    s = vie.Server(max_concurrent=4)
+    res, _ = run(s, reqs)
+    s.close()
+    assert all(r["status"] == vie.VIE_OK for r in res)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20), (free0, free1)
