@@ -353,66 +353,43 @@ __global__ void __launch_bounds__(kXYThreads, XYCfg<L, C>::MINB)
         }
         cp_async_commit();
     }
-    // The per-voxel coefficients (c2, and c1 for op PA) of this thread's voxels are loaded D
-    // voxels ahead of their use, the first D before the x transform, so that their L2 latency
-    // overlaps the transform and the previous voxels' arithmetic.
-    const int nvox = ny * nx;
-    const long long zoff = (p % nz) * (long long)nvox;
-    const C* c1 = reinterpret_cast<const C*>(epi.c1);
-    const C* c2 = reinterpret_cast<const C*>(epi.c2);
-    const bool need2 = epi.op == VIE_OP_A || epi.op == VIE_OP_PA, need1 = epi.op == VIE_OP_PA;
-    constexpr int D = 4;
-    C pc1[D], pc2[D];
-    auto fetch = [&](int j, int slot) {  // the j-th voxel of this thread into ring slot `slot`
-        const int idx = tid + j * NT;
-        if (idx < nvox) {
-            if (need2) pc2[slot] = c2[zoff + idx];
-            if (need1) pc1[slot] = c1[zoff + idx];
-        }
-    };
-#pragma unroll
-    for (int u = 0; u < D; ++u) fetch(u, u);
     fft2::inverse<L, NT>(xr, ny, [](int n) { return n * RS; }, 1, tw, nx);
     if (pre) {
         cp_async_wait<0>();
         __syncthreads();
     }
     const int alpha = (int)((p / nz) % nc);
+    const long long zoff = (p % nz) * (long long)ny * nx;
     const R gl = (R)(comp_is_constant(alpha, nc) ? epi.g1 : epi.g234);
     const R ig = (R)1 / gl;
+    const C* c1 = reinterpret_cast<const C*>(epi.c1);
+    const C* c2 = reinterpret_cast<const C*>(epi.c2);
     C sh = mk((R)0, (R)0);  // shift of op PA for this plane's right-hand side
     if (epi.shift) {
         const double2 d = epi.shift[po / rplanes];
         sh = mk((R)d.x, (R)d.y);
     }
     C* conv = CONV ? reinterpret_cast<C*>(epi.conv) : nullptr;
-#pragma unroll 1
-    for (int j0 = 0; tid + j0 * NT < nvox; j0 += D) {
-#pragma unroll
-        for (int u = 0; u < D; ++u) {
-            const int idx = tid + (j0 + u) * NT;
-            const C k1 = pc1[u], k2 = pc2[u];
-            fetch(j0 + u + D, u);  // the slot's next voxel
-            if (idx >= nvox) continue;
-            const int yy = idx / nx, xx = idx % nx;
-            long long o = base + idx;
-            C v = xr[yy * RS + xx];
-            if (CONV) conv[base + idx] = v;  // every voxel of the plane, full-grid layout
-            if (epi.rows) {
-                const int4 q = rw[yy];
-                if (xx < q.x || xx >= q.y) continue;
-                o = cbase + q.z + (xx - q.x);
-            }
-            if (epi.op == VIE_OP_A) {
-                const C xv = pre ? ck[idx] : xin[o];
-                v = csub(mk(gl * xv.x, gl * xv.y), cmul(k2, v));
-            } else if (epi.op == VIE_OP_PA) {
-                const C xv = pre ? ck[idx] : xin[o];
-                const C t = cmul(k2, v);
-                v = csub(cmul(csub(k1, sh), xv), mk(ig * t.x, ig * t.y));
-            }
-            y[o] = v;
+#pragma unroll 4
+    for (int idx = tid; idx < ny * nx; idx += NT) {
+        const int yy = idx / nx, xx = idx % nx;
+        long long o = base + idx;
+        C v = xr[yy * RS + xx];
+        if (CONV) conv[base + idx] = v;  // every voxel of the plane, full-grid layout
+        if (epi.rows) {
+            const int4 q = rw[yy];
+            if (xx < q.x || xx >= q.y) continue;
+            o = cbase + q.z + (xx - q.x);
         }
+        if (epi.op == VIE_OP_A) {
+            const C xv = pre ? ck[idx] : xin[o];
+            v = csub(mk(gl * xv.x, gl * xv.y), cmul(c2[zoff + idx], v));
+        } else if (epi.op == VIE_OP_PA) {
+            const C xv = pre ? ck[idx] : xin[o];
+            const C t = cmul(c2[zoff + idx], v);
+            v = csub(cmul(csub(c1[zoff + idx], sh), xv), mk(ig * t.x, ig * t.y));
+        }
+        y[o] = v;
     }
 }
 
