@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--fp64-reps", type=int, default=3, help="plain FP64 solves timed (the median is reported)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the incl64 three-arm precision comparison attached to the default line")
     ap.add_argument("--serving", type=int, default=0, metavar="N",
                     help="serving stream: N requests (grids from --serving-sizes, 1-32 dipoles, 64/128/298 MHz), "
                          "first all at once (capacity), then as Poisson arrivals at 0.8x that capacity "
@@ -389,21 +391,25 @@ def run_ours(args, ws, rank, local):
         return rc, info, P
 
     def run_e2e():
-        """The same step through the C ABI with pinned host buffers, copies inside the timed region."""
+        """The same step through the C ABI with the inputs (b, e_inc) in pinned host memory and the
+        results (field map, SAR map, P_abs) read back into pinned host memory, copies inside the
+        timed region; the current coefficients x stay on the device between the two calls, as the
+        intermediate they are."""
         bh = b.cpu().pin_memory()
         eh = e_inc.cpu().pin_memory()
-        xh = torch.empty(shape, dtype=torch.complex128).pin_memory()
+        xd = torch.empty_like(b)
         ph = torch.empty((NRHS,) + g.shape, dtype=torch.float64).pin_memory()
         ech = torch.empty(shape, dtype=torch.complex128).pin_memory()
         split = [0.0, 0.0]
 
         def step_host():
-            # both calls return after their device-to-host copies (host buffers synchronize the stream)
+            # vie_solve returns with x on the device; vie_fields returns after its device-to-host
+            # copies (host buffers synchronize the stream)
             t0 = time.perf_counter()
-            vie.vie_solve(h, bh, xh, tol=TOL, restart=RESTART, maxit=MAXIT, mode=vie.VIE_SOLVE_FP32_REFINE,
+            vie.vie_solve(h, bh, xd, tol=TOL, restart=RESTART, maxit=MAXIT, mode=vie.VIE_SOLVE_FP32_REFINE,
                           stream=stream)
             t1 = time.perf_counter()
-            P = vie.vie_fields(h, xh, eh, ech, ph, stream=stream)
+            P = vie.vie_fields(h, xd, eh, ech, ph, stream=stream)
             split[0] += t1 - t0
             split[1] += time.perf_counter() - t1
             return P
@@ -419,11 +425,11 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         te = max_over_ranks((time.perf_counter() - t0) / ke, dev)
         vb = NRHS * 12 * g.nv * 16
-        return dict(value=job_throughput(NRHS, ws, te), unit="solves/s", h2d_bytes_per_step=3 * vb,
-                    d2h_bytes_per_step=2 * vb + NRHS * g.nv * 8 + NRHS * 8,
+        return dict(value=job_throughput(NRHS, ws, te), unit="solves/s", h2d_bytes_per_step=2 * vb,
+                    d2h_bytes_per_step=vb + NRHS * g.nv * 8 + NRHS * 8,
                     solve_ms=1e3 * split[0] / ke, fields_ms=1e3 * split[1] / ke,
-                    note="C ABI with pinned host buffers: b in, x out; x and e_inc in, field map, p_abs and "
-                         "P_abs out; slowest rank")
+                    note="C ABI with pinned host buffers: b and e_inc in, field map, p_abs and P_abs out "
+                         "(x stays on the device between vie_solve and vie_fields); slowest rank")
 
     for _ in range(max(3, args.warmup)):
         rc, info, P = step()
@@ -575,6 +581,13 @@ def run_ours(args, ws, rank, local):
 
     if e2e is not None:
         out["e2e"] = e2e
+    if not args.no_configs and ws == 1:
+        # the high-contrast precision stress (64^3 inclusions, 32 RHS, 447 MHz): BF16x3 vs FP32 vs
+        # FP64 arms, iterations and the solvers' forward-error estimates (errors against an FP64
+        # solve to 1e-10: --config-run incl64)
+        torch.cuda.synchronize()
+        out["configs"] = {"incl64": config_measure("incl64", local, no_fp64=args.no_fp64, no_ref=True)}
+        torch.cuda.set_stream(stream)
     if not args.no_cpu and ws == 1:
         try:
             out["cpu_baseline"] = cpu_baseline_block()
@@ -733,16 +746,25 @@ def run_serving(args, local):
 
 def run_config(args, local):
     """Mixed vs plain FP64 on one named workload (precision stress / body scale)."""
+    import torch
+
+    torch.cuda.set_device(local)
+    print(json.dumps(config_measure(args.config_run, local, args.no_fp64, args.no_ref)), flush=True)
+
+
+def config_measure(name, local, no_fp64=False, no_ref=False):
+    """The arms BF16x3, FP32 (+ FP64 refinement) and plain FP64 on one named workload, with
+    iterations, times, the solvers' error estimates and, unless no_ref, the error against an FP64
+    solve to 1e-10; returns the result as a dict."""
     import numpy as np
     import torch
 
     import paper_1902_02196_gb300 as vie
     from synth import workload
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     vie.build()
-    w = workload(args.config_run)
+    w = workload(name)
     g = w["grid"]
     R = int(w["dip_pos"].shape[0])
     t0 = time.perf_counter()
@@ -755,15 +777,15 @@ def run_config(args, local):
     e_inc = torch.empty(shape, dtype=torch.complex128, device=dev)
     b = torch.empty_like(e_inc)
     vie.vie_rhs_dipoles(h, w["dip_pos"], w["dip_mom"], e_inc, b, stream=stream)
-    out = dict(mode="config-run", workload=args.config_run, grid=[g.nx, g.ny, g.nz], fft=list(L), nrhs=R,
+    out = dict(mode="config-run", workload=name, grid=[g.nx, g.ny, g.nz], fft=list(L), nrhs=R,
                freq_mhz=w["freq"] / 1e6, tol=TOL, restart=RESTART, setup_s=setup_s, data="synthetic")
     sol = {}
     arms = [("bf16x3", vie.VIE_SOLVE_BF16X3_REFINE, TOL), ("mixed", vie.VIE_SOLVE_FP32_REFINE, TOL)]
-    if not args.no_fp64:
+    if not no_fp64:
         # the plain FP64 arm, and the same method to 1e-10 as the reference the arms' errors are taken
         # against (the FP64 path is parity-pinned to the oracle; the oracle itself cannot solve this size)
         arms += [("fp64", vie.VIE_SOLVE_FP64, TOL)]
-        if not args.no_ref:
+        if not no_ref:
             arms += [("fp64_ref", vie.VIE_SOLVE_FP64, 1e-10)]
     for name, mode, tol in arms:
         x = torch.empty_like(b)
@@ -814,7 +836,7 @@ def run_config(args, local):
         mvb16 = a0.elapsed_time(a1) / 5
         out["matvec_bf16x3"] = dict(ms=mvb16, alg_gbs=mvb / (mvb16 / 1000) / 1e9)
     h.close()
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_tucker(args, local):
