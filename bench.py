@@ -938,7 +938,41 @@ def run_jm(args, local):
         P = vie.vie_jm_fields(h, x, e_t, h_t)[0]
         h.close()
         rows.append(dict(n=n, rc=rc, seconds=sec, iterations=info[0]["iterations"], P_abs=P))
-    print(json.dumps(dict(mode="jm", workload="magnetodielectric sphere, plane wave", runs=rows,
+    # the K operator (row f1) on the head64 batch: FP64 K matvec of 16 right-hand sides (the K
+    # spectrum built on first use, timed apart) and the magnetic post-processing (h, b1+, W_m)
+    from synth import workload
+
+    wl = workload("head64")
+    g = wl["grid"]
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), wl["freq"], wl["eps_real"], wl["sigma"])
+    dev = torch.device("cuda", local)
+    shape = (NRHS, 12) + g.shape
+    x = torch.randn(shape, dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vie.vie_matvec(h, x[:1], y[:1], vie.VIE_FP64, vie.VIE_OP_K)
+    torch.cuda.synchronize()
+    kspec_s = time.perf_counter() - t0
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        vie.vie_matvec(h, x, y, vie.VIE_FP64, vie.VIE_OP_K)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    hinc = torch.empty_like(x)
+    vie.vie_rhs_dipoles_h(h, wl["dip_pos"], wl["dip_mom"], hinc)
+    b1 = torch.empty((NRHS,) + g.shape, dtype=torch.complex128, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vie.vie_hfields(h, x, hinc, None, b1)
+    torch.cuda.synchronize()
+    hf_s = time.perf_counter() - t0
+    h.close()
+    kmv = dict(workload="head64, 16 RHS, FP64", k_spectrum_setup_s=kspec_s, k_matvec_ms=1e3 * min(times),
+               hfields_ms=1e3 * hf_s,
+               note="full-circulant FP64 correctness path: 12 R padded volumes transformed forward and back")
+    print(json.dumps(dict(mode="jm", workload="magnetodielectric sphere, plane wave", runs=rows, k_operator=kmv,
                           data="synthetic")), flush=True)
 
 

@@ -97,3 +97,39 @@ def test_tucker_matvec_and_solve(vie):
     assert rel(y, ref) <= 10 * tol
     assert rel(x1, x0) <= 100 * tol
     assert nbytes < 0.5 * 60 * g.nv * 16  # at 16^3 the form is already smaller than the table
+
+
+def test_tucker_recompress_pwc_and_arguments(vie):
+    """A second compression starts from the first one's reconstruction (the table is gone after
+    VIE_TUCKER_APPLY) and keeps the bound against the original within the sum of the tolerances; a
+    PWC handle's matvec runs on the compressed tensors; out-of-range tolerances are refused."""
+    g = Grid(10, 9, 11, 0.005, 0.005, 0.005)
+    eps, sig = random_tissue(g, 8)
+    h = handle(vie, g, eps, sig)
+    T = np.empty((60,) + g.shape, dtype=np.complex128)
+    vie.vie_green_toeplitz(h, T)
+    vie.vie_green_tucker(h, 1e-6, apply=True)
+    ranks2, err2, _ = vie.vie_green_tucker(h, 1e-4, apply=True)
+    R = np.empty_like(T)
+    vie.vie_green_toeplitz(h, R)
+    for t in range(60):
+        assert np.linalg.norm(R[t] - T[t]) <= (1e-4 + 1e-6) * np.linalg.norm(T[t])
+    for bad in (0.0, 1e-8, 1.0, float("nan")):
+        with pytest.raises(vie.VieError) as e:
+            vie.vie_green_tucker(h, bad)
+        assert e.value.code == vie.VIE_EINVAL
+    h.close()
+    # PWC: the l = 1 sub-block of the compressed Green function against the oracle's exact operator
+    tol = 1e-6
+    hp = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), F, eps, sig, vie.VIE_SETUP_PWC)
+    vie.vie_green_tucker(hp, tol, apply=True)
+    x = random_coefficients(g, 2, seed=9, ncomp=3)
+    y = np.empty_like(x)
+    vie.vie_matvec(hp, x, y, vie.VIE_FP64, vie.VIE_OP_PA)
+    hp.close()
+    prob = O.Problem(g, F, eps, sig)
+    Nop = O.NOperator(g, prob.k0)
+    xf = np.zeros((2, 12) + g.shape, dtype=complex)
+    xf[:, 0::4] = x
+    ref = O.apply_PA_pwc(prob, Nop, xf)[:, 0::4]
+    assert rel(y, ref) <= 10 * tol
