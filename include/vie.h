@@ -58,7 +58,7 @@ extern "C" {
 #define VIE_OP_A 0      /* y = A x = M_eps G x - M_chi N x                     (Eq. 24) */
 #define VIE_OP_PA 1     /* y = P^-1 A x, P = M_eps G: x/eps - tau G^-1 (N - G) x (Section IV-B, Eq. 17) */
 #define VIE_OP_NSCAT 2  /* y = (N - G) x, the Galerkin "N - I" operator (tested scattered field * c_e) */
-#define VIE_OP_K 3      /* y = K x, K u = curl S u (Eq. 8): the tested scattered magnetic field (Eq. 13); FP64 only */
+#define VIE_OP_K 3      /* y = K x, K u = curl S u (Eq. 8): the tested scattered magnetic field (Eq. 13); FP64 or FP32 */
 
 /* Solver modes of vie_solve. */
 #define VIE_SOLVE_FP64 0         /* plain FP64 GMRES */
@@ -143,10 +143,12 @@ void vie_destroy(vie_handle* h);
  *   nrhs      : number of vectors >= 1
  *   x, y      : [nrhs][12][nz][ny][nx] complex, element type by `precision`
  *               (VIE_FP64: double pairs, VIE_FP32 and VIE_BF16X3: float pairs); x and y must not overlap
- *   precision : VIE_FP64, VIE_FP32 or VIE_BF16X3 (VIE_OP_K: VIE_FP64 only)
+ *   precision : VIE_FP64, VIE_FP32 or VIE_BF16X3 (VIE_OP_K: VIE_FP64 or VIE_FP32)
  *   op        : VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT or VIE_OP_K.  VIE_OP_K transforms the 30
- *               tensors of vie_green_toeplitz_k once per handle (kept until vie_destroy) and
- *               applies the K block (96 signed entries) on full circulant spectra, in FP64.
+ *               tensors of vie_green_toeplitz_k once per handle into octant spectra (30 Ox Oy Oz
+ *               values in FP64 and FP32, kept until vie_destroy and counted by vie_info) and runs
+ *               the same transforms as the N operator with the K block (96 signed entries) at
+ *               every frequency point, the other octants from the K parities.
  */
 int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream);
 

@@ -385,7 +385,7 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
     REQUIRE(precision == VIE_FP64 || precision == VIE_FP32 || precision == VIE_BF16X3, "unknown precision");
     REQUIRE(op == VIE_OP_A || op == VIE_OP_PA || op == VIE_OP_NSCAT || op == VIE_OP_K, "unknown operator");
-    REQUIRE(op != VIE_OP_K || precision == VIE_FP64, "the K operator is FP64 only");
+    REQUIRE(op != VIE_OP_K || precision != VIE_BF16X3, "the K operator runs in FP64 or FP32");
     REQUIRE(op != VIE_OP_K || h->nc == 12, "the K operator is built for the PWL system only");
     REQUIRE(x != y, "x and y must not overlap");
     const size_t bytes = (size_t)nrhs * h->nc * h->nv * (precision == VIE_FP64 ? sizeof(double2) : sizeof(float2));
@@ -395,10 +395,7 @@ int vie_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, i
     sg.add(y, bytes, true);
     std::vector<void*> d;
     VIE_TRY(sg.bind(d));
-    if (op == VIE_OP_K)
-        VIE_TRY(kmatvec_device(h, nrhs, static_cast<const double2*>(d[0]), static_cast<double2*>(d[1]), st));
-    else
-        VIE_TRY(matvec_device(h, nrhs, d[0], d[1], precision, op, st));
+    VIE_TRY(matvec_device(h, nrhs, d[0], d[1], precision, op, st));
     return sg.finish(d);
 }
 

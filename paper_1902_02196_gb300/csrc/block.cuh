@@ -57,6 +57,32 @@ constexpr BlockTableB make_block_table_b() {
 }
 __device__ constexpr BlockTableB kBlockB = make_block_table_b();
 
+// The 96 non-zero entries of the K block (kblock.h) grouped by the 30 stored tensors
+#include "kblock.h"
+struct KBlockTable {
+    BlockEntry e[96];
+    int start[31];
+};
+constexpr KBlockTable make_kblock_table() {
+    KBlockTable T{};
+    int n = 0;
+    for (int t = 0; t < 30; ++t) {
+        T.start[t] = n;
+        for (int a = 0; a < 12; ++a)
+            for (int b = 0; b < 12; ++b)
+                if (kblock::tensor(a, b) == t) {
+                    T.e[n].a = (signed char)a;
+                    T.e[n].b = (signed char)b;
+                    T.e[n].s = (signed char)kblock::sign(a, b);
+                    ++n;
+                }
+    }
+    T.start[30] = n;
+    return T;
+}
+__device__ constexpr KBlockTable kKBlock = make_kblock_table();
+static_assert(make_kblock_table().start[30] == 96, "the K block has 96 non-zero entries from 30 tensors");
+
 // ---------------------------------------------------------------------------
 // cp.async (shared <- global) helpers
 // ---------------------------------------------------------------------------

@@ -119,6 +119,10 @@ struct vie_handle {
     float2* green32t;
     // FP64 copy in the same layout, for the FP64 fused z pass
     double2* green64t;
+    // the 30 K tensors' transformed circulants, octant storage [30][Oz][Oy][Ox], scaled by
+    // 1/(Lx Ly Lz), FP64 and FP32 (kmatvec.cu, built on the first K product)
+    double2* kgreen64;
+    float2* kgreen32;
     // bf16 split of green32t in the same layout, for the BF16x3 z pass: per tensor (hi, lo),
     // each a bf16 (re, im) pair with hi = bf16(v), lo = bf16(v - hi)
     uint2* greenbf;
@@ -310,6 +314,8 @@ int rhs_planewave_device(vie_handle* h, const double pol[3], const double dir[3]
 int rhs_dipoles_device(vie_handle* h, int nrhs, const double* pos, const double* mom, double2* e, double2* b,
                        cudaStream_t s);
 int materials_device(vie_handle* h, const double* eps_real, const double* sigma, cudaStream_t s);
+// kmatvec.cu: the K octant spectra of a handle, built on first use
+int k_octants(vie_handle* h, cudaStream_t s);
 // jmvie.cu: the full JM-VIE (Eq. 14-15), FP64.  Vectors [R][2][12][nz][ny][nx] (j, then m' = m / eta0).
 int jm_materials(vie_handle* h, const double* mu_real, const double* mu_imag, cudaStream_t s);  // device maps or NULL
 int jm_matvec_full(vie_handle* h, int R, const double2* x, double2* y, int op, cudaStream_t s,

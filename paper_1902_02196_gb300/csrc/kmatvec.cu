@@ -1,17 +1,16 @@
-// K operator matvec (K u = curl S u, Eq. 8), FP64: y = K x for nrhs vectors by circulant
-// embedding and 3-D FFTs (Section IV-A), the tested scattered magnetic field h~ = K x
-// (Eq. 13: h_sca = K j).
+// K operator (K u = curl S u, Eq. 8): its Green tensors in octant storage for the matvec, so
+// that y = K x (the tested scattered magnetic field h~ = K x, Eq. 13: h_sca = K j) runs the
+// same transforms as the N operator (Section IV-A) with the K block in the z pass (matvec.cu,
+// zpass_kernel with KOP), in FP64 or FP32.
 //
 // The 30 Toeplitz tensors P_t (green.cu, assemble_k_kernel) are embedded into full 2N
-// circulants, the entries at negative offsets taken from the reflection parities of the
-// block table (kblock.h), and transformed once per handle (kept in a table keyed by the
-// handle, released with it).  A matvec pads x into [12R][Lz][Ly][Lx], transforms forward,
-// applies the signed 12 x 12 K block at every frequency point, and transforms back as
-// conj(FFT(conj(.))) with the same forward transform; the 1/(Lx Ly Lz) of the inverse is
-// folded into the block product.  Correctness path: full spectra, no octant storage.
+// circulants, the entries at negative offsets taken from the reflection parities of the block
+// table (kblock.h), transformed, and their octant k_i in [0, L_i/2] kept, scaled by
+// 1/(Lx Ly Lz), as [30][Oz][Oy][Ox] in FP64 and FP32.  The other octants follow in the z pass
+// from the same parities: K(R_i k) = -S_i K(k) S_i.  Built on the first K product of a handle
+// and released with it.
 #include <algorithm>
 #include <mutex>
-#include <unordered_map>
 
 #include "common.cuh"
 #include "kblock.h"
@@ -20,16 +19,16 @@ int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);  // green.cu
 
 namespace {
 
-std::mutex g_kmu;
-std::unordered_map<const vie_handle*, double2*> g_kspec;  // [30][Lz][Ly][Lx] transformed circulants
+std::mutex g_kmu;  // the first K product of a handle builds its spectra once
 
-// circulant of the 30 tensors: C_t(j) = P_t(d), d = j (j < N) or j - L (j > L - N), else 0 per axis
-__global__ void embed_k_kernel(const double2* __restrict__ P, int nx, int ny, int nz, int Lx, int Ly, int Lz,
-                               double2* __restrict__ C) {
+// circulants of tensors t0 .. t0 + nt - 1: C_t(j) = P_t(d), d = j (j < N) or j - L (j > L - N),
+// else 0 per axis, with the reflection parity of the tensor's representative entry
+__global__ void embed_k_kernel(const double2* __restrict__ P, int nx, int ny, int nz, int Lx, int Ly, int Lz, int t0,
+                               int nt, double2* __restrict__ C) {
     const long long vol = (long long)Lx * Ly * Lz;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= vol * 30) return;
-    const int t = (int)(gid / vol);
+    if (gid >= vol * nt) return;
+    const int t = t0 + (int)(gid / vol);
     const long long j = gid % vol;
     const int J[3] = {(int)(j % Lx), (int)((j / Lx) % Ly), (int)(j / ((long long)Lx * Ly))};
     const int N[3] = {nx, ny, nz}, Lv[3] = {Lx, Ly, Lz};
@@ -55,140 +54,92 @@ __global__ void embed_k_kernel(const double2* __restrict__ P, int nx, int ny, in
     C[gid] = v;
 }
 
-// W[r][a] (vol each) <- x[r][a] zero-padded from [nz][ny][nx] to [Lz][Ly][Lx]
-__global__ void pad_kernel(const double2* __restrict__ x, int nx, int ny, int nz, int Lx, int Ly, int Lz,
-                           long long planes, double2* __restrict__ W) {
-    const long long vol = (long long)Lx * Ly * Lz;
+// octant k_i in [0, L_i/2] of the transformed circulants of tensors t0 .. t0 + nt - 1, scaled
+__global__ void k_octant_kernel(const double2* __restrict__ C, int Lx, int Ly, int Lz, int t0, int nt, double scale,
+                                double2* __restrict__ g64, float2* __restrict__ g32) {
+    const int Ox = Lx / 2 + 1, Oy = Ly / 2 + 1, Oz = Lz / 2 + 1;
+    const long long ovol = (long long)Ox * Oy * Oz;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= vol * planes) return;
-    const long long c = gid / vol, j = gid % vol;
-    const int jx = (int)(j % Lx), jy = (int)((j / Lx) % Ly), jz = (int)(j / ((long long)Lx * Ly));
-    double2 v = make_double2(0, 0);
-    if (jx < nx && jy < ny && jz < nz) v = x[((c * nz + jz) * ny + jy) * nx + jx];
-    W[gid] = v;
-}
-
-// at every frequency point of every right-hand side: Y_a = s sum_b sign(a, b) KS_t(a,b) X_b, stored
-// conjugated for the inverse by the forward transform; s = 1 / (Lx Ly Lz)
-__global__ void kblock_kernel(double2* __restrict__ W, const double2* __restrict__ KS, long long vol, int R,
-                              double s) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= vol * R) return;
-    const long long r = gid / vol, k = gid % vol;
-    double2* w = W + r * 12 * vol + k;
-    double2 X[12];
-#pragma unroll
-    for (int b = 0; b < 12; ++b) X[b] = w[b * vol];
-#pragma unroll
-    for (int a = 0; a < 12; ++a) {
-        double2 acc = make_double2(0, 0);
-#pragma unroll
-        for (int b = 0; b < 12; ++b) {
-            const int t = kblock::tensor(a, b);
-            if (t < 0) continue;
-            const double2 g = KS[(long long)t * vol + k];
-            const double sg = (double)kblock::sign(a, b);
-            acc.x += sg * (g.x * X[b].x - g.y * X[b].y);
-            acc.y += sg * (g.x * X[b].y + g.y * X[b].x);
-        }
-        w[a * vol] = make_double2(s * acc.x, -s * acc.y);
-    }
-}
-
-// y[c] <- conj(W[c]) cropped from [Lz][Ly][Lx] to [nz][ny][nx]
-__global__ void crop_conj_kernel(const double2* __restrict__ W, int nx, int ny, int nz, int Lx, int Ly, int Lz,
-                                 long long planes, double2* __restrict__ y) {
-    const long long nv = (long long)nx * ny * nz;
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= nv * planes) return;
-    const long long c = gid / nv, i = gid % nv;
-    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
-    const double2 v = W[c * (long long)Lx * Ly * Lz + ((long long)iz * Ly + iy) * Lx + ix];
-    y[gid] = make_double2(v.x, -v.y);
+    if (gid >= ovol * nt) return;
+    const int tl = (int)(gid / ovol);
+    const long long o = gid % ovol;
+    const int kx = (int)(o % Ox), ky = (int)((o / Ox) % Oy), kz = (int)(o / ((long long)Ox * Oy));
+    double2 v = C[(long long)tl * Lx * Ly * Lz + ((long long)kz * Ly + ky) * Lx + kx];
+    v.x *= scale;
+    v.y *= scale;
+    const long long dst = (long long)(t0 + tl) * ovol + o;
+    g64[dst] = v;
+    g32[dst] = make_float2((float)v.x, (float)v.y);
 }
 
 unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
-// the transformed K circulants of this handle, built on first use
-int kspectrum(vie_handle* h, cudaStream_t s, const double2** out) {
+}  // namespace
+
+// the K octant spectra of the handle (h->kgreen64, h->kgreen32), built on first use
+int k_octants(vie_handle* h, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_kmu);
-    auto it = g_kspec.find(h);
-    if (it != g_kspec.end()) {
-        *out = it->second;
-        return VIE_OK;
-    }
+    if (h->kgreen64) return VIE_OK;
     const int Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
     const long long vol = (long long)Lx * Ly * Lz, nd = (long long)h->nv;
-    double2 *P = nullptr, *C = nullptr;
-    if (cudaMalloc(&P, sizeof(double2) * 30 * nd) != cudaSuccess ||
-        cudaMalloc(&C, sizeof(double2) * 30 * vol) != cudaSuccess) {
+    const long long ovol = (long long)h->O[0] * h->O[1] * h->O[2];
+    const int chunk = (int)std::max<long long>(1, std::min<long long>(30, (4LL << 30) / (vol * (long long)sizeof(double2))));
+    double2 *P = nullptr, *C = nullptr, *g64 = nullptr;
+    float2* g32 = nullptr;
+    auto fail = [&](int code, const char* msg) {
         cudaGetLastError();
         cudaFree(P);
         cudaFree(C);
-        set_error("K spectrum allocation failed");
-        return VIE_ENOMEM;
-    }
+        cudaFree(g64);
+        cudaFree(g32);
+        set_error(msg);
+        return code;
+    };
+    if (cudaMalloc(&P, sizeof(double2) * 30 * nd) != cudaSuccess ||
+        cudaMalloc(&C, sizeof(double2) * vol * chunk) != cudaSuccess ||
+        cudaMalloc(&g64, sizeof(double2) * 30 * ovol) != cudaSuccess ||
+        cudaMalloc(&g32, sizeof(float2) * 30 * ovol) != cudaSuccess)
+        return fail(VIE_ENOMEM, "K spectrum allocation failed");
     int rc = green_k_toeplitz(h, P, s);
-    if (rc == VIE_OK) {
-        VIE_KLAUNCH("k_embed", s, embed_k_kernel<<<blocks(vol * 30), 256, 0, s>>>(P, h->nx, h->ny, h->nz, Lx, Ly, Lz, C));
-        if (cudaGetLastError() != cudaSuccess) rc = (set_error("K embed launch"), VIE_EDEVICE);
+    for (int t0 = 0; rc == VIE_OK && t0 < 30; t0 += chunk) {
+        const int nt = std::min(chunk, 30 - t0);
+        VIE_KLAUNCH("k_embed", s,
+                    embed_k_kernel<<<blocks(vol * nt), 256, 0, s>>>(P, h->nx, h->ny, h->nz, Lx, Ly, Lz, t0, nt, C));
+        if (cudaGetLastError() != cudaSuccess) return fail(VIE_EDEVICE, "K embed launch failed");
+        rc = fft3d_inplace64(h, C, nt, s);
+        if (rc < 0) break;
+        VIE_KLAUNCH("k_octant", s,
+                    k_octant_kernel<<<blocks(ovol * nt), 256, 0, s>>>(C, Lx, Ly, Lz, t0, nt, 1.0 / (double)vol, g64,
+                                                                      g32));
+        if (cudaGetLastError() != cudaSuccess) return fail(VIE_EDEVICE, "K octant launch failed");
     }
-    if (rc == VIE_OK) rc = fft3d_inplace64(h, C, 30, s);
-    if (rc == VIE_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = (set_error("K spectrum sync"), VIE_EDEVICE);
-    cudaFree(P);
-    if (rc != VIE_OK) {
+    if (rc == VIE_OK && cudaStreamSynchronize(s) != cudaSuccess) return fail(VIE_EDEVICE, "K spectrum sync failed");
+    if (rc < 0) {
+        cudaFree(P);
         cudaFree(C);
+        cudaFree(g64);
+        cudaFree(g32);
         return rc;
     }
-    g_kspec[h] = C;
-    h->bytes_held += sizeof(double2) * 30 * (size_t)vol;  // counted until kmatvec_release
-    *out = C;
+    cudaFree(P);
+    cudaFree(C);
+    h->kgreen64 = g64;
+    h->kgreen32 = g32;
+    h->bytes_held += (sizeof(double2) + sizeof(float2)) * 30 * (size_t)ovol;  // until kmatvec_release
     return VIE_OK;
 }
 
-// right-hand sides per pass of the K matvec: the padded spectra of a pass ([12 Rc][Lz][Ly][Lx]
-// FP64) stay within 4 GiB of scratch, one right-hand side at least
-constexpr size_t kKPassBytes = size_t(4) << 30;
-
-}  // namespace
-
-// y = K x, FP64, x and y device [R][12][nz][ny][nx]; the right-hand sides go through in passes
-// of at most kKPassBytes of padded spectra each
+// y = K x, FP64, x and y device [R][12][nz][ny][nx]
 int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s) {
-    const double2* KS = nullptr;
-    VIE_TRY(kspectrum(h, s, &KS));
-    const int Lx = h->L[0], Ly = h->L[1], Lz = h->L[2];
-    const long long vol = (long long)Lx * Ly * Lz, nv = (long long)h->nv;
-    const size_t per_rhs = sizeof(double2) * 12 * (size_t)vol;
-    const int Rc = (int)std::max<size_t>(1, std::min<size_t>((size_t)R, kKPassBytes / per_rhs));
-    VIE_TRY(ws_reserve(h, h->post_ws, per_rhs * (size_t)Rc));
-    double2* W = static_cast<double2*>(h->post_ws.ptr);
-    for (int r0 = 0; r0 < R; r0 += Rc) {
-        const int Rp = std::min(Rc, R - r0);
-        const long long planes = 12LL * Rp;
-        const double2* xp = x + (long long)r0 * 12 * nv;
-        double2* yp = y + (long long)r0 * 12 * nv;
-        VIE_KLAUNCH("k_pad", s,
-                    pad_kernel<<<blocks(vol * planes), 256, 0, s>>>(xp, h->nx, h->ny, h->nz, Lx, Ly, Lz, planes, W));
-        VIE_CHECK_LAUNCH();
-        VIE_TRY(fft3d_inplace64(h, W, (int)planes, s));
-        VIE_KLAUNCH("k_block", s, kblock_kernel<<<blocks(vol * Rp), 256, 0, s>>>(W, KS, vol, Rp, 1.0 / (double)vol));
-        VIE_CHECK_LAUNCH();
-        VIE_TRY(fft3d_inplace64(h, W, (int)planes, s));
-        VIE_KLAUNCH("k_crop", s,
-                    crop_conj_kernel<<<blocks(nv * planes), 256, 0, s>>>(W, h->nx, h->ny, h->nz, Lx, Ly, Lz, planes,
-                                                                           yp));
-        VIE_CHECK_LAUNCH();
-    }
-    return VIE_OK;
+    return matvec_device(h, R, x, y, VIE_FP64, VIE_OP_K, s);
 }
 
-// frees the handle's K spectrum, if any (called when the handle is released)
+// frees the handle's K spectra, if any (called when the handle is released)
 void kmatvec_release(vie_handle* h) {
-    std::lock_guard<std::mutex> lk(g_kmu);
-    auto it = g_kspec.find(h);
-    if (it == g_kspec.end()) return;
-    cudaFree(it->second);
-    g_kspec.erase(it);
-    h->bytes_held -= sizeof(double2) * 30 * (size_t)h->L[0] * h->L[1] * h->L[2];
+    if (!h->kgreen64) return;
+    cudaFree(h->kgreen64);
+    cudaFree(h->kgreen32);
+    h->kgreen64 = nullptr;
+    h->kgreen32 = nullptr;
+    h->bytes_held -= (sizeof(double2) + sizeof(float2)) * 30 * (size_t)h->O[0] * h->O[1] * h->O[2];
 }

@@ -59,6 +59,25 @@ __device__ __forceinline__ void block_product(C* xv, C* acc, const C* __restrict
     }
 }
 
+// y[12] = K(k) x[12] at one frequency point (VIE_OP_K): the 96 signed entries of the 30 tensors
+template <typename C>
+__device__ __forceinline__ void block_product_k(C* xv, C* acc, const C* __restrict__ gp, long long tstride) {
+#pragma unroll
+    for (int a = 0; a < 12; ++a) acc[a] = mk(decltype(xv[0].x)(0), decltype(xv[0].x)(0));
+#pragma unroll
+    for (int t = 0; t < 30; ++t) {
+        const C u = gp[t * tstride];
+#pragma unroll
+        for (int i = kKBlock.start[t]; i < kKBlock.start[t + 1]; ++i) {
+            const int a = kKBlock.e[i].a, b = kKBlock.e[i].b;
+            if (kKBlock.e[i].s > 0)
+                cfma(acc[a], u, xv[b]);
+            else
+                cfma(acc[a], cneg(u), xv[b]);
+        }
+    }
+}
+
 template <typename T, int L, int NC = 12>
 struct ZCfg {
     static constexpr int TB0 = (sizeof(T) == 4 ? 1024 : 512) / L;
@@ -80,7 +99,9 @@ struct ZArgs {
     int ay, by;
 };
 
-template <typename T, int L, int NC>
+// KOP: the K block (Eq. 8, 25) instead of the N block, on the 30 K tensors; a frequency point
+// reflected along an odd number of axes also changes the block's overall sign (the curl's parity)
+template <typename T, int L, int NC, bool KOP = false>
 __global__ void __launch_bounds__(ZCfg<T, L, NC>::NT) zpass_kernel(ZArgs z, const typename CT<T>::C* twg) {
     using C = typename CT<T>::C;
     constexpr int TB = ZCfg<T, L, NC>::TB, GS = ZCfg<T, L, NC>::GS, NT = ZCfg<T, L, NC>::NT;
@@ -122,6 +143,8 @@ __global__ void __launch_bounds__(ZCfg<T, L, NC>::NT) zpass_kernel(ZArgs z, cons
             int kxo = kx <= z.Lx / 2 ? kx : z.Lx - kx;
             int kzo = kz <= Lz / 2 ? kz : Lz - kz;
             unsigned mask = fy ^ (kx > z.Lx / 2 ? z.mx : 0u) ^ (kz > Lz / 2 ? z.mz : 0u);
+            unsigned omask = mask;  // output flips
+            if (KOP && (((ky > z.Ly / 2) + (kx > z.Lx / 2) + (kz > Lz / 2)) & 1)) omask ^= 0xFFFu;
             C xv[NC], acc[NC];
 #pragma unroll
             for (int b = 0; b < NC; ++b) {
@@ -129,12 +152,14 @@ __global__ void __launch_bounds__(ZCfg<T, L, NC>::NT) zpass_kernel(ZArgs z, cons
                 xv[b] = ((mask >> b) & 1u) ? cneg(v) : v;
             }
             const C* gp = green + ((long long)kzo * z.Oy + kyo) * z.Ox + kxo;
-            if constexpr (NC == 12)
+            if constexpr (KOP)
+                block_product_k(xv, acc, gp, z.tstride);
+            else if constexpr (NC == 12)
                 block_product(xv, acc, gp, z.tstride);
             else
                 block_product_pwc(xv, acc, gp, z.tstride);
 #pragma unroll
-            for (int a = 0; a < NC; ++a) s[a * GS + kz * TB + tb] = ((mask >> a) & 1u) ? cneg(acc[a]) : acc[a];
+            for (int a = 0; a < NC; ++a) s[a * GS + kz * TB + tb] = ((omask >> a) & 1u) ? cneg(acc[a]) : acc[a];
         }
         __syncthreads();
         fft_smem<C, L, NC, TB, TB, GS, NT>(s, tw, +1);
@@ -451,36 +476,38 @@ static int launch_line(const char* name, const vie_handle* h, int L, const LineA
     return VIE_EINVAL;
 }
 
-template <typename T, int L, int NC>
+template <typename T, int L, int NC, bool KOP = false>
 static int launch_z_L(const char* name, const vie_handle* h, const ZArgs& z, cudaStream_t s) {
     using C = typename CT<T>::C;
     using Cfg = ZCfg<T, L, NC>;
     constexpr int TB = Cfg::TB;
     size_t smem = sizeof(C) * (size_t)(NC * Cfg::GS + L);
     // set on every call: the attribute is per device and launches may come from several threads
-    VIE_CUDA(cudaFuncSetAttribute(zpass_kernel<T, L, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VIE_CUDA(cudaFuncSetAttribute(zpass_kernel<T, L, NC, KOP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     long long blocks = (long long)z.Ly * ((z.Lx + TB - 1) / TB);
-    // the z lines read and written once, and the octant tensors the block reads (60 or 6)
+    // the z lines read and written once, and the octant tensors the block reads (60, 30 or 6)
     const double bytes = (double)sizeof(C) * (2.0 * z.R * NC * z.nz * z.Ly * z.Lx +
-                                              (NC == 12 ? 60.0 : 6.0) * z.Ox * z.Oy * z.Oz);
-    VIE_KLAUNCH_B(name, s, bytes, zpass_kernel<T, L, NC><<<(unsigned)blocks, Cfg::NT, smem, s>>>(z, twiddles<T>(h, L)));
+                                              (KOP ? 30.0 : (NC == 12 ? 60.0 : 6.0)) * z.Ox * z.Oy * z.Oz);
+    VIE_KLAUNCH_B(name, s, bytes,
+                  (zpass_kernel<T, L, NC, KOP><<<(unsigned)blocks, Cfg::NT, smem, s>>>(z, twiddles<T>(h, L))));
     VIE_CHECK_LAUNCH();
     return VIE_OK;
 }
 
-template <typename T, int NC = 12>
+template <typename T, int NC = 12, bool KOP = false>
 static int launch_z(const char* name, const vie_handle* h, int L, const ZArgs& z, cudaStream_t s) {
     switch (L) {
-        case 2: return launch_z_L<T, 2, NC>(name, h, z, s);
-        case 4: return launch_z_L<T, 4, NC>(name, h, z, s);
-        case 8: return launch_z_L<T, 8, NC>(name, h, z, s);
-        case 16: return launch_z_L<T, 16, NC>(name, h, z, s);
-        case 32: return launch_z_L<T, 32, NC>(name, h, z, s);
-        case 64: return launch_z_L<T, 64, NC>(name, h, z, s);
-        case 128: return launch_z_L<T, 128, NC>(name, h, z, s);
-        case 256: return launch_z_L<T, 256, NC>(name, h, z, s);
-        case 512: return launch_z_L<T, 512, NC>(name, h, z, s);
-        case 1024: return launch_z_L<T, 1024, NC>(name, h, z, s);
+        case 2: return launch_z_L<T, 2, NC, KOP>(name, h, z, s);
+        case 4: return launch_z_L<T, 4, NC, KOP>(name, h, z, s);
+        case 8: return launch_z_L<T, 8, NC, KOP>(name, h, z, s);
+        case 16: return launch_z_L<T, 16, NC, KOP>(name, h, z, s);
+        case 32: return launch_z_L<T, 32, NC, KOP>(name, h, z, s);
+        case 64: return launch_z_L<T, 64, NC, KOP>(name, h, z, s);
+        case 128: return launch_z_L<T, 128, NC, KOP>(name, h, z, s);
+        case 256: return launch_z_L<T, 256, NC, KOP>(name, h, z, s);
+        case 512: return launch_z_L<T, 512, NC, KOP>(name, h, z, s);
+        case 1024: return launch_z_L<T, 1024, NC, KOP>(name, h, z, s);
     }
     set_error("unsupported FFT length " + std::to_string(L));
     return VIE_EINVAL;
@@ -605,7 +632,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     C* W2 = xy_ok(h) ? W1 : W1 + comps * ny * Lx;
     MatvecEpi e{};
     e.x = x;
-    e.op = op;
+    e.op = op == VIE_OP_K ? VIE_OP_NSCAT : op;  // K: the plain product, no voxel-wise terms
     e.nc = nc;
     e.nx = nx, e.ny = ny, e.nz = nz;
     const double dV = h->dx * h->dy * h->dz;
@@ -633,6 +660,22 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
+        if (op == VIE_OP_K) {  // the generic z pass with the K block on the 30 K tensors
+            if (bf16 || nc != 12 || !h->kgreen64) {
+                set_error("the K operator runs in FP64 or FP32 on the PWL system");
+                return VIE_EINVAL;
+            }
+            ZArgs z{};
+            z.w = W2;
+            z.green = sizeof(T) == 8 ? (const void*)h->kgreen64 : (const void*)h->kgreen32;
+            z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+            z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+            z.tstride = (long long)h->O[0] * h->O[1] * h->O[2];
+            z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+            z.colkx = h->colkx32;
+            z.ay = ay, z.by = by;
+            return launch_z<T, 12, true>(sizeof(T) == 8 ? "zpass_block_k_f64" : "zpass_block_k_f32", h, Lz, z, s);
+        }
         if (nc == 3) {  // PWC: the generic z pass with the 3 x 3 block of the l = 1 tensors
             if (bf16) {
                 set_error("the BF16x3 matvec is built for the PWL system only");
@@ -768,6 +811,7 @@ int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s) {
 
 static int matvec_full(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s,
                        void* conv) {
+    if (op == VIE_OP_K) VIE_TRY(k_octants(h, s));
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, nrhs, precision)));
     if (precision == VIE_FP64) return matvec_impl<double>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv);
     return matvec_impl<float>(h, nrhs, x, y, op, s, h->fft_ws.ptr, Support{}, nullptr, conv, nullptr, nullptr,

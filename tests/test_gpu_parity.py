@@ -101,21 +101,26 @@ def test_green_toeplitz_k_parity(vie, shape, delta):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("shape,nrhs", [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 5, 6), 2)])
+@pytest.mark.parametrize("shape,nrhs", [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 5, 6), 2), ((16, 16, 20), 2),
+                                         ((40, 40, 9), 1), ((3, 4, 70), 1)])
 def test_k_matvec_parity(vie, shape, nrhs):
-    """y = K x (VIE_OP_K, FP64) vs the oracle's K operator (its own K tensors, circulant + FFT)."""
+    """y = K x (VIE_OP_K, FP64 and FP32: the N operator's transforms with the K block on the octant
+    K spectra) vs the oracle's K operator (its own K tensors, circulant + FFT), on grids that take the
+    fused xy kernels (16 x 16 x 20, 40 x 40 x 9) and the line transforms (Lz = 256 for 3 x 4 x 70)."""
     g = Grid(*shape, 0.004, 0.005, 0.0045)
     eps, sig = random_tissue(g, seed=sum(shape) + 1)
     freq = 298e6
     h = setup(vie, g, freq, eps, sig)
     x = random_coefficients(g, nrhs, seed=21 + nrhs)
     y = gpu_matvec(vie, h, x, vie.VIE_FP64, vie.VIE_OP_K)
+    y32 = gpu_matvec(vie, h, x, vie.VIE_FP32, vie.VIE_OP_K)
     with pytest.raises(vie.VieError) as e:
-        gpu_matvec(vie, h, x, vie.VIE_FP32, vie.VIE_OP_K)
+        gpu_matvec(vie, h, x, vie.VIE_BF16X3, vie.VIE_OP_K)
     assert e.value.code == vie.VIE_EINVAL
     h.close()
     ref = O.KOperator(g, O.k0_of(freq)).apply(x)
     assert rel(y, ref) <= 1e-12
+    assert rel(y32, ref) <= 1e-5
 
 
 @pytest.mark.parametrize("shape", [(6, 5, 4), (9, 7, 6)])
