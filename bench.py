@@ -903,9 +903,10 @@ def run_tucker(args, local):
 
 def run_jm(args, local):
     """Full JM-VIE (vie_jm_*): a magnetodielectric sphere (eps_r 50, sigma 0.5 S/m, mu_r 2 - 0.5 i,
-    radius 0.1 m) in an x-polarised plane wave along z at 298 MHz on 16^3 .. 32^3: FP64 GMRES to
-    1e-8, the absorbed power (electric + magnetic loss) under refinement, and the solve time.  (The
-    comparison with the Mie series is a GPU test.)"""
+    radius 0.1 m) in an x-polarised plane wave along z at 298 MHz on 16^3 .. 64^3: GMRES to 1e-8 in
+    FP64 and in FP32 with FP64 refinement, the absorbed power (electric + magnetic loss) under
+    refinement, and the solve times (the K spectra built by one product before the timed solves).
+    (The comparison with the Mie series is a GPU test.)"""
     import numpy as np
     import torch
 
@@ -917,7 +918,7 @@ def run_jm(args, local):
     f, eta0 = 298e6, 1.0 / (8.8541878128e-12 * 299792458.0)
     mu_s = 2.0 - 0.5j
     rows = []
-    for n in (16, 24, 32):
+    for n in (16, 24, 32, 64):
         hgt = 0.2 / n
         g = Grid(n, n, n, hgt, hgt, hgt)
         eps, sig = sphere_phantom(g, 0.1, 50.0, 0.5)
@@ -931,13 +932,18 @@ def run_jm(args, local):
         b = np.empty((1, 2, 12) + g.shape, dtype=np.complex128)
         vie.vie_jm_rhs(h, e_t, h_t, b)
         x = np.empty_like(b)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, info = vie.vie_jm_solve(h, b, x, tol=1e-8, restart=60, maxit=40)
-        sec = time.perf_counter() - t0
-        P = vie.vie_jm_fields(h, x, e_t, h_t)[0]
+        vie.vie_jm_matvec(h, b, x, vie.VIE_OP_PA)  # builds the K spectra
+        row = dict(n=n)
+        for tag, mode in (("fp64", vie.VIE_SOLVE_FP64), ("fp32_refine", vie.VIE_SOLVE_FP32_REFINE)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = vie.vie_jm_solve(h, b, x, tol=1e-8, restart=60, maxit=40, mode=mode)
+            sec = time.perf_counter() - t0
+            P = vie.vie_jm_fields(h, x, e_t, h_t)[0]
+            row[tag] = dict(rc=rc, seconds=sec, iterations=info[0]["iterations"], fp64_matvecs=info[0]["fp64_matvecs"],
+                            fp32_matvecs=info[0]["fp32_matvecs"], P_abs=P)
         h.close()
-        rows.append(dict(n=n, rc=rc, seconds=sec, iterations=info[0]["iterations"], P_abs=P))
+        rows.append(row)
     # the K operator (row f1) on the head64 batch: FP64 K matvec of 16 right-hand sides (the K
     # spectrum built on first use, timed apart) and the magnetic post-processing (h, b1+, W_m)
     from synth import workload

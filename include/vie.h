@@ -347,7 +347,8 @@ int vie_hfields(vie_handle* h, int nrhs, const void* x, const void* h_inc, void*
 /*
  * Full JM-VIE (Eq. 14-15): polarization current j and magnetization current m of a scatterer
  * with relative permeability mu_r = mu' - i mu'' (Eq. 1-2; chi_m = mu_r - 1, Eq. 7).  PWL
- * handles only, FP64 throughout (the K products are those of VIE_OP_K).
+ * handles only, FP64 (the K products are those of VIE_OP_K; vie_jm_solve can run its inner
+ * GMRES in FP32).
  *
  * Unknowns: both currents in the PWL functions of Section III, with the magnetization scaled,
  * m' = m / eta0 (eta0 = sqrt(mu0/eps0)), and the second row of Eq. 15 divided by eta0.  Since
@@ -384,17 +385,21 @@ int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int op, void*
 int vie_jm_rhs(vie_handle* h, int nrhs, const void* e_inc, const void* h_inc, void* b, void* stream);
 
 /*
- * vie_jm_solve -- restarted GMRES(restart) on P^-1 A x = P^-1 b of the JM system, FP64, with the
+ * vie_jm_solve -- restarted GMRES(restart) on P^-1 A x = P^-1 b of the JM system with the
  * batched device Arnoldi steps of vie_solve (the restart cycles launched directly, not as CUDA
  * graphs), stopping when ||P^-1 (b - A x)|| / ||P^-1 b|| <= tol.  The solver's vectors cover the
  * voxels where chi_e, chi_m, b or the guess is non-zero (rows of the grid as for vie_solve).
  *   b, x  : [nrhs][2][12][nz][ny][nx] C128; x is the initial guess when (flags & 1)
+ *   mode  : VIE_SOLVE_FP64, or VIE_SOLVE_FP32_REFINE (FP32 inner GMRES, both products of the
+ *           operator in FP32, inside FP64 iterative refinement as vie_solve's mode of that name);
+ *           VIE_SOLVE_BF16X3_REFINE is refused (the K block has no BF16x3 z pass)
  *   flags : bit 0 = use x as initial guess; bit 1 = also compute true_resid (||b - A x|| / ||b||)
  *   info  : vie_solve_info[nrhs] or NULL
- * Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol.
+ * Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol; VIE_EINVAL for
+ * an unknown mode or flag.
  */
-int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int flags,
-                 vie_solve_info* info, void* stream);
+int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int mode,
+                 int flags, vie_solve_info* info, void* stream);
 
 /*
  * vie_jm_fields -- total fields of the JM solution (Eq. 13, tested, then divided by G):

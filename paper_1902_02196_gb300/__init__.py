@@ -111,7 +111,7 @@ def _lib():
     lib.vie_green_tucker.argtypes = [P, D, I, P, P, ctypes.POINTER(S)]
     lib.vie_jm_matvec.argtypes = [P, I, P, P, I, P]
     lib.vie_jm_rhs.argtypes = [P, I, P, P, P, P]
-    lib.vie_jm_solve.argtypes = [P, I, P, P, D, I, I, I, ctypes.POINTER(vie_solve_info), P]
+    lib.vie_jm_solve.argtypes = [P, I, P, P, D, I, I, I, I, ctypes.POINTER(vie_solve_info), P]
     lib.vie_jm_fields.argtypes = [P, I, P, P, P, P, P, P, ctypes.POINTER(D), P]
     lib.vie_strerror.argtypes = [I]
     lib.vie_strerror.restype = ctypes.c_char_p
@@ -320,13 +320,15 @@ def vie_jm_rhs(h, e_inc, h_inc, b, stream=None):
                   "vie_jm_rhs")
 
 
-def vie_jm_solve(h, b, x, tol=1e-6, restart=50, maxit=200, guess=False, true_resid=False, stream=None):
-    """FP64 GMRES on the JM system; returns (rc, [info dict per right-hand side])."""
+def vie_jm_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP64, guess=False, true_resid=False,
+                 stream=None):
+    """GMRES on the JM system (FP64, or FP32 inner solves with FP64 refinement); returns
+    (rc, [info dict per right-hand side])."""
     n = _nrhs_jm(b, h)
     info = (vie_solve_info * n)()
     flags = (1 if guess else 0) | (2 if true_resid else 0)
-    rc = _check(_lib().vie_jm_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), flags, info,
-                                    _stream(stream)), "vie_jm_solve")
+    rc = _check(_lib().vie_jm_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
+                                    flags, info, _stream(stream)), "vie_jm_solve")
     return rc, [i.as_dict() for i in info]
 
 

@@ -608,8 +608,8 @@ int vie_jm_rhs(vie_handle* h, int nrhs, const void* e_inc, const void* h_inc, vo
     return sg.finish(d);
 }
 
-int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int flags,
-                 vie_solve_info* info, void* stream) {
+int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, int restart, int maxit, int mode,
+                 int flags, vie_solve_info* info, void* stream) {
     g_last_error.clear();
     REQUIRE(h && b && x, "NULL argument");
     REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
@@ -617,6 +617,7 @@ int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, in
     REQUIRE(std::isfinite(tol) && tol > 0 && tol < 1, "tol must be in (0, 1)");
     REQUIRE(restart >= 1 && restart <= 128, "restart must be in [1, 128]");
     REQUIRE(maxit >= 1, "maxit must be >= 1");
+    REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE, "mode must be VIE_SOLVE_FP64 or VIE_SOLVE_FP32_REFINE");
     REQUIRE((flags & ~3) == 0, "unknown flags");
     const size_t bytes = (size_t)nrhs * 24 * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
@@ -626,8 +627,8 @@ int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, in
     std::vector<void*> d;
     VIE_TRY(sg.bind(d));
     sg.items[1].is_out = true;
-    int rc = solve_device(h, nrhs, (const double2*)d[0], (double2*)d[1], tol, restart, maxit, VIE_SOLVE_FP64,
-                          flags | 4, info, st, true);
+    int rc = solve_device(h, nrhs, (const double2*)d[0], (double2*)d[1], tol, restart, maxit, mode, flags | 4, info,
+                          st, true);
     if (rc < 0) return rc;
     VIE_TRY(sg.finish(d));
     VIE_CUDA(cudaStreamSynchronize(st));

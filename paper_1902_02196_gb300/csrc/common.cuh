@@ -316,12 +316,13 @@ int rhs_dipoles_device(vie_handle* h, int nrhs, const double* pos, const double*
 int materials_device(vie_handle* h, const double* eps_real, const double* sigma, cudaStream_t s);
 // kmatvec.cu: the K octant spectra of a handle, built on first use
 int k_octants(vie_handle* h, cudaStream_t s);
-// jmvie.cu: the full JM-VIE (Eq. 14-15), FP64.  Vectors [R][2][12][nz][ny][nx] (j, then m' = m / eta0).
+// jmvie.cu: the full JM-VIE (Eq. 14-15).  Vectors [R][2][12][nz][ny][nx] (j, then m' = m / eta0);
+// the support form runs in FP64 (double2 vectors) or FP32 (float2), the full form in FP64.
 int jm_materials(vie_handle* h, const double* mu_real, const double* mu_imag, cudaStream_t s);  // device maps or NULL
 int jm_matvec_full(vie_handle* h, int R, const double2* x, double2* y, int op, cudaStream_t s,
                    const double2* shift = nullptr);
-int jm_matvec_support(vie_handle* h, int R, const double2* x, double2* y, int op, const Support& sp, void* tmp,
-                      cudaStream_t s, const double2* shift);
+int jm_matvec_support(vie_handle* h, int R, const void* x, void* y, int op, const Support& sp, void* tmp,
+                      cudaStream_t s, const double2* shift, int precision);
 int jm_rhs_device(vie_handle* h, int R, const double2* einc, const double2* hinc, double2* b, cudaStream_t s);
 int jm_fields_device(vie_handle* h, int R, const double2* x, const double2* einc, const double2* hinc, double2* eout,
                      double2* hout, double* p_abs, double* P_abs_host, cudaStream_t s);

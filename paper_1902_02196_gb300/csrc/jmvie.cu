@@ -9,19 +9,19 @@
 // so that both unknowns have the same size (j ~ c_e e, m' ~ c_e e as well), and the
 // preconditioner is P = diag(M_eps G, M_mu G).  Vectors are [R][2][12][nz][ny][nx]: j, then m'.
 //
-// The operator is composed from the library's FP64 matvecs on the 2R stacked currents: one
-// (N - G) product (VIE_OP_NSCAT) and one K product (Eq. 8), then one element-wise kernel that
-// forms both rows (N = (N - G) + G, and eps - chi_e = mu - chi_m = 1):
+// The operator is composed from the library's matvecs on the 2R stacked currents: one (N - G)
+// product (VIE_OP_NSCAT) and one K product (Eq. 8), then one element-wise kernel that forms both
+// rows (N = (N - G) + G, and eps - chi_e = mu - chi_m = 1):
 //     row j : G j  - chi_e (N - G) j  + i k0 chi_e K m'
 //     row m': G m' - chi_m (N - G) m' - i k0 chi_m K j
-// (P^-1 A divides each row by eps G, resp. mu G).  This is a correctness path in FP64, off the
-// tissue path (tissue is non-magnetic, which reduces the system to Eq. 16).
+// (P^-1 A divides each row by eps G, resp. mu G).  The products run in FP64, or in FP32 for the
+// inner solves of the mixed-precision mode (FP64 refinement around them); the material maps stay
+// FP64 and are rounded in the combining kernel.  Off the tissue path: tissue is non-magnetic,
+// which reduces the system to Eq. 16.
 #include <cmath>
 #include <vector>
 
 #include "common.cuh"
-
-int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s);  // kmatvec.cu
 
 namespace {
 
@@ -52,13 +52,34 @@ __global__ void jm_materials_kernel(const double* __restrict__ mr, const double*
     sup[v] = make_double2(hypot(c.x, c.y) + hypot(m.x - 1.0, m.y), 0.0);
 }
 
+template <typename C>
+__device__ __forceinline__ C to_c(double2 v);
+template <>
+__device__ __forceinline__ double2 to_c<double2>(double2 v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float2 to_c<float2>(double2 v) {
+    return make_float2((float)v.x, (float)v.y);
+}
+template <typename C>
+__device__ __forceinline__ C cdiv(C a, C b) {
+    const auto d = b.x * b.x + b.y * b.y;
+    C r;
+    r.x = (a.x * b.x + a.y * b.y) / d;
+    r.y = (a.y * b.x - a.x * b.y) / d;
+    return r;
+}
+
 // y = A x (op VIE_OP_A) or P^-1 A x - shift x (op VIE_OP_PA), from x, nx = (N - G) x and kx = K x,
-// all [R][2][12][nv]
-__global__ void jm_combine_kernel(const double2* __restrict__ x, const double2* __restrict__ nx,
-                                  const double2* __restrict__ kx, const double2* __restrict__ eps,
-                                  const double2* __restrict__ chie, const double2* __restrict__ mu,
-                                  const double2* __restrict__ chim, double2* __restrict__ y, long long nv, int R,
-                                  int op, double k0, double g1, double g234, const double2* __restrict__ shift) {
+// all [R][2][12][nv], in the precision of C (the material maps are read in FP64 and rounded)
+template <typename C>
+__global__ void jm_combine_kernel(const C* __restrict__ x, const C* __restrict__ nx, const C* __restrict__ kx,
+                                  const double2* __restrict__ eps, const double2* __restrict__ chie,
+                                  const double2* __restrict__ mu, const double2* __restrict__ chim, C* __restrict__ y,
+                                  long long nv, int R, int op, double k0, double g1, double g234,
+                                  const double2* __restrict__ shift) {
+    using T = decltype(C{}.x);
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long half_len = 12 * nv;
     if (e >= 2 * half_len * R) return;
@@ -68,24 +89,24 @@ __global__ void jm_combine_kernel(const double2* __restrict__ x, const double2* 
     const int alpha = (int)((rem / nv) % 12);
     const long long v = e % nv;
     const long long eo = half ? e - half_len : e + half_len;  // the same unknown of the other current
-    const double g = comp_is_constant(alpha, 12) ? g1 : g234;
-    const double2 c = half ? chim[v] : chie[v];
+    const T g = (T)(comp_is_constant(alpha, 12) ? g1 : g234);
+    const C c = to_c<C>(half ? chim[v] : chie[v]);
     // coupling: + i k0 c K m' in row j, - i k0 c K j in row m'
-    const double s = half ? -k0 : k0;
-    const double2 ko = kx[eo];
-    const double2 cpl = zmul(c, make_double2(-s * ko.y, s * ko.x));
-    const double2 cn = zmul(c, nx[e]);
-    const double2 xv = x[e];
-    double2 out;
+    const T s = (T)(half ? -k0 : k0);
+    const C ko = kx[eo];
+    const C cpl = cmul(c, mk(-s * ko.y, s * ko.x));
+    const C cn = cmul(c, nx[e]);
+    const C xv = x[e];
+    C out;
     if (op == VIE_OP_A) {
-        out = make_double2(g * xv.x - cn.x + cpl.x, g * xv.y - cn.y + cpl.y);
+        out = mk(g * xv.x - cn.x + cpl.x, g * xv.y - cn.y + cpl.y);
     } else {
-        const double2 m = half ? mu[v] : eps[v];
-        const double2 t = zdiv(make_double2((cpl.x - cn.x) / g, (cpl.y - cn.y) / g), m);
-        const double2 xm = zdiv(xv, m);
-        out = make_double2(xm.x + t.x, xm.y + t.y);
+        const C m = to_c<C>(half ? mu[v] : eps[v]);
+        const C t = cdiv(mk((cpl.x - cn.x) / g, (cpl.y - cn.y) / g), m);
+        const C xm = cdiv(xv, m);
+        out = mk(xm.x + t.x, xm.y + t.y);
         if (shift) {
-            const double2 sx = zmul(shift[r], xv);
+            const C sx = cmul(to_c<C>(shift[r]), xv);
             out.x -= sx.x;
             out.y -= sx.y;
         }
@@ -169,24 +190,60 @@ __global__ void jm_sum_kernel(const double* __restrict__ partial, int nblk, doub
 }
 
 // y -= shift[r] x for vectors of n complex values per right-hand side
-__global__ void jm_shift_kernel(double2* __restrict__ y, const double2* __restrict__ x,
-                                const double2* __restrict__ shift, long long n) {
+template <typename C>
+__global__ void jm_shift_kernel(C* __restrict__ y, const C* __restrict__ x, const double2* __restrict__ shift,
+                                long long n) {
     const int r = blockIdx.y;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const long long o = (long long)r * n + e;
-    const double2 sx = zmul(shift[r], x[o]);
-    y[o] = make_double2(y[o].x - sx.x, y[o].y - sx.y);
+    const C sx = cmul(to_c<C>(shift[r]), x[o]);
+    y[o] = mk(y[o].x - sx.x, y[o].y - sx.y);
 }
 
-// (N - G) and K of the 2R stacked currents into the handle's JM scratch
-int jm_products(vie_handle* h, int R, const double2* x, double2** nx, double2** kx, cudaStream_t s) {
-    const size_t per = sizeof(double2) * (size_t)R * 24 * h->nv;
+// (N - G) and K of the 2R stacked currents into the handle's JM scratch, in FP64 or FP32
+template <typename C>
+int jm_products(vie_handle* h, int R, const C* x, C** nx, C** kx, cudaStream_t s) {
+    const int prec = sizeof(C) == 16 ? VIE_FP64 : VIE_FP32;
+    const size_t per = sizeof(C) * (size_t)R * 24 * h->nv;
     VIE_TRY(ws_reserve(h, h->jm_ws, 2 * per));
-    *nx = static_cast<double2*>(h->jm_ws.ptr);
+    *nx = static_cast<C*>(h->jm_ws.ptr);
     *kx = *nx + (size_t)R * 24 * h->nv;
-    VIE_TRY(matvec_device(h, 2 * R, x, *nx, VIE_FP64, VIE_OP_NSCAT, s));
-    VIE_TRY(kmatvec_device(h, 2 * R, x, *kx, s));
+    VIE_TRY(matvec_device(h, 2 * R, x, *nx, prec, VIE_OP_NSCAT, s));
+    VIE_TRY(matvec_device(h, 2 * R, x, *kx, prec, VIE_OP_K, s));
+    return VIE_OK;
+}
+
+template <typename C>
+int jm_matvec_full_t(vie_handle* h, int R, const C* x, C* y, int op, cudaStream_t s, const double2* shift) {
+    if (!h->mu64) VIE_TRY(jm_materials(h, nullptr, nullptr, s));
+    C *nx = nullptr, *kx = nullptr;
+    VIE_TRY(jm_products<C>(h, R, x, &nx, &kx, s));
+    const long long nv = (long long)h->nv;
+    const double dV = h->dx * h->dy * h->dz;
+    VIE_KLAUNCH("jm_combine", s,
+                jm_combine_kernel<C><<<grid1(24 * nv * R), 256, 0, s>>>(x, nx, kx, h->eps64, h->chi64, h->mu64,
+                                                                       h->chim64, y, nv, R, op, h->k0, dV, dV / 12.0,
+                                                                       op == VIE_OP_PA ? shift : nullptr));
+    VIE_CHECK_LAUNCH();
+    return VIE_OK;
+}
+
+template <typename C>
+int jm_matvec_support_t(vie_handle* h, int R, const C* x, C* y, int op, const Support& sp, void* tmp, cudaStream_t s,
+                        const double2* shift) {
+    if (!sp.rows) return jm_matvec_full_t<C>(h, R, x, y, op, s, shift);
+    const int prec = sizeof(C) == 16 ? VIE_FP64 : VIE_FP32;
+    C* tx = static_cast<C*>(tmp);
+    C* ty = tx + (size_t)R * 24 * h->nv;
+    VIE_TRY(support_scatter(h, 2 * R, x, tx, prec, sp, s));
+    VIE_TRY(jm_matvec_full_t<C>(h, R, tx, ty, op, s, nullptr));
+    VIE_TRY(support_gather(h, 2 * R, ty, y, prec, sp, s));
+    if (shift && op == VIE_OP_PA) {
+        const long long n = 24 * sp.ns;
+        VIE_KLAUNCH("jm_shift", s, jm_shift_kernel<C><<<dim3(grid1(n), R), 256, 0, s>>>(y, x, shift, n));
+        VIE_CHECK_LAUNCH();
+    }
     return VIE_OK;
 }
 
@@ -215,33 +272,19 @@ int jm_materials(vie_handle* h, const double* mr, const double* mi, cudaStream_t
 }
 
 int jm_matvec_full(vie_handle* h, int R, const double2* x, double2* y, int op, cudaStream_t s, const double2* shift) {
-    if (!h->mu64) VIE_TRY(jm_materials(h, nullptr, nullptr, s));
-    double2 *nx = nullptr, *kx = nullptr;
-    VIE_TRY(jm_products(h, R, x, &nx, &kx, s));
-    const long long nv = (long long)h->nv;
-    const double dV = h->dx * h->dy * h->dz;
-    VIE_KLAUNCH("jm_combine", s,
-                jm_combine_kernel<<<grid1(24 * nv * R), 256, 0, s>>>(x, nx, kx, h->eps64, h->chi64, h->mu64, h->chim64,
-                                                                    y, nv, R, op, h->k0, dV, dV / 12.0,
-                                                                    op == VIE_OP_PA ? shift : nullptr));
-    VIE_CHECK_LAUNCH();
-    return VIE_OK;
+    return jm_matvec_full_t<double2>(h, R, x, y, op, s, shift);
 }
 
-int jm_matvec_support(vie_handle* h, int R, const double2* x, double2* y, int op, const Support& sp, void* tmp,
-                      cudaStream_t s, const double2* shift) {
-    if (!sp.rows) return jm_matvec_full(h, R, x, y, op, s, shift);
-    double2* tx = static_cast<double2*>(tmp);
-    double2* ty = tx + (size_t)R * 24 * h->nv;
-    VIE_TRY(support_scatter(h, 2 * R, x, tx, VIE_FP64, sp, s));
-    VIE_TRY(jm_matvec_full(h, R, tx, ty, op, s, nullptr));
-    VIE_TRY(support_gather(h, 2 * R, ty, y, VIE_FP64, sp, s));
-    if (shift && op == VIE_OP_PA) {
-        const long long n = 24 * sp.ns;
-        VIE_KLAUNCH("jm_shift", s, jm_shift_kernel<<<dim3(grid1(n), R), 256, 0, s>>>(y, x, shift, n));
-        VIE_CHECK_LAUNCH();
-    }
-    return VIE_OK;
+int jm_matvec_support(vie_handle* h, int R, const void* x, void* y, int op, const Support& sp, void* tmp,
+                      cudaStream_t s, const double2* shift, int precision) {
+    if (precision == VIE_FP64)
+        return jm_matvec_support_t<double2>(h, R, static_cast<const double2*>(x), static_cast<double2*>(y), op, sp, tmp,
+                                            s, shift);
+    if (precision == VIE_FP32)
+        return jm_matvec_support_t<float2>(h, R, static_cast<const float2*>(x), static_cast<float2*>(y), op, sp, tmp,
+                                           s, shift);
+    set_error("the JM-VIE runs in FP64 or FP32");
+    return VIE_EINVAL;
 }
 
 int jm_rhs_device(vie_handle* h, int R, const double2* einc, const double2* hinc, double2* b, cudaStream_t s) {
@@ -258,7 +301,7 @@ int jm_fields_device(vie_handle* h, int R, const double2* x, const double2* einc
                      double2* hout, double* p_abs, double* P_abs_host, cudaStream_t s) {
     if (!h->mu64) VIE_TRY(jm_materials(h, nullptr, nullptr, s));
     double2 *nx = nullptr, *kx = nullptr;
-    VIE_TRY(jm_products(h, R, x, &nx, &kx, s));
+    VIE_TRY(jm_products<double2>(h, R, x, &nx, &kx, s));
     const long long nv = (long long)h->nv;
     const int nblk = (int)((nv + 255) / 256);
     VIE_TRY(ws_reserve(h, h->post_ws, sizeof(double) * (size_t)R * (nblk + 1)));

@@ -748,8 +748,8 @@ int enqueue_steps(Solver& S, VC* U, const double2* r64, const double* rn2, int p
         VC* w = U + (j + 1) * ustride;
         // only the active right-hand sides (the others' w is never read)
         if (S.jm)  // every right-hand side transformed (the others' w is never read)
-            VIE_TRY(jm_matvec_support(h, R, reinterpret_cast<const double2*>(uj), reinterpret_cast<double2*>(w),
-                                      VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift));
+            VIE_TRY(jm_matvec_support(h, R, uj, w, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift,
+                                      sizeof(VC) == sizeof(double2) ? VIE_FP64 : VIE_FP32));
         else
             VIE_TRY(matvec_support(h, R, uj, w, precision, VIE_OP_PA, S.sp, S.mv_tmp, st, S.gs.shift, nullptr,
                                    S.gs.nactive + 1, S.gs.nactive));
@@ -890,10 +890,11 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
         return VIE_EINVAL;
     }
     h->fcache_valid = 0;  // a new solve replaces the point kept for vie_fields
-    // the JM system (FP64 only): unknowns per voxel 24 = two currents of 12, copied to and from the
-    // support as 2R vectors of 12 components; no point is kept for vie_fields
-    if (jm && mode != VIE_SOLVE_FP64) {
-        set_error("the JM-VIE system is solved in FP64 only");
+    // the JM system (FP64, or FP32 inner solves with FP64 refinement): unknowns per voxel 24 = two
+    // currents of 12, copied to and from the support as 2R vectors of 12 components; no point is
+    // kept for vie_fields
+    if (jm && mode != VIE_SOLVE_FP64 && mode != VIE_SOLVE_FP32_REFINE) {
+        set_error("the JM-VIE system is solved in FP64 or FP32 with FP64 refinement");
         return VIE_EINVAL;
     }
     if (jm && !h->mu64) VIE_TRY(jm_materials(h, nullptr, nullptr, st));
@@ -975,7 +976,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     // first cycle is captured so that no later reservation moves the buffer under the graph
     VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, VIE_FP64)));
     dev_bytes_ptr("zpass_block_f32");  // looks the counters' address up outside any capture
-    if (mode == VIE_SOLVE_FP32_REFINE) VIE_TRY(matvec_tune(h, R, VIE_FP32, st));
+    if (mode == VIE_SOLVE_FP32_REFINE) VIE_TRY(matvec_tune(h, Rv, VIE_FP32, st));
     if (mode == VIE_SOLVE_BF16X3_REFINE) VIE_TRY(matvec_tune(h, R, VIE_BF16X3, st));
     S.R = R;
     S.m = m;
@@ -1133,7 +1134,10 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
                 float2* d32 = reinterpret_cast<float2*>(base + oU);
                 float2* ad32 = d32 + total;
                 VIE_KLAUNCH("refine_correction", st, to32_kernel<<<gt, 256, 0, st>>>(t64, d32, total));
-                VIE_TRY(matvec_support(h, R, d32, ad32, VIE_FP32, VIE_OP_PA, sp, S.mv_tmp, st));
+                if (jm)
+                    VIE_TRY(jm_matvec_support(h, R, d32, ad32, VIE_OP_PA, sp, S.mv_tmp, st, nullptr, VIE_FP32));
+                else
+                    VIE_TRY(matvec_support(h, R, d32, ad32, VIE_FP32, VIE_OP_PA, sp, S.mv_tmp, st));
                 ++mv32;
                 VIE_KLAUNCH("residual_sub", st, sub32_kernel<<<gt, 256, 0, st>>>(rs0, ad32, r64, total));
                 done_update = true;
@@ -1143,7 +1147,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
             // the matvec also leaves (N - G) x on the full grid, kept with x for vie_fields
             double2* cx = keep ? static_cast<double2*>(h->fcache_ws.ptr) : nullptr;
             if (jm)
-                VIE_TRY(jm_matvec_support(h, R, xs, t64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr));
+                VIE_TRY(jm_matvec_support(h, R, xs, t64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr, VIE_FP64));
             else
                 VIE_TRY(matvec_support(h, R, xs, t64, VIE_FP64, VIE_OP_PA, sp, S.mv_tmp, st, nullptr,
                                        keep ? cx + (size_t)R * nfull : nullptr));

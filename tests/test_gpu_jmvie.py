@@ -102,10 +102,12 @@ def test_jm_rhs_fields_and_power_parity(vie):
     assert np.allclose(P, Pr, rtol=1e-12, atol=0)
 
 
-def test_jm_solve_parity_dense(vie):
+@pytest.mark.parametrize("mode", ["fp64", "fp32_refine"])
+def test_jm_solve_parity_dense(vie, mode):
     """vie_jm_solve at a 1e-13 preconditioned residual against the oracle's dense LU solve of the same
     system (the unpreconditioned residual is within the condition number of P = diag(eps G, mu G),
-    about 1e3 here, of the preconditioned one)."""
+    about 1e3 here, of the preconditioned one).  The mixed mode reaches the same FP64 bound through
+    its refinement sweeps, its inner products all FP32."""
     g = Grid(5, 4, 3, 0.004, 0.005, 0.0045)
     eps, sig, mr, mi, prob = problem(g, 44)
     from oracle import green as OG
@@ -118,11 +120,14 @@ def test_jm_solve_parity_dense(vie):
     ref = np.stack([OS.direct_solve(A, b[r]) for r in range(3)])
     h = handle(vie, g, eps, sig, mr, mi)
     x = np.empty_like(b)
-    rc, info = vie.vie_jm_solve(h, b, x, tol=1e-13, restart=80, maxit=20, true_resid=True)
+    m = vie.VIE_SOLVE_FP64 if mode == "fp64" else vie.VIE_SOLVE_FP32_REFINE
+    rc, info = vie.vie_jm_solve(h, b, x, tol=1e-13, restart=80, maxit=20, mode=m, true_resid=True)
     h.close()
     assert rc == vie.VIE_OK and all(i["converged"] for i in info)
     assert all(i["true_resid"] < 1e-9 for i in info), [i["true_resid"] for i in info]
     assert rel(x, ref) <= 1e-9
+    if mode == "fp32_refine":
+        assert info[0]["fp32_matvecs"] > info[0]["fp64_matvecs"] and info[0]["refinements"] >= 2, info[0]
 
 
 def test_jm_nonmagnetic_equals_dielectric_solve(vie):
@@ -183,9 +188,11 @@ def test_jm_duality_on_the_gpu(vie):
     assert rel(xj[:, 1], xd) <= 1e-9
 
 
-def test_jm_solve_matches_oracle_gmres_on_a_sphere(vie):
+@pytest.mark.parametrize("mode", ["fp64", "fp32_refine"])
+def test_jm_solve_matches_oracle_gmres_on_a_sphere(vie, mode):
     """A magnetodielectric sphere (eps_r 50, sigma 0.5 S/m, mu_r 2 - 0.5 i) at 10^3 in a plane wave:
-    the GPU solution, fields and absorbed power against the oracle's GMRES at the same tolerance."""
+    the GPU solution (FP64, or FP32 inner solves with FP64 refinement), fields and absorbed power
+    against the oracle's GMRES at the same tolerance."""
     n = 10
     hgt = 0.2 / n
     g = Grid(n, n, n, hgt, hgt, hgt)
@@ -203,7 +210,9 @@ def test_jm_solve_matches_oracle_gmres_on_a_sphere(vie):
     assert info["converged"]
     h = handle(vie, g, eps, sig, mr, mi)
     x = np.empty_like(b)
-    rc, _ = vie.vie_jm_solve(h, np.ascontiguousarray(b), x, tol=1e-10, restart=100, maxit=10)
+    m = vie.VIE_SOLVE_FP64 if mode == "fp64" else vie.VIE_SOLVE_FP32_REFINE
+    rc, _ = vie.vie_jm_solve(h, np.ascontiguousarray(b), x, tol=1e-10, restart=100, maxit=10 if mode == "fp64" else 30,
+                             mode=m)
     assert rc == vie.VIE_OK
     ec = np.empty_like(e_t)
     hc = np.empty_like(h_t)
@@ -256,6 +265,10 @@ def test_jm_invalid_arguments(vie):
     x = np.zeros((1, 2, 12) + g.shape, dtype=np.complex128)
     with pytest.raises(vie.VieError):
         vie.vie_jm_matvec(h, x, x.copy(), vie.VIE_OP_NSCAT)
+    x[0, 0, 0, 1, 1, 1] = 1.0
+    with pytest.raises(vie.VieError) as e:  # the K block has no BF16x3 z pass
+        vie.vie_jm_solve(h, x, x.copy(), mode=vie.VIE_SOLVE_BF16X3_REFINE)
+    assert e.value.code == vie.VIE_EINVAL
     h.close()
     hp = vie.vie_setup((4, 4, 4, 0.005, 0.005, 0.005), F, eps, sig, vie.VIE_SETUP_PWC)
     with pytest.raises(vie.VieError):
