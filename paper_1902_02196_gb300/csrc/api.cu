@@ -10,8 +10,7 @@
 
 // green.cu: the 30 Toeplitz tensors of the K operator into device memory
 int green_k_toeplitz(vie_handle* h, double2* out, cudaStream_t s);
-// kmatvec.cu: y = K x (FP64) and the release of a handle's K spectrum
-int kmatvec_device(vie_handle* h, int R, const double2* x, double2* y, cudaStream_t s);
+// kmatvec.cu: the release of a handle's K spectra
 void kmatvec_release(vie_handle* h);
 // rhs_post.cu: tested incident magnetic field of dipoles; magnetic field, b1+ and W_m from x
 int rhs_dipoles_h_device(vie_handle* h, int R, const double* pos, const double* mom, double2* hinc, cudaStream_t s);
