@@ -934,6 +934,19 @@ def run_jm(args, local):
         x = np.empty_like(b)
         vie.vie_jm_matvec(h, b, x, vie.VIE_OP_PA)  # builds the K spectra
         row = dict(n=n)
+        # one JM product P^-1 A x of the right-hand side, device buffers, FP64 and FP32
+        for tag, prec, dt in (("jm_matvec_fp64_ms", vie.VIE_FP64, torch.complex128),
+                              ("jm_matvec_fp32_ms", vie.VIE_FP32, torch.complex64)):
+            xd = torch.from_numpy(b).to(device=f"cuda:{local}", dtype=dt)
+            yd = torch.empty_like(xd)
+            ts = []
+            for _ in range(4):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                vie.vie_jm_matvec(h, xd, yd, vie.VIE_OP_PA, precision=prec)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            row[tag] = 1e3 * min(ts[1:])
         for tag, mode in (("fp64", vie.VIE_SOLVE_FP64), ("fp32_refine", vie.VIE_SOLVE_FP32_REFINE)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()

@@ -373,9 +373,12 @@ int vie_set_permeability(vie_handle* h, const double* mu_real, const double* mu_
 
 /*
  * vie_jm_matvec -- y = A x (op VIE_OP_A) or y = P^-1 A x (op VIE_OP_PA) of the JM system above
- * for nrhs vectors.  x and y must not overlap.
+ * for nrhs vectors.  precision VIE_FP64 (x, y double pairs) or VIE_FP32 (float pairs: both
+ * products and the combination in FP32, the operator of vie_jm_solve's inner GMRES in
+ * VIE_SOLVE_FP32_REFINE).  x and y must not overlap.  Errors: VIE_EINVAL (NULL, PWC handle,
+ * another precision or operator), VIE_ENOMEM.
  */
-int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int op, void* stream);
+int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream);
 
 /*
  * vie_jm_rhs -- right-hand sides b = (c_e chi_e e_inc, i k0 chi_m h_inc) (Eq. 14, second row
@@ -386,14 +389,15 @@ int vie_jm_rhs(vie_handle* h, int nrhs, const void* e_inc, const void* h_inc, vo
 
 /*
  * vie_jm_solve -- restarted GMRES(restart) on P^-1 A x = P^-1 b of the JM system with the
- * batched device Arnoldi steps of vie_solve (the restart cycles launched directly, not as CUDA
- * graphs), stopping when ||P^-1 (b - A x)|| / ||P^-1 b|| <= tol.  The solver's vectors cover the
+ * batched device Arnoldi steps of vie_solve (chunks of steps replayed as CUDA graphs, as there),
+ * stopping when ||P^-1 (b - A x)|| / ||P^-1 b|| <= tol.  The solver's vectors cover the
  * voxels where chi_e, chi_m, b or the guess is non-zero (rows of the grid as for vie_solve).
  *   b, x  : [nrhs][2][12][nz][ny][nx] C128; x is the initial guess when (flags & 1)
  *   mode  : VIE_SOLVE_FP64, or VIE_SOLVE_FP32_REFINE (FP32 inner GMRES, both products of the
  *           operator in FP32, inside FP64 iterative refinement as vie_solve's mode of that name);
  *           VIE_SOLVE_BF16X3_REFINE is refused (the K block has no BF16x3 z pass)
- *   flags : bit 0 = use x as initial guess; bit 1 = also compute true_resid (||b - A x|| / ||b||)
+ *   flags : bit 0 = use x as initial guess; bit 1 = also compute true_resid (||b - A x|| / ||b||);
+ *           bit 3 = launch the steps directly instead of replaying CUDA graphs
  *   info  : vie_solve_info[nrhs] or NULL
  * Returns VIE_NOT_CONVERGED (x = best iterate) when a right-hand side misses tol; VIE_EINVAL for
  * an unknown mode or flag.

@@ -109,7 +109,7 @@ def _lib():
     lib.vie_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(S)]
     lib.vie_set_permeability.argtypes = [P, P, P]
     lib.vie_green_tucker.argtypes = [P, D, I, P, P, ctypes.POINTER(S)]
-    lib.vie_jm_matvec.argtypes = [P, I, P, P, I, P]
+    lib.vie_jm_matvec.argtypes = [P, I, P, P, I, I, P]
     lib.vie_jm_rhs.argtypes = [P, I, P, P, P, P]
     lib.vie_jm_solve.argtypes = [P, I, P, P, D, I, I, I, I, ctypes.POINTER(vie_solve_info), P]
     lib.vie_jm_fields.argtypes = [P, I, P, P, P, P, P, P, ctypes.POINTER(D), P]
@@ -308,10 +308,11 @@ def vie_set_permeability(h, mu_real, mu_imag):
     return _check(_lib().vie_set_permeability(h.ptr, _ptr(mu_real), _ptr(mu_imag)), "vie_set_permeability")
 
 
-def vie_jm_matvec(h, x, y, op=VIE_OP_A, stream=None):
-    """y = A x or P^-1 A x of the full JM-VIE system, x, y [R][2][12][nz][ny][nx] complex128."""
-    return _check(_lib().vie_jm_matvec(h.ptr, _nrhs_jm(x, h), _ptr(x), _ptr(y), int(op), _stream(stream)),
-                  "vie_jm_matvec")
+def vie_jm_matvec(h, x, y, op=VIE_OP_A, precision=VIE_FP64, stream=None):
+    """y = A x or P^-1 A x of the full JM-VIE system, x, y [R][2][12][nz][ny][nx] complex128
+    (VIE_FP64) or complex64 (VIE_FP32)."""
+    return _check(_lib().vie_jm_matvec(h.ptr, _nrhs_jm(x, h), _ptr(x), _ptr(y), int(precision), int(op),
+                                       _stream(stream)), "vie_jm_matvec")
 
 
 def vie_jm_rhs(h, e_inc, h_inc, b, stream=None):
@@ -321,12 +322,12 @@ def vie_jm_rhs(h, e_inc, h_inc, b, stream=None):
 
 
 def vie_jm_solve(h, b, x, tol=1e-6, restart=50, maxit=200, mode=VIE_SOLVE_FP64, guess=False, true_resid=False,
-                 stream=None):
+                 graph=True, stream=None):
     """GMRES on the JM system (FP64, or FP32 inner solves with FP64 refinement); returns
-    (rc, [info dict per right-hand side])."""
+    (rc, [info dict per right-hand side]).  graph=False: direct launches (flags bit 3)."""
     n = _nrhs_jm(b, h)
     info = (vie_solve_info * n)()
-    flags = (1 if guess else 0) | (2 if true_resid else 0)
+    flags = (1 if guess else 0) | (2 if true_resid else 0) | (0 if graph else 8)
     rc = _check(_lib().vie_jm_solve(h.ptr, n, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit), int(mode),
                                     flags, info, _stream(stream)), "vie_jm_solve")
     return rc, [i.as_dict() for i in info]

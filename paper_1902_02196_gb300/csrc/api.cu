@@ -571,21 +571,22 @@ int vie_set_permeability(vie_handle* h, const double* mu_real, const double* mu_
     return rc;
 }
 
-int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int op, void* stream) {
+int vie_jm_matvec(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, void* stream) {
     g_last_error.clear();
     REQUIRE(h && x && y, "NULL argument");
     REQUIRE(h->nc == 12, "the JM-VIE is built for the PWL system only");
     REQUIRE(nrhs >= 1, "nrhs must be >= 1");
+    REQUIRE(precision == VIE_FP64 || precision == VIE_FP32, "precision must be VIE_FP64 or VIE_FP32");
     REQUIRE(op == VIE_OP_A || op == VIE_OP_PA, "unknown operator (VIE_OP_A or VIE_OP_PA)");
     REQUIRE(x != y, "x and y must not overlap");
-    const size_t bytes = (size_t)nrhs * 24 * h->nv * sizeof(double2);
+    const size_t bytes = (size_t)nrhs * 24 * h->nv * (precision == VIE_FP64 ? sizeof(double2) : sizeof(float2));
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};
     sg.add(x, bytes, false);
     sg.add(y, bytes, true);
     std::vector<void*> d;
     VIE_TRY(sg.bind(d));
-    VIE_TRY(jm_matvec_full(h, nrhs, static_cast<const double2*>(d[0]), static_cast<double2*>(d[1]), op, st));
+    VIE_TRY(jm_matvec_support(h, nrhs, d[0], d[1], op, Support{}, nullptr, st, nullptr, precision));
     return sg.finish(d);
 }
 
@@ -617,7 +618,7 @@ int vie_jm_solve(vie_handle* h, int nrhs, const void* b, void* x, double tol, in
     REQUIRE(restart >= 1 && restart <= 128, "restart must be in [1, 128]");
     REQUIRE(maxit >= 1, "maxit must be >= 1");
     REQUIRE(mode == VIE_SOLVE_FP64 || mode == VIE_SOLVE_FP32_REFINE, "mode must be VIE_SOLVE_FP64 or VIE_SOLVE_FP32_REFINE");
-    REQUIRE((flags & ~3) == 0, "unknown flags");
+    REQUIRE((flags & ~11) == 0, "unknown flags");
     const size_t bytes = (size_t)nrhs * 24 * h->nv * sizeof(double2);
     cudaStream_t st = pick(h, stream);
     Stager sg{h, st};

@@ -970,11 +970,16 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     S.st = st;
     // CUDA graphs for the cycles unless flags bit 3 asks for direct launches; the legacy and
     // per-thread default streams cannot be captured
-    S.use_graph = !(flags & 8) && !jm && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    S.use_graph = !(flags & 8) && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     S.jm = jm;
-    // the largest spectrum scratch any matvec of this solve takes (FP64), reserved before the
-    // first cycle is captured so that no later reservation moves the buffer under the graph
-    VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, R, VIE_FP64)));
+    // the largest spectrum scratch any matvec of this solve takes (FP64; the JM products transform
+    // 2R vectors), reserved before the first cycle is captured so that no later reservation moves
+    // the buffer under the graph; the JM operator's product scratch and K spectra likewise
+    VIE_TRY(ws_reserve(h, h->fft_ws, matvec_workspace_bytes(h, Rv, VIE_FP64)));
+    if (jm) {
+        VIE_TRY(ws_reserve(h, h->jm_ws, 2 * sizeof(double2) * (size_t)R * 24 * h->nv));
+        VIE_TRY(k_octants(h, st));
+    }
     dev_bytes_ptr("zpass_block_f32");  // looks the counters' address up outside any capture
     if (mode == VIE_SOLVE_FP32_REFINE) VIE_TRY(matvec_tune(h, Rv, VIE_FP32, st));
     if (mode == VIE_SOLVE_BF16X3_REFINE) VIE_TRY(matvec_tune(h, R, VIE_BF16X3, st));

@@ -55,10 +55,11 @@ def ops(g):
     return O.NOperator(g, k0), O.KOperator(g, k0)
 
 
-@pytest.mark.parametrize("shape,nrhs", [((7, 5, 4), 2), ((9, 6, 11), 1)])
+@pytest.mark.parametrize("shape,nrhs", [((7, 5, 4), 2), ((9, 6, 11), 1), ((20, 18, 9), 3)])
 def test_jm_matvec_parity(vie, shape, nrhs):
     """A x and P^-1 A x of the JM system on ragged grids, random materials (with air and
-    non-magnetic voxels) and random currents."""
+    non-magnetic voxels) and random currents: FP64 within 1e-12 and FP32 (the operator of the
+    mixed solve's inner GMRES) within 1e-5 of the oracle, on the fused and the line xy paths."""
     g = Grid(*shape, 0.004, 0.005, 0.0045)
     eps, sig, mr, mi, prob = problem(g, sum(shape))
     Nop, Kop = ops(g)
@@ -74,6 +75,13 @@ def test_jm_matvec_parity(vie, shape, nrhs):
         yh = np.empty_like(x)  # host buffers take the same path
         vie.vie_jm_matvec(h, x, yh, op)
         assert np.array_equal(yh, yd.cpu().numpy())
+        x32 = np.ascontiguousarray(x.astype(np.complex64))
+        y32 = np.empty_like(x32)
+        vie.vie_jm_matvec(h, x32, y32, op, precision=vie.VIE_FP32)
+        assert rel(y32, ref) <= 1e-5
+    with pytest.raises(vie.VieError) as e:
+        vie.vie_jm_matvec(h, x.astype(np.complex64), np.empty(x.shape, np.complex64), precision=vie.VIE_BF16X3)
+    assert e.value.code == vie.VIE_EINVAL
     h.close()
 
 
@@ -128,6 +136,28 @@ def test_jm_solve_parity_dense(vie, mode):
     assert rel(x, ref) <= 1e-9
     if mode == "fp32_refine":
         assert info[0]["fp32_matvecs"] > info[0]["fp64_matvecs"] and info[0]["refinements"] >= 2, info[0]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32_refine"])
+def test_jm_graph_replay_matches_direct_launches(vie, mode):
+    """The JM solve's Arnoldi chunks replayed as CUDA graphs give the same bits and counts as the
+    same steps launched kernel by kernel (flags bit 3)."""
+    g = Grid(9, 8, 7, 0.005, 0.005, 0.005)
+    eps, sig, mr, mi, _ = problem(g, 61)
+    h = handle(vie, g, eps, sig, mr, mi)
+    rng = np.random.Generator(np.random.PCG64(62))
+    shp = (2, 2, 12) + g.shape
+    b = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    m = vie.VIE_SOLVE_FP64 if mode == "fp64" else vie.VIE_SOLVE_FP32_REFINE
+    out = []
+    for graph in (True, False):
+        x = np.empty_like(b)
+        rc, info = vie.vie_jm_solve(h, b, x, tol=1e-10, restart=16, maxit=60, mode=m, graph=graph)
+        assert rc == vie.VIE_OK, info
+        out.append((x, info))
+    h.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
 
 
 def test_jm_nonmagnetic_equals_dielectric_solve(vie):
