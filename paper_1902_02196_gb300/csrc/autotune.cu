@@ -11,7 +11,7 @@
 #include "autotune.h"
 
 namespace {
-const char* const kKinds[] = {"zpass_block_f32", "zpass_block_bf16x3"};
+const char* const kKinds[] = {"zpass_block_f32", "zpass_block_bf16x3", "zpass_block_k_f32"};
 
 std::mutex g_mu;
 std::map<std::array<int, 6>, int> g_pick;

@@ -83,6 +83,26 @@ constexpr KBlockTable make_kblock_table() {
 __device__ constexpr KBlockTable kKBlock = make_kblock_table();
 static_assert(make_kblock_table().start[30] == 96, "the K block has 96 non-zero entries from 30 tensors");
 
+// The 96 non-zero K entries ordered by input component b, then output a (as kBlockB)
+struct KBlockTableB {
+    BlockEntryT e[96];
+};
+constexpr KBlockTableB make_kblock_table_b() {
+    KBlockTableB T{};
+    int n = 0;
+    for (int b = 0; b < 12; ++b)
+        for (int a = 0; a < 12; ++a)
+            if (kblock::tensor(a, b) >= 0) {
+                T.e[n].a = (signed char)a;
+                T.e[n].b = (signed char)b;
+                T.e[n].t = (signed char)kblock::tensor(a, b);
+                T.e[n].s = (signed char)kblock::sign(a, b);
+                ++n;
+            }
+    return T;
+}
+__device__ constexpr KBlockTableB kKBlockB = make_kblock_table_b();
+
 // ---------------------------------------------------------------------------
 // cp.async (shared <- global) helpers
 // ---------------------------------------------------------------------------

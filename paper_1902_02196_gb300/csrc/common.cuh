@@ -123,6 +123,8 @@ struct vie_handle {
     // 1/(Lx Ly Lz), FP64 and FP32 (kmatvec.cu, built on the first K product)
     double2* kgreen64;
     float2* kgreen32;
+    // FP32 copy [Oy][Ox][Oz][30] for the fused FP32 z pass with the K block (zpass_f32.cu)
+    float2* kgreen32t;
     // bf16 split of green32t in the same layout, for the BF16x3 z pass: per tensor (hi, lo),
     // each a bf16 (re, im) pair with hi = bf16(v), lo = bf16(v - hi)
     uint2* greenbf;
@@ -276,7 +278,8 @@ int green_split_bf16(vie_handle* h);            // zpass_bf16.cu: greenbf from g
 int twiddle_setup(vie_handle* h);               // matvec.cu
 int matvec_device(vie_handle* h, int nrhs, const void* x, void* y, int precision, int op, cudaStream_t s);
 size_t matvec_workspace_bytes(const vie_handle* h, int nrhs, int precision);
-int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s);  // z-pass autotuner, outside capture
+// z-pass autotuner, outside capture (op: the N block, or VIE_OP_K for the K block)
+int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s, int op = VIE_OP_NSCAT);
 
 // Support of a solve: per (z, y) row of the grid the voxel interval [x0, x1) whose
 // unknowns are kept and the offset of voxel (x0, y, z) within a component block of ns

@@ -26,7 +26,6 @@
 
 int zpass_bf16_fused(const vie_handle* h, const ZFArgs& z, cudaStream_t s);  // zpass_bf16.cu
 int zpass_bf16_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s);   // zpass_bf16.cu
-int zpass_f32_tune(const vie_handle* h, const ZFArgs& z, cudaStream_t s);    // zpass_f32.cu
 
 // y[3] = B(k) x[3] of the PWC system (the l = 1 sub-block): entry (p, q) is tensor 10 pq + 0
 // (scalar pair (1, 1)) with sign +1
@@ -660,10 +659,21 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
-        if (op == VIE_OP_K) {  // the generic z pass with the K block on the 30 K tensors
+        if (op == VIE_OP_K) {  // the K block on the 30 K tensors: fused FP32 z pass, else the generic one
             if (bf16 || nc != 12 || !h->kgreen64) {
                 set_error("the K operator runs in FP64 or FP32 on the PWL system");
                 return VIE_EINVAL;
+            }
+            if (sizeof(T) == 4 && zfused_ok(h) && h->kgreen32t) {
+                ZFArgs z{};
+                z.w = reinterpret_cast<float2*>(W2);
+                z.green_t = h->kgreen32t;
+                z.colkx = h->colkx32;
+                z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+                z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+                z.ay = ay, z.by = by;
+                z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+                return zpass_f32_fused_k(h, z, s);
             }
             ZArgs z{};
             z.w = W2;
@@ -793,19 +803,25 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     return VIE_OK;
 }
 
-// Runs the z-pass autotuner for nrhs right-hand sides of this precision now (outside any stream
-// capture), so that a CUDA graph captured later launches the tuned tile width.
-int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s) {
+// Runs the z-pass autotuner for nrhs right-hand sides of this precision and operator (the N
+// block, or the K block with op VIE_OP_K) now, outside any stream capture, so that a CUDA graph
+// captured later launches the tuned tile width.
+int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s, int op) {
     if (precision == VIE_FP64 || !zfused_ok(h) || h->nc != 12) return VIE_OK;
+    if (op == VIE_OP_K) {
+        if (precision != VIE_FP32) return VIE_OK;
+        VIE_TRY(k_octants(h, s));
+    }
     ZFArgs z{};
     z.w = nullptr;
-    z.green_t = h->green32t;
+    z.green_t = op == VIE_OP_K ? h->kgreen32t : h->green32t;
     z.colkx = h->colkx32;
     z.R = nrhs, z.nz = h->nz, z.Lx = h->L[0], z.Ly = h->L[1];
     z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
     const int ay = xy_ok(h) ? fft2::split_a(h->L[1]) : 1, by = xy_ok(h) ? h->L[1] / fft2::split_a(h->L[1]) : h->L[1];
     z.ay = ay, z.by = by;
     z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+    if (op == VIE_OP_K) return zpass_f32_tune_k(h, z, s);
     return precision == VIE_BF16X3 ? zpass_bf16_tune(h, z, s) : zpass_f32_tune(h, z, s);
 }
 

@@ -982,6 +982,7 @@ int solve_device(vie_handle* h, int R, const double2* b, double2* x, double tol,
     }
     dev_bytes_ptr("zpass_block_f32");  // looks the counters' address up outside any capture
     if (mode == VIE_SOLVE_FP32_REFINE) VIE_TRY(matvec_tune(h, Rv, VIE_FP32, st));
+    if (mode == VIE_SOLVE_FP32_REFINE && jm) VIE_TRY(matvec_tune(h, Rv, VIE_FP32, st, VIE_OP_K));
     if (mode == VIE_SOLVE_BF16X3_REFINE) VIE_TRY(matvec_tune(h, R, VIE_BF16X3, st));
     S.R = R;
     S.m = m;
