@@ -146,7 +146,8 @@ void vie_destroy(vie_handle* h);
  *   precision : VIE_FP64, VIE_FP32 or VIE_BF16X3 (VIE_OP_K: VIE_FP64 or VIE_FP32)
  *   op        : VIE_OP_A, VIE_OP_PA, VIE_OP_NSCAT or VIE_OP_K.  VIE_OP_K transforms the 30
  *               tensors of vie_green_toeplitz_k once per handle into octant spectra (30 Ox Oy Oz
- *               values in FP64 and FP32, kept until vie_destroy and counted by vie_info) and runs
+ *               values in FP64 and FP32, each in two layouts: 48 bytes per value in all, kept
+ *               until vie_destroy and counted by vie_info) and runs
  *               the same transforms as the N operator with the K block (96 signed entries) at
  *               every frequency point, the other octants from the K parities.
  */

@@ -123,8 +123,9 @@ struct vie_handle {
     // 1/(Lx Ly Lz), FP64 and FP32 (kmatvec.cu, built on the first K product)
     double2* kgreen64;
     float2* kgreen32;
-    // FP32 copy [Oy][Ox][Oz][30] for the fused FP32 z pass with the K block (zpass_f32.cu)
+    // copies [Oy][Ox][Oz][30] for the fused z passes with the K block (zpass_f32.cu, zpass_f64.cu)
     float2* kgreen32t;
+    double2* kgreen64t;
     // bf16 split of green32t in the same layout, for the BF16x3 z pass: per tensor (hi, lo),
     // each a bf16 (re, im) pair with hi = bf16(v), lo = bf16(v - hi)
     uint2* greenbf;

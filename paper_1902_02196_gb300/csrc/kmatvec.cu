@@ -6,8 +6,8 @@
 // The 30 Toeplitz tensors P_t (green.cu, assemble_k_kernel) are embedded into full 2N
 // circulants, the entries at negative offsets taken from the reflection parities of the block
 // table (kblock.h), transformed, and their octant k_i in [0, L_i/2] kept, scaled by
-// 1/(Lx Ly Lz), as [30][Oz][Oy][Ox] in FP64 and FP32, and in FP32 once more as [Oy][Ox][Oz][30]
-// (the 30 values of a point side by side, for the fused FP32 z pass).  The other octants follow
+// 1/(Lx Ly Lz), as [30][Oz][Oy][Ox] in FP64 and FP32, and once more in both as [Oy][Ox][Oz][30]
+// (the 30 values of a point side by side, for the fused z passes).  The other octants follow
 // in the z pass from the same parities: K(R_i k) = -S_i K(k) S_i.  Built on the first K product
 // of a handle and released with it.
 #include <algorithm>
@@ -57,7 +57,8 @@ __global__ void embed_k_kernel(const double2* __restrict__ P, int nx, int ny, in
 
 // octant k_i in [0, L_i/2] of the transformed circulants of tensors t0 .. t0 + nt - 1, scaled
 __global__ void k_octant_kernel(const double2* __restrict__ C, int Lx, int Ly, int Lz, int t0, int nt, double scale,
-                                double2* __restrict__ g64, float2* __restrict__ g32, float2* __restrict__ g32t) {
+                                double2* __restrict__ g64, float2* __restrict__ g32, float2* __restrict__ g32t,
+                                double2* __restrict__ g64t) {
     const int Ox = Lx / 2 + 1, Oy = Ly / 2 + 1, Oz = Lz / 2 + 1;
     const long long ovol = (long long)Ox * Oy * Oz;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,7 +72,9 @@ __global__ void k_octant_kernel(const double2* __restrict__ C, int Lx, int Ly, i
     const long long dst = (long long)(t0 + tl) * ovol + o;
     g64[dst] = v;
     g32[dst] = make_float2((float)v.x, (float)v.y);
-    g32t[(((long long)ky * Ox + kx) * Oz + kz) * 30 + t0 + tl] = make_float2((float)v.x, (float)v.y);
+    const long long dt = (((long long)ky * Ox + kx) * Oz + kz) * 30 + t0 + tl;
+    g32t[dt] = make_float2((float)v.x, (float)v.y);
+    g64t[dt] = v;
 }
 
 unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
@@ -86,7 +89,7 @@ int k_octants(vie_handle* h, cudaStream_t s) {
     const long long vol = (long long)Lx * Ly * Lz, nd = (long long)h->nv;
     const long long ovol = (long long)h->O[0] * h->O[1] * h->O[2];
     const int chunk = (int)std::max<long long>(1, std::min<long long>(30, (4LL << 30) / (vol * (long long)sizeof(double2))));
-    double2 *P = nullptr, *C = nullptr, *g64 = nullptr;
+    double2 *P = nullptr, *C = nullptr, *g64 = nullptr, *g64t = nullptr;
     float2 *g32 = nullptr, *g32t = nullptr;
     auto fail = [&](int code, const char* msg) {
         cudaGetLastError();
@@ -95,6 +98,7 @@ int k_octants(vie_handle* h, cudaStream_t s) {
         cudaFree(g64);
         cudaFree(g32);
         cudaFree(g32t);
+        cudaFree(g64t);
         set_error(msg);
         return code;
     };
@@ -102,7 +106,8 @@ int k_octants(vie_handle* h, cudaStream_t s) {
         cudaMalloc(&C, sizeof(double2) * vol * chunk) != cudaSuccess ||
         cudaMalloc(&g64, sizeof(double2) * 30 * ovol) != cudaSuccess ||
         cudaMalloc(&g32, sizeof(float2) * 30 * ovol) != cudaSuccess ||
-        cudaMalloc(&g32t, sizeof(float2) * 30 * ovol) != cudaSuccess)
+        cudaMalloc(&g32t, sizeof(float2) * 30 * ovol) != cudaSuccess ||
+        cudaMalloc(&g64t, sizeof(double2) * 30 * ovol) != cudaSuccess)
         return fail(VIE_ENOMEM, "K spectrum allocation failed");
     int rc = green_k_toeplitz(h, P, s);
     for (int t0 = 0; rc == VIE_OK && t0 < 30; t0 += chunk) {
@@ -114,7 +119,7 @@ int k_octants(vie_handle* h, cudaStream_t s) {
         if (rc < 0) break;
         VIE_KLAUNCH("k_octant", s,
                     k_octant_kernel<<<blocks(ovol * nt), 256, 0, s>>>(C, Lx, Ly, Lz, t0, nt, 1.0 / (double)vol, g64,
-                                                                      g32, g32t));
+                                                                      g32, g32t, g64t));
         if (cudaGetLastError() != cudaSuccess) return fail(VIE_EDEVICE, "K octant launch failed");
     }
     if (rc == VIE_OK && cudaStreamSynchronize(s) != cudaSuccess) return fail(VIE_EDEVICE, "K spectrum sync failed");
@@ -124,6 +129,7 @@ int k_octants(vie_handle* h, cudaStream_t s) {
         cudaFree(g64);
         cudaFree(g32);
         cudaFree(g32t);
+        cudaFree(g64t);
         return rc;
     }
     cudaFree(P);
@@ -131,7 +137,8 @@ int k_octants(vie_handle* h, cudaStream_t s) {
     h->kgreen64 = g64;
     h->kgreen32 = g32;
     h->kgreen32t = g32t;
-    h->bytes_held += (sizeof(double2) + 2 * sizeof(float2)) * 30 * (size_t)ovol;  // until kmatvec_release
+    h->kgreen64t = g64t;
+    h->bytes_held += 2 * (sizeof(double2) + sizeof(float2)) * 30 * (size_t)ovol;  // until kmatvec_release
     return VIE_OK;
 }
 
@@ -146,8 +153,10 @@ void kmatvec_release(vie_handle* h) {
     cudaFree(h->kgreen64);
     cudaFree(h->kgreen32);
     cudaFree(h->kgreen32t);
+    cudaFree(h->kgreen64t);
     h->kgreen64 = nullptr;
     h->kgreen32 = nullptr;
     h->kgreen32t = nullptr;
-    h->bytes_held -= (sizeof(double2) + 2 * sizeof(float2)) * 30 * (size_t)h->O[0] * h->O[1] * h->O[2];
+    h->kgreen64t = nullptr;
+    h->bytes_held -= 2 * (sizeof(double2) + sizeof(float2)) * 30 * (size_t)h->O[0] * h->O[1] * h->O[2];
 }

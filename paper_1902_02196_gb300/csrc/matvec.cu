@@ -659,7 +659,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     // z pass on a spectrum whose row py holds ky = py / by + ay (py % by) and whose stored
     // columns follow colkx32: the fused kernels (FP32, FP64) where they apply, else the line z pass
     auto zpass = [&](int ay, int by) -> int {
-        if (op == VIE_OP_K) {  // the K block on the 30 K tensors: fused FP32 z pass, else the generic one
+        if (op == VIE_OP_K) {  // the K block on the 30 K tensors: the fused z passes, else the generic one
             if (bf16 || nc != 12 || !h->kgreen64) {
                 set_error("the K operator runs in FP64 or FP32 on the PWL system");
                 return VIE_EINVAL;
@@ -674,6 +674,17 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
                 z.ay = ay, z.by = by;
                 z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
                 return zpass_f32_fused_k(h, z, s);
+            }
+            if (sizeof(T) == 8 && zfused_ok(h) && h->kgreen64t) {
+                ZDArgs z{};
+                z.w = reinterpret_cast<double2*>(W2);
+                z.green_t = h->kgreen64t;
+                z.colkx = h->colkx32;
+                z.R = Rs, z.nz = nz, z.Lx = Lx, z.Ly = Ly;
+                z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
+                z.ay = ay, z.by = by;
+                z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
+                return zpass_f64_fused_k(h, z, s);
             }
             ZArgs z{};
             z.w = W2;

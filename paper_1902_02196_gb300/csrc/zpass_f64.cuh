@@ -5,7 +5,7 @@
 
 struct ZDArgs {
     double2* w;                // spectrum [R*12][Nz][Ly][Lx], in place
-    const double2* green_t;    // [Oy][Ox][Oz][60]
+    const double2* green_t;    // [Oy][Ox][Oz][60] (N), [Oy][Ox][Oz][30] (K)
     const int* colkx;          // [Lx] kx of each stored column (mirror pairs)
     int R, nz, Lx, Ly, Ox, Oy, Oz;
     int ay, by;                // row py holds ky = py / by + ay * (py % by)
@@ -16,3 +16,5 @@ struct ZDArgs {
 
 // Launches the FP64 z pass (Lz in 8..512, Lx >= 4).
 int zpass_f64_fused(const vie_handle* h, const ZDArgs& z, cudaStream_t s);
+// The same z pass with the K block (VIE_OP_K) on the K octant [Oy][Ox][Oz][30].
+int zpass_f64_fused_k(const vie_handle* h, const ZDArgs& z, cudaStream_t s);
