@@ -1,7 +1,8 @@
 // K operator (K u = curl S u, Eq. 8): its Green tensors in octant storage for the matvec, so
 // that y = K x (the tested scattered magnetic field h~ = K x, Eq. 13: h_sca = K j) runs the
-// same transforms as the N operator (Section IV-A) with the K block in the z pass, in FP64
-// (matvec.cu, zpass_kernel with KOP) or FP32 (zpass_f32.cu, zfused_kernel with KOP).
+// same transforms as the N operator (Section IV-A) with the K block in the z pass, in FP64 or
+// FP32: the fused z passes with KOP (zpass_f32.cu, zpass_f64.cu), or the generic one
+// (matvec.cu, zpass_kernel with KOP) for FFT lengths along z outside 8..512.
 //
 // The 30 Toeplitz tensors P_t (green.cu, assemble_k_kernel) are embedded into full 2N
 // circulants, the entries at negative offsets taken from the reflection parities of the block
