@@ -21,6 +21,7 @@
 #include "block.cuh"
 #include "fft.cuh"
 #include "fft2.cuh"
+#include "line2.cuh"
 #include "zpass_f32.cuh"
 #include "zpass_f64.cuh"
 
@@ -766,6 +767,13 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
         set_error("internal: the line-transform matvec takes full-grid vectors only");
         return VIE_EINVAL;
     }
+    // The line transforms: the two-pass kernels (line2.cu) for lengths 8..512, else the radix-4
+    // line kernels; the inverse x transform with the voxel-wise terms always on the radix-4 one.
+    // Both store the x spectrum in the column order of colkx32; the y spectrum's rows are in
+    // fft2's transposed order after the two-pass kernel (row py holds ky = py / B + A (py % B),
+    // A B = Ly) and in natural order after the radix-4 one.
+    const bool fp64 = sizeof(T) == 8;
+    const bool x2 = line2_ok(Lx), y2 = line2_ok(Ly);
     // x-pass: lines along x, contiguous; frequencies stored in the column order of colkx32
     LineArgs a{};
     a.in = x;
@@ -776,7 +784,10 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.oa = 0, a.ol = 1, a.ob = Lx;
     a.n_in = nx, a.n_out = Lx, a.dir = -1;
     a.pout = h->colpos32;
-    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
+    if (x2)
+        VIE_TRY(line2_forward(fp64 ? "fft_x_f64" : "fft_x_f32", h, Lx, fp64, a, h->colkx32, s));
+    else
+        VIE_TRY((launch_line<T, false>(fp64 ? "fft_x_f64" : "fft_x_f32", h, Lx, a, noepi, s)));
     // y-pass
     a = LineArgs{};
     a.in = W1;
@@ -786,10 +797,16 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.ia = (long long)ny * Lx, a.il = Lx, a.ib = 1;
     a.oa = (long long)Ly * Lx, a.ol = Lx, a.ob = 1;
     a.n_in = ny, a.n_out = Ly, a.dir = -1;
-    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
-    // z-pass with block product (rows in natural ky order: by = Ly, ay = 1 for the fused
-    // kernels' formula, by = 0 for the line z pass)
-    VIE_TRY(zfused_ok(h) ? zpass(1, Ly) : zpass(0, 0));
+    if (y2)
+        VIE_TRY(line2_forward(fp64 ? "fft_y_f64" : "fft_y_f32", h, Ly, fp64, a, nullptr, s));
+    else
+        VIE_TRY((launch_line<T, false>(fp64 ? "fft_y_f64" : "fft_y_f32", h, Ly, a, noepi, s)));
+    // z-pass with block product: row order (ay, by) of the y spectrum, the natural order as
+    // (1, Ly) for the fused kernels' formula and (0, 0) for the line z pass
+    if (y2)
+        VIE_TRY(zpass(fft2::split_a(Ly), Ly / fft2::split_a(Ly)));
+    else
+        VIE_TRY(zfused_ok(h) ? zpass(1, Ly) : zpass(0, 0));
     // y-inverse
     a = LineArgs{};
     a.in = W2;
@@ -799,7 +816,10 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.ia = (long long)Ly * Lx, a.il = Lx, a.ib = 1;
     a.oa = (long long)ny * Lx, a.ol = Lx, a.ob = 1;
     a.n_in = Ly, a.n_out = ny, a.dir = +1;
-    VIE_TRY((launch_line<T, false>(sizeof(T) == 8 ? "ifft_y_f64" : "ifft_y_f32", h, Ly, a, noepi, s)));
+    if (y2)
+        VIE_TRY(line2_inverse(fp64 ? "ifft_y_f64" : "ifft_y_f32", h, Ly, fp64, a, nullptr, s));
+    else
+        VIE_TRY((launch_line<T, false>(fp64 ? "ifft_y_f64" : "ifft_y_f32", h, Ly, a, noepi, s)));
     // x-inverse (frequencies read from their stored columns) + crop + material/Gram terms
     a = LineArgs{};
     a.in = W1;
@@ -810,7 +830,7 @@ static int matvec_impl(vie_handle* h, int R, const void* x, void* y, int op, cud
     a.oa = 0, a.ol = 1, a.ob = nx;
     a.n_in = Lx, a.n_out = nx, a.dir = +1;
     a.pin = h->colpos32;
-    VIE_TRY((launch_line<T, true>(sizeof(T) == 8 ? "ifft_x_epilogue_f64" : "ifft_x_epilogue_f32", h, Lx, a, e, s)));
+    VIE_TRY((launch_line<T, true>(fp64 ? "ifft_x_epilogue_f64" : "ifft_x_epilogue_f32", h, Lx, a, e, s)));
     return VIE_OK;
 }
 
@@ -829,7 +849,10 @@ int matvec_tune(vie_handle* h, int nrhs, int precision, cudaStream_t s, int op) 
     z.colkx = h->colkx32;
     z.R = nrhs, z.nz = h->nz, z.Lx = h->L[0], z.Ly = h->L[1];
     z.Ox = h->O[0], z.Oy = h->O[1], z.Oz = h->O[2];
-    const int ay = xy_ok(h) ? fft2::split_a(h->L[1]) : 1, by = xy_ok(h) ? h->L[1] / fft2::split_a(h->L[1]) : h->L[1];
+    // the row order of the y spectrum (transposed after the fused xy kernels and the two-pass
+    // line kernels, natural after the radix-4 ones)
+    const bool yt = xy_ok(h) || line2_ok(h->L[1]);
+    const int ay = yt ? fft2::split_a(h->L[1]) : 1, by = yt ? h->L[1] / fft2::split_a(h->L[1]) : h->L[1];
     z.ay = ay, z.by = by;
     z.mx = flip_mask(0), z.my = flip_mask(1), z.mz = flip_mask(2);
     if (op == VIE_OP_K) return zpass_f32_tune_k(h, z, s);

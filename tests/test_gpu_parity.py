@@ -150,12 +150,14 @@ def test_magnetic_post_parity(vie, shape):
 
 
 # (12, 5, 6) has Lx != Ly (line transforms along x and y), (5, 6, 70) has Lz = 256 and
-# (3, 2, 130) Lz = 512 (the FP32 z pass with 2-column tiles)
+# (3, 2, 130) Lz = 512 (the FP32 z pass with 2-column tiles); (100, 6, 5) and (6, 100, 5) take the
+# two-pass line kernels at length 256 along x, resp. y (the body grid's length), (3, 2, 130) the
+# radix-4 line kernel along y (Ly = 4)
 # FFT lengths (Lx, Ly, Lz): (8, 8, 8), (16, 16, 32), (32, 32, 16), (32, 32, 32), (32, 16, 16), (16, 16, 256),
-# (8, 4, 512), (16, 16, 64), (16, 16, 128), (16, 8, 128): every z-pass kernel (Lz 64 and 128 take the
-# split-product one), on the fused xy path (square xy circulant) and the line path
+# (8, 4, 512), (16, 16, 64), (16, 16, 128), (16, 8, 128), (256, 16, 16), (16, 256, 16): the z-pass
+# kernels at every length and tile width, on the fused xy path (square xy circulant) and the line path
 CASES = [((4, 4, 4), 1), ((7, 5, 9), 2), ((12, 10, 6), 3), ((16, 16, 16), 1), ((12, 5, 6), 2), ((5, 6, 70), 1),
-         ((3, 2, 130), 1), ((6, 5, 20), 2), ((6, 6, 36), 2), ((5, 4, 40), 1)]
+         ((3, 2, 130), 1), ((6, 5, 20), 2), ((6, 6, 36), 2), ((5, 4, 40), 1), ((100, 6, 5), 2), ((6, 100, 5), 2)]
 
 
 @pytest.fixture(scope="module")
