@@ -668,7 +668,7 @@ struct Solver {
     vie_handle* h;
     cudaStream_t st = nullptr;
     bool use_graph = false;
-    bool jm = false;  // the full JM-VIE system (FP64, two currents per voxel)
+    bool jm = false;  // the full JM-VIE system (two currents per voxel)
     // per matvec precision (VIE_FP64, VIE_FP32, VIE_BF16X3): the chunks of a cycle, then its end
     CycleGraph graph[3][kMaxChunks + 1];
     int* pinned = nullptr;                // [kMaxChunks] active counts after each chunk (pinned host memory)
