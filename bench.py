@@ -84,6 +84,10 @@ def parse():
     ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
                     help="profiling mode: set up the head64 workload and run N batched FP32 matvecs and one FP64 "
                          "matvec (16 RHS), print their timings; the solve benchmark is not run")
+    ap.add_argument("--line-matvec", action="store_true",
+                    help="profiling mode for the line-transform path: one warm-up and one timed FP32 matvec of 4 "
+                         "random RHS on a 128 x 96 x 64 tissue grid (FFT 256 x 256 x 128, about 3 GB on the "
+                         "device), per-kernel device times printed")
     return ap.parse_args()
 
 
@@ -1061,6 +1065,38 @@ def run_cufft_compare(args, local):
                           cufft_fft_pair_only_ms=t_fft, ratio=t_cufft / t_ours)), flush=True)
 
 
+def run_line_matvec(args, local):
+    """One warm-up and one timed FP32 matvec (op PA) of 4 random right-hand sides on a 128 x 96 x 64
+    grid of random tissue (3 mm voxels, 298 MHz): Lx = Ly = 256, so the xy transforms take the
+    line path, on inputs larger than L2; per-kernel device times from the library's counters."""
+    import torch
+
+    import paper_1902_02196_gb300 as vie
+    from synth import Grid, random_tissue
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    vie.build()
+    g = Grid(128, 96, 64, 0.003, 0.003, 0.003)
+    eps, sig = random_tissue(g, seed=3)
+    h = vie.vie_setup((g.nx, g.ny, g.nz, g.dx, g.dy, g.dz), 298e6, eps, sig)
+    x = torch.randn((4, 12) + g.shape, dtype=torch.complex64, device=dev,
+                    generator=torch.Generator(device=dev).manual_seed(5))
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    vie.vie_matvec(h, x, y, vie.VIE_FP32, vie.VIE_OP_PA)
+    torch.cuda.synchronize()
+    vie.vie_stats_reset(True)
+    vie.vie_matvec(h, x, y, vie.VIE_FP32, vie.VIE_OP_PA)
+    torch.cuda.synchronize()
+    _, st = vie.vie_stats_read()
+    vie.vie_stats_reset(False)
+    h.close()
+    kernels = {k: dict(launches=v[0], ms=v[1], gbs=v[2] / max(v[1], 1e-9) / 1e6) for k, v in st.items()}
+    print(json.dumps(dict(mode="line-matvec", workload="128x96x64 random tissue, 4 RHS, FP32 op PA",
+                          fft=[256, 256, 128], kernels=kernels)), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
@@ -1086,6 +1122,10 @@ def main():
         return
     if args.matvec_only:
         run_matvec_only(args, local)
+        return
+    if args.line_matvec:
+        if rank == 0:
+            run_line_matvec(args, local)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)
