@@ -11,7 +11,7 @@
 // and writes natural order, cropped.  The inverse loads, all L elements of each line, are issued
 // at once by cp.async; the forward ones (at most L/2 per line) are plain loads.  (The inverse x
 // transform with the voxel-wise terms stays on the radix-4 line kernel, which measured faster
-// with its epilogue: 5.6 ms against 6.1 ms on the body grid's 8-RHS spectrum.)
+// with its epilogue: 5.6 ms against 6.1 ms for 8 right-hand sides on a 128 x 128 x 256 grid.)
 #include "block.cuh"
 #include "fft.cuh"
 #include "fft2.cuh"
